@@ -1,0 +1,179 @@
+"""Plain FP64 CPU oracle of the MHD step of arXiv:1502.02935 (Section 2.1).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's
+``cpu_baseline`` / ``--impl reference`` legs may import this package; the product
+library never does.  The C sources next to this file are compiled with gcc
+(``-O2 -ffp-contract=off -fopenmp``) on first use, or by ``build()``.
+
+State arrays use the library's host format: U is (5, nz, ny, nx) with fields
+[rho, rho vx, rho vy, rho vz, E]; Bx is (nz, ny, nx+1), By (nz, ny+1, nx),
+Bz (nz+1, ny, nx), each face array holding the face at the low side of its index.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRCS = ["mhd_oracle.c", "thermal_oracle.c"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class OrcPatch(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("bc", C.c_int * 6), ("gamma", C.c_double)]
+
+
+class OrcSource(C.Structure):
+    _fields_ = [("potential", C.c_int), ("psi0", C.c_double), ("xc", C.c_double),
+                ("xw", C.c_double), ("v0", C.c_double), ("rc", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so from the C sources beside this file."""
+    srcs = [os.path.join(_HERE, s) for s in _SRCS if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "mhd_oracle.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            dp = C.POINTER(C.c_double)
+            L.orc_step.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp, C.c_double]
+            L.orc_step.restype = C.c_int
+            L.orc_cfl_dt.argtypes = [C.POINTER(OrcPatch), dp, dp, dp, dp, C.c_double]
+            L.orc_cfl_dt.restype = C.c_double
+            L.orc_run.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp,
+                                  C.c_double, C.c_double, C.c_int]
+            L.orc_run.restype = C.c_int
+            L.orc_hlld_batch.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp]
+            L.orc_reconstruct_1d.argtypes = [C.c_int, dp, dp, dp]
+            L.orc_diagnostics.argtypes = [C.POINTER(OrcPatch), dp, dp, dp, dp, dp, dp]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
+            _bind_thermal(L)
+            _lib = L
+    return _lib
+
+
+def _bind_thermal(L):
+    if not hasattr(L, "orc_thermal_integrate"):
+        return
+    dp = C.POINTER(C.c_double)
+    L.orc_thermal_integrate.argtypes = [C.c_long, dp, dp, dp, C.c_double, dp, C.POINTER(C.c_int)]
+    L.orc_thermal_integrate.restype = C.c_int
+    L.orc_cooling.argtypes = [C.c_long, dp, C.c_double, dp, dp]
+    L.orc_mlp_forward.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_mlp_backward.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_mlp_backward.restype = C.c_double
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "oracle wants C-contiguous float64"
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def patch_struct(g) -> OrcPatch:
+    p = OrcPatch()
+    p.nx, p.ny, p.nz = g.nx, g.ny, g.nz
+    p.x0, p.y0, p.z0 = g.x0, g.y0, g.z0
+    p.dx, p.dy, p.dz = g.dx, g.dy, g.dz
+    for a in range(6):
+        p.bc[a] = int(g.bc[a])
+    p.gamma = g.gamma
+    return p
+
+
+def source_struct(src) -> OrcSource:
+    s = OrcSource()
+    if src is None:
+        return s
+    s.potential = int(src.get("potential", 0))
+    for k in ("psi0", "xc", "xw", "v0", "rc"):
+        setattr(s, k, float(src.get(k, 0.0)))
+    return s
+
+
+def _copy_state(st):
+    return (np.ascontiguousarray(st.U, dtype=np.float64).copy(),
+            np.ascontiguousarray(st.Bx, dtype=np.float64).copy(),
+            np.ascontiguousarray(st.By, dtype=np.float64).copy(),
+            np.ascontiguousarray(st.Bz, dtype=np.float64).copy())
+
+
+def step(st, dt: float, source=None, nsteps: int = 1):
+    """``nsteps`` van Leer steps of fixed size dt; returns a new State."""
+    L = lib()
+    U, Bx, By, Bz = _copy_state(st)
+    p, s = patch_struct(st.geom), source_struct(source)
+    for _ in range(nsteps):
+        if L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt)) != 0:
+            raise ValueError("orc_step rejected its arguments")
+    return st.replace(U=U, Bx=Bx, By=By, Bz=Bz)
+
+
+def cfl_dt(st, cfl: float) -> float:
+    U, Bx, By, Bz = _copy_state(st)
+    return float(lib().orc_cfl_dt(C.byref(patch_struct(st.geom)), _p(U), _p(Bx), _p(By), _p(Bz), cfl))
+
+
+def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None):
+    """Advance to t_end with CFL time steps; returns (State, steps)."""
+    U, Bx, By, Bz = _copy_state(st)
+    p, s = patch_struct(st.geom), source_struct(source)
+    n = lib().orc_run(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(cfl),
+                      float(t_end), int(max_steps))
+    if n < 0:
+        raise ValueError("orc_run rejected its arguments")
+    return st.replace(U=U, Bx=Bx, By=By, Bz=Bz), n
+
+
+def hlld(wl, wr, bn, gamma: float) -> np.ndarray:
+    wl = np.ascontiguousarray(np.atleast_2d(wl), dtype=np.float64)
+    wr = np.ascontiguousarray(np.atleast_2d(wr), dtype=np.float64)
+    bn = np.ascontiguousarray(np.atleast_1d(bn), dtype=np.float64)
+    n = wl.shape[0]
+    out = np.zeros((n, 8))
+    lib().orc_hlld_batch(n, _p(wl), _p(wr), _p(bn), float(gamma), _p(out))
+    return out
+
+
+def reconstruct_1d(w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    wl = np.full_like(w, np.nan)
+    wr = np.full_like(w, np.nan)
+    lib().orc_reconstruct_1d(w.size, _p(w), _p(wl), _p(wr))
+    return wl, wr
+
+
+def diagnostics(st):
+    """(sums of the 5 cell fields over the interior, max |div B| * min(d))."""
+    U, Bx, By, Bz = _copy_state(st)
+    sums = np.zeros(5)
+    m = np.zeros(1)
+    lib().orc_diagnostics(C.byref(patch_struct(st.geom)), _p(U), _p(Bx), _p(By), _p(Bz),
+                          _p(sums), _p(m))
+    return sums, float(m[0])
+
+
+def set_threads(n: int) -> int:
+    return int(lib().orc_set_threads(int(n)))

@@ -1,0 +1,78 @@
+/*
+ * mhd_oracle.h -- plain, slow FP64 CPU oracle of the magneto-gas-dynamics step of
+ * Khoperskov, Vasiliev, Khoperskov & Lubimov (arXiv:1502.02935), Section 2.1.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call
+ * this file; only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * --impl reference legs use it.  It shares no code with the CUDA library.
+ *
+ * State format (identical to the library's host format, so both can be fed the
+ * same arrays):
+ *   U     : 5 cell fields [rho, rho*vx, rho*vy, rho*vz, E], each nz*ny*nx, x fastest.
+ *   Bx    : (nz, ny, nx+1) x-face values, Bx[k][j][i] sits on face x_{i-1/2}.
+ *   By    : (nz, ny+1, nx) y-face values on y_{j-1/2}.
+ *   Bz    : (nz+1, ny, nx) z-face values on z_{k-1/2}.
+ * For periodic axes and for trivial axes (n == 1) the last face layer repeats
+ * the first one.
+ */
+#ifndef MHD_ORACLE_H
+#define MHD_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1 };
+enum { ORC_POT_NONE = 0, ORC_POT_GAUSS_X = 1, ORC_POT_LOG_DISC = 2 };
+
+typedef struct {
+  int nx, ny, nz;
+  double x0, y0, z0;   /* coordinate of the low face of cell 0 along each axis */
+  double dx, dy, dz;
+  int bc[6];           /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
+  double gamma;
+} orc_patch;
+
+typedef struct {
+  int potential;
+  double psi0, xc, xw; /* Gaussian well Psi = -psi0 exp(-((x-xc)/xw)^2) (bow-shock test) */
+  double v0, rc;       /* logarithmic potential Psi = v0^2/2 ln(x^2+y^2+rc^2+z^2) */
+} orc_source;
+
+/* One van Leer predictor-corrector step of size dt (Eq. 7, Eq. 8).  Arrays are
+ * updated in place.  Returns 0, or -1 on bad arguments. */
+int orc_step(const orc_patch* p, const orc_source* s, double* U, double* Bx,
+             double* By, double* Bz, double dt);
+
+/* cfl * min over interior cells and active axes of d/(|v_d| + c_f,d). */
+double orc_cfl_dt(const orc_patch* p, const double* U, const double* Bx,
+                  const double* By, const double* Bz, double cfl);
+
+/* Advance to t_end with CFL steps (the last one clipped so t_end is hit).
+ * Returns the number of steps taken (max_steps caps it), -1 on bad arguments. */
+int orc_run(const orc_patch* p, const orc_source* s, double* U, double* Bx,
+            double* By, double* Bz, double cfl, double t_end, int max_steps);
+
+/* HLLD flux (Miyoshi & Kusano 2005) for a batch of n interfaces, in the frame of
+ * the interface normal: w = [rho, vn, vt1, vt2, p, (unused), Bt1, Bt2], bn = normal
+ * field.  flux = [rho, mn, mt1, mt2, E, 0, Bt1, Bt2] fluxes, 8 per interface. */
+void orc_hlld_batch(int n, const double* wl, const double* wr, const double* bn,
+                    double gamma, double* flux);
+
+/* kappa = 1/3 compressive minmod reconstruction on a 1D array of n values:
+ * for interfaces m = 2..n-2 (between w[m-1] and w[m]) writes wl[m], wr[m]. */
+void orc_reconstruct_1d(int n, const double* w, double* wl, double* wr);
+
+/* Total over the interior of the 5 cell fields (fixed order) and the maximum of
+ * |div B| * min(d) over interior cells. */
+void orc_diagnostics(const orc_patch* p, const double* U, const double* Bx,
+                     const double* By, const double* Bz, double sums[5],
+                     double* max_divb);
+
+/* Number of OpenMP threads used by the step (1 when built without OpenMP). */
+int orc_set_threads(int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,317 @@
+"""Seeded synthetic initial states for the MHD step (shared by the CUDA path and the oracle).
+
+This module only builds inputs: grid geometry, initial primitive fields and
+their conserved form.  It contains none of the step's arithmetic.  All fields
+are FP64 numpy arrays in the library's host format:
+
+  U  : (5, nz, ny, nx)   [rho, rho vx, rho vy, rho vz, E]
+  Bx : (nz, ny, nx+1)    Bx[k, j, i] on face x_{i-1/2}
+  By : (nz, ny+1, nx)    on face y_{j-1/2}
+  Bz : (nz+1, ny, nx)    on face z_{k-1/2}
+
+Units are code units with Heaviside-Lorentz field (P* = P + B^2/2, the text
+after Eq. 3 of arXiv:1502.02935); initial field values that the tests quote
+with a 1/sqrt(4 pi) keep it.  Non-uniform fields are built from a vector
+potential on cell edges, so that their discrete divergence is zero.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BC_PERIODIC = 0
+BC_OUTFLOW = 1
+
+
+@dataclasses.dataclass(frozen=True)
+class Geom:
+    nx: int
+    ny: int
+    nz: int
+    x0: float = 0.0
+    y0: float = 0.0
+    z0: float = 0.0
+    dx: float = 1.0
+    dy: float = 1.0
+    dz: float = 1.0
+    bc: tuple = (0, 0, 0, 0, 0, 0)
+    gamma: float = 5.0 / 3.0
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def centres(self):
+        x = self.x0 + (np.arange(self.nx) + 0.5) * self.dx
+        y = self.y0 + (np.arange(self.ny) + 0.5) * self.dy
+        z = self.z0 + (np.arange(self.nz) + 0.5) * self.dz
+        return x, y, z
+
+    def faces(self):
+        x = self.x0 + np.arange(self.nx + 1) * self.dx
+        y = self.y0 + np.arange(self.ny + 1) * self.dy
+        z = self.z0 + np.arange(self.nz + 1) * self.dz
+        return x, y, z
+
+
+@dataclasses.dataclass
+class State:
+    geom: Geom
+    U: np.ndarray
+    Bx: np.ndarray
+    By: np.ndarray
+    Bz: np.ndarray
+
+    def replace(self, **kw) -> "State":
+        return dataclasses.replace(self, **kw)
+
+    def copy(self) -> "State":
+        return State(self.geom, self.U.copy(), self.Bx.copy(), self.By.copy(), self.Bz.copy())
+
+    def faces_flat(self) -> np.ndarray:
+        """Bx, By, Bz concatenated (the library's face block)."""
+        return np.concatenate([self.Bx.ravel(), self.By.ravel(), self.Bz.ravel()])
+
+    def bcc(self):
+        """Cell-centred field as the mean of the two face values (Eq. 6 of the paper)."""
+        return (0.5 * (self.Bx[:, :, :-1] + self.Bx[:, :, 1:]),
+                0.5 * (self.By[:, :-1, :] + self.By[:, 1:, :]),
+                0.5 * (self.Bz[:-1, :, :] + self.Bz[1:, :, :]))
+
+
+def face_block_size(g: Geom) -> int:
+    return ((g.nx + 1) * g.ny * g.nz + g.nx * (g.ny + 1) * g.nz + g.nx * g.ny * (g.nz + 1))
+
+
+def state_from_prim(g: Geom, rho, vx, vy, vz, p, Bx, By, Bz) -> State:
+    """Conserved state from primitive cell fields and face fields.
+
+    E = p/(gamma-1) + rho v^2/2 + Bcc^2/2 with Bcc the mean of the face values, so
+    that the closure recovers p exactly up to rounding (text after Eq. 3)."""
+    shp = (g.nz, g.ny, g.nx)
+    rho, vx, vy, vz, p = (np.broadcast_to(np.asarray(a, dtype=np.float64), shp) for a in (rho, vx, vy, vz, p))
+    Bx = np.ascontiguousarray(np.broadcast_to(np.asarray(Bx, dtype=np.float64), (g.nz, g.ny, g.nx + 1)))
+    By = np.ascontiguousarray(np.broadcast_to(np.asarray(By, dtype=np.float64), (g.nz, g.ny + 1, g.nx)))
+    Bz = np.ascontiguousarray(np.broadcast_to(np.asarray(Bz, dtype=np.float64), (g.nz + 1, g.ny, g.nx)))
+    st = State(g, np.zeros((5,) + shp), Bx, By, Bz)
+    bx, by, bz = st.bcc()
+    U = st.U
+    U[0] = rho
+    U[1] = rho * vx
+    U[2] = rho * vy
+    U[3] = rho * vz
+    U[4] = p / (g.gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz)
+    return st
+
+
+def faces_from_Az(g: Geom, Az):
+    """Face fields of B = curl(A_z z^) from A_z(x, y) sampled on z-edges (exact zero divergence)."""
+    xf, yf, _ = g.faces()
+    A = Az(xf[None, :], yf[:, None])  # (ny+1, nx+1) at edges (x_{i-1/2}, y_{j-1/2})
+    bx = (A[1:, :] - A[:-1, :]) / g.dy          # (ny, nx+1)
+    by = -(A[:, 1:] - A[:, :-1]) / g.dx         # (ny+1, nx)
+    Bx = np.broadcast_to(bx, (g.nz, g.ny, g.nx + 1))
+    By = np.broadcast_to(by, (g.nz, g.ny + 1, g.nx))
+    Bz = np.zeros((g.nz + 1, g.ny, g.nx))
+    return Bx, By, Bz
+
+
+# ---------------------------------------------------------------- workloads --
+
+def brio_wu(n: int = 800, axis: int = 0, transverse: int = 1) -> State:
+    """Brio-Wu shock tube (Section 3.4): gamma = 2, Bn = 0.75; left rho = 1, p = 1,
+    Bt = 1; right rho = 0.125, p = 0.1, Bt = -1; domain [0, 1], interface at 0.5,
+    outflow ends.  The tube runs along ``axis``; ``transverse`` other cells pad the
+    other axes (periodic) for plane-parallel checks."""
+    dims = [transverse, transverse, transverse]
+    dims[axis] = n
+    d = [1.0 / n, 1.0 / n, 1.0 / n]
+    bc = [BC_PERIODIC] * 6
+    bc[2 * axis] = bc[2 * axis + 1] = BC_OUTFLOW
+    g = Geom(dims[0], dims[1], dims[2], 0.0, 0.0, 0.0, d[0], d[1], d[2], tuple(bc), 2.0)
+    t1 = (axis + 1) % 3
+    xs = g.centres()[axis]
+    left = xs < 0.5
+    shp = (g.nz, g.ny, g.nx)
+
+    def along(v):
+        s = [1, 1, 1]
+        s[2 - axis] = v.size
+        return np.broadcast_to(v.reshape(s), shp)
+
+    rho = along(np.where(left, 1.0, 0.125))
+    p = along(np.where(left, 1.0, 0.1))
+    bt = np.where(left, 1.0, -1.0)
+    B = [None, None, None]
+    fshape = [(g.nz, g.ny, g.nx + 1), (g.nz, g.ny + 1, g.nx), (g.nz + 1, g.ny, g.nx)]
+    for a in range(3):
+        if a == axis:
+            B[a] = np.full(fshape[a], 0.75)
+        elif a == t1:
+            s = [1, 1, 1]
+            s[2 - axis] = n
+            B[a] = np.broadcast_to(bt.reshape(s), fshape[a]).copy()
+        else:
+            B[a] = np.zeros(fshape[a])
+    return state_from_prim(g, rho, 0.0, 0.0, 0.0, p, *B)
+
+
+def ryu_jones(n: int = 800) -> State:
+    """Ryu-Jones 7-wave Riemann problem (Section 3.5), gamma = 5/3, on [0, 1] with the
+    discontinuity at 0.5 and outflow ends."""
+    g = Geom(n, 1, 1, 0.0, 0.0, 0.0, 1.0 / n, 1.0, 1.0, (1, 1, 0, 0, 0, 0), 5.0 / 3.0)
+    x = g.centres()[0]
+    left = x < 0.5
+    s4 = 1.0 / math.sqrt(4.0 * math.pi)
+    sel = lambda a, b: np.where(left, a, b)[None, None, :]
+    Bx = np.full((1, 1, n + 1), 4.0 * s4)
+    By = np.broadcast_to(sel(3.6 * s4, 4.0 * s4), (1, 2, n)).copy()
+    Bz = np.broadcast_to(sel(2.0 * s4, 2.0 * s4), (2, 1, n)).copy()
+    return state_from_prim(g, sel(1.08, 1.0), sel(1.2, 0.0), sel(0.01, 0.0), sel(0.5, 0.0),
+                           sel(0.95, 1.0), Bx, By, Bz)
+
+
+def sod(n: int = 200) -> State:
+    """Sod shock tube (Section 3.1) with B = 0, gamma = 1.4, on [-1, 1], interface at 0."""
+    g = Geom(n, 1, 1, -1.0, 0.0, 0.0, 2.0 / n, 1.0, 1.0, (1, 1, 0, 0, 0, 0), 1.4)
+    x = g.centres()[0]
+    left = (x < 0.0)[None, None, :]
+    return state_from_prim(g, np.where(left, 1.0, 0.125), 0.0, 0.0, 0.0, np.where(left, 1.0, 0.1),
+                           0.0, 0.0, 0.0)
+
+
+def orszag_tang(nx: int = 512, ny: int | None = None) -> State:
+    """2D periodic MHD vortex on [0, 1]^2, gamma = 5/3, rho = 25/(36 pi), p = 5/(12 pi),
+    v = (-sin 2 pi y, sin 2 pi x, 0), B = (-sin 2 pi y, sin 4 pi x, 0)/sqrt(4 pi)
+    from A_z = (cos 4 pi x/(4 pi) + cos 2 pi y/(2 pi))/sqrt(4 pi)."""
+    ny = nx if ny is None else ny
+    g = Geom(nx, ny, 1, 0.0, 0.0, 0.0, 1.0 / nx, 1.0 / ny, 1.0, (0,) * 6, 5.0 / 3.0)
+    s4 = 1.0 / math.sqrt(4.0 * math.pi)
+    Az = lambda x, y: (np.cos(4 * np.pi * x) / (4 * np.pi) + np.cos(2 * np.pi * y) / (2 * np.pi)) * s4
+    Bx, By, Bz = faces_from_Az(g, Az)
+    x, y, _ = g.centres()
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    vx = -np.sin(2 * np.pi * Y)[None]
+    vy = np.sin(2 * np.pi * X)[None]
+    return state_from_prim(g, 25.0 / (36.0 * np.pi), vx, vy, 0.0, 5.0 / (12.0 * np.pi), Bx, By, Bz)
+
+
+def solenoidal_velocity(n: tuple, seed: int, kmin: float = 2.0, kmax: float = 8.0) -> np.ndarray:
+    """Random-phase solenoidal field on a periodic (nz, ny, nx) box: Gaussian modes for
+    integer wavevectors with kmin <= |k| <= kmax, amplitude |v(k)| ~ |k|^-2 (shell
+    spectrum ~ k^-2), projected with v <- v - k (k.v)/k^2; unit rms.  Returns
+    (3, nz, ny, nx)."""
+    nz, ny, nx = n
+    rng = np.random.default_rng(seed)
+    kz = np.fft.fftfreq(nz, 1.0 / nz)[:, None, None]
+    ky = np.fft.fftfreq(ny, 1.0 / ny)[None, :, None]
+    kx = np.fft.rfftfreq(nx, 1.0 / nx)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    kk = np.sqrt(k2)
+    mask = (kk >= kmin) & (kk <= kmax)
+    shape = k2.shape
+    amp = np.where(mask, np.maximum(kk, 1e-30) ** -2.0, 0.0)
+    vh = []
+    for _ in range(3):
+        re = rng.standard_normal(shape)
+        im = rng.standard_normal(shape)
+        vh.append(amp * (re + 1j * im))
+    kdotv = kx * vh[0] + ky * vh[1] + kz * vh[2]
+    k2s = np.where(k2 > 0, k2, 1.0)
+    vh = [vh[0] - kx * kdotv / k2s, vh[1] - ky * kdotv / k2s, vh[2] - kz * kdotv / k2s]
+    v = np.stack([np.fft.irfftn(c, s=(nz, ny, nx), axes=(0, 1, 2)) for c in vh])
+    rms = math.sqrt(float(np.mean(np.sum(v * v, axis=0))))
+    return v / rms
+
+
+def turbulence(n=256, seed: int = 1502, mach: float = 2.0) -> State:
+    """Driven-free turbulent box: periodic [0, 1]^3, gamma = 5/3, rho = 1, p = 1,
+    B = (0.1, 0, 0), solenoidal random velocity (2 <= |k| <= 8, shell spectrum
+    ~ k^-2) scaled to rms Mach ``mach``.  ``n`` is an int or (nx, ny, nz)."""
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+    g = Geom(nx, ny, nz, 0.0, 0.0, 0.0, 1.0 / nx, 1.0 / ny, 1.0 / nz, (0,) * 6, 5.0 / 3.0)
+    v = solenoidal_velocity((nz, ny, nx), seed) * (mach * math.sqrt(5.0 / 3.0))
+    return state_from_prim(g, 1.0, v[0], v[1], v[2], 1.0, 0.1, 0.0, 0.0)
+
+
+def _splitmix64(state: int):
+    state = (state + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return state, z ^ (z >> 31)
+
+
+def blast_patch_specs(n_patches: int = 64, seed: int = 1502, sizes=(32, 48, 64, 96, 128)):
+    """Per-patch (edge, centre, field direction) drawn with splitmix64 from ``seed``."""
+    s = seed & 0xFFFFFFFFFFFFFFFF
+    out = []
+
+    def u01():
+        nonlocal s
+        s, z = _splitmix64(s)
+        return (z >> 11) * (1.0 / 9007199254740992.0)
+
+    for _ in range(n_patches):
+        edge = sizes[min(int(u01() * len(sizes)), len(sizes) - 1)]
+        centre = (u01(), u01(), u01())
+        cz = 2.0 * u01() - 1.0
+        ph = 2.0 * math.pi * u01()
+        r = math.sqrt(max(0.0, 1.0 - cz * cz))
+        out.append((edge, centre, (r * math.cos(ph), r * math.sin(ph), cz)))
+    return out
+
+
+def blast(edge: int, centre, direction, gamma: float = 5.0 / 3.0) -> State:
+    """Periodic blast patch on [0, 1]^3 with edge^3 cells: rho = 1, p = 0.1, p = 10 within
+    0.1 (minimum-image distance) of ``centre``, uniform B = (1/sqrt 2) * direction."""
+    n = edge
+    g = Geom(n, n, n, 0.0, 0.0, 0.0, 1.0 / n, 1.0 / n, 1.0 / n, (0,) * 6, gamma)
+    x, y, z = g.centres()
+
+    def mi(a, c):
+        d = np.abs(a - c)
+        return np.minimum(d, 1.0 - d)
+
+    r2 = (mi(z, centre[2])[:, None, None] ** 2 + mi(y, centre[1])[None, :, None] ** 2
+          + mi(x, centre[0])[None, None, :] ** 2)
+    p = np.where(r2 < 0.01, 10.0, 0.1)
+    b = [c / math.sqrt(2.0) for c in direction]
+    return state_from_prim(g, 1.0, 0.0, 0.0, 0.0, p, b[0], b[1], b[2])
+
+
+def blast_batch(n_patches: int = 64, seed: int = 1502, sizes=(32, 48, 64, 96, 128)):
+    return [blast(e, c, d) for (e, c, d) in blast_patch_specs(n_patches, seed, sizes)]
+
+
+def uniform(g: Geom, rho=1.0, v=(0.0, 0.0, 0.0), p=1.0, B=(0.0, 0.0, 0.0)) -> State:
+    return state_from_prim(g, rho, v[0], v[1], v[2], p, B[0], B[1], B[2])
+
+
+def alfven_wave(n: int, amp: float = 1e-6, gamma: float = 5.0 / 3.0, polarisation: str = "inplane") -> State:
+    """Linear Alfven wave on the periodic box [0, 1]^2 (n x n cells): rho = 1, p = 1/gamma,
+    B0 = khat (|B0| = 1 along k = 2 pi (1, 1), wavelength 1/sqrt 2, Alfven speed 1).
+    dv = amp sin(k.x) e, dB = -sqrt(rho) dv (a wave moving along +k), with e either the
+    in-plane unit vector perpendicular to k ("inplane", field from a vector potential)
+    or z ("z")."""
+    rho0, p0 = 1.0, 1.0 / gamma
+    g = Geom(n, n, 1, 0.0, 0.0, 0.0, 1.0 / n, 1.0 / n, 1.0, (0,) * 6, gamma)
+    kx = ky = 2.0 * np.pi
+    kn = math.hypot(kx, ky)
+    kh = (kx / kn, ky / kn)
+    x, y, _ = g.centres()
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    sph = np.sin(kx * X + ky * Y)[None]
+    if polarisation == "inplane":
+        e = (-kh[1], kh[0])
+        c = -amp * math.sqrt(rho0) / kn
+        # B = curl(A_z z) with A_z = y kh_x - x kh_y (uniform B0 = khat) + c cos(k.x)
+        Az = lambda xx, yy: yy * kh[0] - xx * kh[1] + c * np.cos(kx * xx + ky * yy)
+        Bx, By, Bz = faces_from_Az(g, Az)
+        return state_from_prim(g, rho0, amp * e[0] * sph, amp * e[1] * sph, 0.0, p0, Bx, By, Bz)
+    Az = lambda xx, yy: yy * kh[0] - xx * kh[1]
+    Bx, By, _ = faces_from_Az(g, Az)
+    Bz = np.broadcast_to(-math.sqrt(rho0) * amp * sph, (2, n, n)).copy()
+    return state_from_prim(g, rho0, 0.0, 0.0, amp * sph, p0, Bx, By, Bz)
