@@ -1,0 +1,47 @@
+// mhd_backend.h -- per-precision launch table shared by the host runtime.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace mhd {
+struct PatchDev;
+struct StageArgs;
+
+// Optional per-launch CUDA-event pairs recorded on the launching stream.
+enum { KC_PRIM = 0, KC_FLUX1 = 1, KC_FLUX2 = 4, KC_EMF = 7, KC_UPDATE = 8, KC_CFL = 9, KC_COUNT = 10 };
+struct ProfRec {
+  static constexpr int kMax = 64;
+  cudaEvent_t a[kMax], b[kMax];
+  int cls[kMax];
+  int n = 0;
+};
+
+struct ProfScope {
+  ProfRec* p;
+  int slot;
+  cudaStream_t s;
+  ProfScope(ProfRec* p_, int cls, cudaStream_t s_) : p(p_), slot(-1), s(s_) {
+    if (p && p->n < ProfRec::kMax) {
+      slot = p->n++;
+      p->cls[slot] = cls;
+      cudaEventRecord(p->a[slot], s);
+    }
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(p->b[slot], s);
+  }
+};
+
+struct Backend {
+  size_t scratch_elem;  // bytes per scratch value (8 for FP64, 4 for the mixed path)
+  // one stage (0 predictor, 1 corrector) of a van Leer step of one patch
+  int (*stage)(const PatchDev&, const StageArgs&, cudaStream_t, long long* launches, ProfRec* prof);
+  // CFL limit of the current state into the patch's cfl_min slot
+  int (*cfl)(const PatchDev&, cudaStream_t, long long* launches);
+  int (*hlld)(int n, const double* wl, const double* wr, const double* bn, double gamma,
+              double* flux, cudaStream_t s);
+};
+
+Backend backend_fp64();
+Backend backend_mixed();
+}  // namespace mhd

@@ -1,0 +1,588 @@
+// mhd_device.cuh -- device data layout and per-point phase functions of the MHD step
+// (arXiv:1502.02935, Section 2.1), templated on the bulk arithmetic type R:
+//   R = double : the plain FP64 method;
+//   R = float  : FP32 reconstruction / Riemann / EMF / flux-difference arithmetic with
+//                FP64 pressure recovery and FP64 accumulation of the conserved state.
+//
+// Layout in HBM (per patch, all SoA, x fastest):
+//   state  Un, Uh : 8 FP64 fields [rho, mx, my, mz, E, Bx, By, Bz], extents PX*PY*PZ
+//                   with PX = round4(nx+1), PY = ny+1, PZ = nz+1 (one extra layer for
+//                   the high boundary face); cell (i,j,k) and faces i-1/2, j-1/2, k-1/2
+//                   share the index i + PX (j + PY k).  No ghost cells: boundary
+//                   conditions are index maps applied on every load.
+//   scratch W, F, E : R, padded by 2 cells on active axes (QX = nx + 4 ...), holding
+//                   primitives W (8), face fluxes F_d (7 per direction: rho, mx, my, mz,
+//                   E, B_t1, B_t2 with (d, t1, t2) cyclic) and edge EMFs (3).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace mhd {
+
+enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BXF = 5, BYF = 6, BZF = 7 };
+enum { WR = 0, WVX = 1, WVY = 2, WVZ = 3, WP = 4, WBX = 5, WBY = 6, WBZ = 7 };
+enum { NFLUX = 7 };
+enum : int { ERR_NONFINITE = 1, ERR_NEGATIVE = 2, ERR_TIMEOUT = 4 };
+enum { POT_NONE = 0, POT_GAUSS_X = 1, POT_LOG_DISC = 2 };
+
+struct PatchDev {
+  int n[3];      // interior cells per axis
+  int act[3];    // axis active (n > 1)
+  int per[3];    // periodic (trivial axes count as periodic with n = 1)
+  int nface[3];  // owned faces along each normal: n, or n + 1 on an active outflow axis
+  int g2[3];     // scratch padding (2 on active axes)
+  int PX, PY, PZ;
+  long long FS;  // state field stride
+  int QX, QY, QZ;
+  long long QS;  // scratch field stride
+  double d[3], inv_d[3], lo[3], gamma;
+  double* Un;
+  double* Uh;
+  void* W;
+  void* F[3];
+  void* E;
+  unsigned long long* cfl_min;  // per-patch ordered-bits minimum of the CFL limit
+  double* dt_used;
+  int* err;
+  int index;
+};
+
+struct SourceDev {
+  int potential;
+  double psi0, xc, xw, v0, rc;
+};
+
+struct StageArgs {
+  int stage;       // 0 predictor (donor cell, h = dt/2), 1 corrector (kappa-scheme, h = dt)
+  double dt_host;  // > 0: use it; <= 0: cfl * device CFL limit
+  double cfl;
+  SourceDev src;
+};
+
+// ------------------------------------------------------------------ indexing --
+__device__ __forceinline__ int cmap(const PatchDev& P, int a, int i) {
+  const int n = P.n[a];
+  if (i >= 0 && i < n) return i;
+  if (P.per[a]) {
+    int m = i % n;
+    return m < 0 ? m + n : m;
+  }
+  return i < 0 ? 0 : n - 1;
+}
+
+__device__ __forceinline__ int fmap(const PatchDev& P, int a, int f) {
+  const int n = P.n[a];
+  if (P.per[a]) {
+    if (f >= 0 && f < n) return f;
+    int m = f % n;
+    return m < 0 ? m + n : m;
+  }
+  return f < 0 ? 0 : (f > n ? n : f);
+}
+
+__device__ __forceinline__ long long sidx(const PatchDev& P, int i, int j, int k) {
+  return (long long)i + (long long)P.PX * ((long long)j + (long long)P.PY * k);
+}
+
+__device__ __forceinline__ long long qidx(const PatchDev& P, int i, int j, int k) {
+  return (long long)(i + P.g2[0]) +
+         (long long)P.QX * ((long long)(j + P.g2[1]) + (long long)P.QY * (k + P.g2[2]));
+}
+
+__device__ __forceinline__ long long qstride(const PatchDev& P, int a) {
+  return a == 0 ? 1LL : (a == 1 ? (long long)P.QX : (long long)P.QX * P.QY);
+}
+
+// --------------------------------------------------------------- arithmetic --
+template <class R> struct Ar;
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  static constexpr double degen = 1e-8;
+};
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static constexpr float degen = 1e-8f;
+};
+
+// 1/rho for the FP64 pressure recovery.  FP64 path: IEEE division.  Mixed path: the
+// correctly rounded FP32 reciprocal refined by one Newton-Raphson step in FP64
+// (r <- r + r (1 - rho r)), which squares its relative error (~1e-14).
+template <class R> __device__ __forceinline__ double inv_density(double rho);
+template <> __device__ __forceinline__ double inv_density<double>(double rho) { return 1.0 / rho; }
+template <> __device__ __forceinline__ double inv_density<float>(double rho) {
+  double r = (double)__frcp_rn((float)rho);
+  double e = fma(-rho, r, 1.0);
+  return fma(r, e, r);
+}
+
+template <class R> __device__ __forceinline__ R fast_speed(R rho, R p, R bb, R bn2, R gam) {
+  // c_f^2 = [gamma p + B^2 + sqrt((gamma p + B^2)^2 - 4 gamma p Bn^2)] / (2 rho)
+  R gp = gam * p;
+  R s = gp + bb;
+  R disc = s * s - R(4) * gp * bn2;
+  disc = disc > R(0) ? disc : R(0);
+  return Ar<R>::sqrt_((s + Ar<R>::sqrt_(disc)) * Ar<R>::rcp(R(2) * rho));
+}
+
+// ------------------------------------------------------------------ HLLD ----
+// Miyoshi & Kusano (2005) HLLD flux, the MHD Riemann solver named in Section 2.1.
+// w = [rho, vn, vt1, vt2, p, Bt1, Bt2] on each side, bn the face-normal field.
+// f = [rho, m_n, m_t1, m_t2, E, Bt1, Bt2] fluxes (Eq. 3 in the interface frame).
+template <class R>
+__device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f) {
+  const R half = R(0.5);
+  const R igm1 = Ar<R>::rcp(gam - R(1));
+  const R bn2 = bn * bn;
+  const R rl = wl[0], ul = wl[1], vl = wl[2], zl = wl[3], pl = wl[4], byl = wl[5], bzl = wl[6];
+  const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4], byr = wr[5], bzr = wr[6];
+  const R bbl = bn2 + byl * byl + bzl * bzl;
+  const R bbr = bn2 + byr * byr + bzr * bzr;
+  const R ptl = pl + half * bbl, ptr = pr + half * bbr;
+  const R el = pl * igm1 + half * rl * (ul * ul + vl * vl + zl * zl) + half * bbl;
+  const R er = pr * igm1 + half * rr * (ur * ur + vr * vr + zr * zr) + half * bbr;
+  const R cfl = fast_speed<R>(rl, pl, bbl, bn2, gam);
+  const R cfr = fast_speed<R>(rr, pr, bbr, bn2, gam);
+  const R cmax = cfl > cfr ? cfl : cfr;
+  const R sl = (ul < ur ? ul : ur) - cmax;
+  const R sr = (ul > ur ? ul : ur) + cmax;
+  const R vbl = ul * bn + vl * byl + zl * bzl;
+  const R vbr = ur * bn + vr * byr + zr * bzr;
+
+  if (sl > R(0)) {
+    f[0] = rl * ul;
+    f[1] = rl * ul * ul + ptl - bn2;
+    f[2] = rl * ul * vl - bn * byl;
+    f[3] = rl * ul * zl - bn * bzl;
+    f[4] = (el + ptl) * ul - vbl * bn;
+    f[5] = byl * ul - bn * vl;
+    f[6] = bzl * ul - bn * zl;
+    return;
+  }
+  if (sr < R(0)) {
+    f[0] = rr * ur;
+    f[1] = rr * ur * ur + ptr - bn2;
+    f[2] = rr * ur * vr - bn * byr;
+    f[3] = rr * ur * zr - bn * bzr;
+    f[4] = (er + ptr) * ur - vbr * bn;
+    f[5] = byr * ur - bn * vr;
+    f[6] = bzr * ur - bn * zr;
+    return;
+  }
+  const R dl = sl - ul, dr = sr - ur;
+  const R iden = Ar<R>::rcp(dr * rr - dl * rl);
+  const R sm = (dr * rr * ur - dl * rl * ul - ptr + ptl) * iden;
+  const R pts = (dr * rr * ptl - dl * rl * ptr + rl * rr * dr * dl * (ur - ul)) * iden;
+
+  // single-star states on both sides
+  R rs[2], vs[2], zs[2], bys[2], bzs[2], es[2];
+  {
+    const R S[2] = {sl, sr};
+    const R rho[2] = {rl, rr}, un[2] = {ul, ur}, v1[2] = {vl, vr}, v2[2] = {zl, zr};
+    const R b1[2] = {byl, byr}, b2[2] = {bzl, bzr}, ee[2] = {el, er}, pt[2] = {ptl, ptr};
+    const R vb[2] = {vbl, vbr};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const R ds = S[s] - un[s];
+      const R ism = Ar<R>::rcp(S[s] - sm);
+      rs[s] = rho[s] * ds * ism;
+      const R t1 = rho[s] * ds * (S[s] - sm);
+      const R den = t1 - bn2;
+      if (Ar<R>::abs_(den) < Ar<R>::degen * (Ar<R>::abs_(t1) + bn2)) {
+        vs[s] = v1[s];
+        zs[s] = v2[s];
+        bys[s] = b1[s];
+        bzs[s] = b2[s];
+      } else {
+        const R iden2 = Ar<R>::rcp(den);
+        const R fv = bn * (sm - un[s]) * iden2;
+        const R fb = (rho[s] * ds * ds - bn2) * iden2;
+        vs[s] = v1[s] - b1[s] * fv;
+        zs[s] = v2[s] - b2[s] * fv;
+        bys[s] = b1[s] * fb;
+        bzs[s] = b2[s] * fb;
+      }
+      const R vbs = sm * bn + vs[s] * bys[s] + zs[s] * bzs[s];
+      es[s] = (ds * ee[s] - pt[s] * un[s] + pts * sm + bn * (vb[s] - vbs)) * ism;
+    }
+  }
+  const R sqrl = Ar<R>::sqrt_(rs[0]), sqrr = Ar<R>::sqrt_(rs[1]);
+  const R abn = Ar<R>::abs_(bn);
+  const R ssl = sm - abn * Ar<R>::rcp(sqrl);
+  const R ssr = sm + abn * Ar<R>::rcp(sqrr);
+
+  // choose the side and whether the double-star state is needed
+  int side;  // 0: left, 1: right
+  bool dbl;
+  R S, Ss;
+  if (ssl >= R(0)) {
+    side = 0; dbl = false;
+  } else if (sm >= R(0)) {
+    side = 0; dbl = true;
+  } else if (ssr >= R(0)) {
+    side = 1; dbl = true;
+  } else {
+    side = 1; dbl = false;
+  }
+  S = side ? sr : sl;
+  Ss = side ? ssr : ssl;
+  const R rho = side ? rr : rl, un = side ? ur : ul, v1 = side ? vr : vl, v2 = side ? zr : zl;
+  const R b1 = side ? byr : byl, b2 = side ? bzr : bzl, ee = side ? er : el, pt = side ? ptr : ptl;
+  const R vb = side ? vbr : vbl;
+  // F_a = physical flux of the outer state
+  R F0 = rho * un;
+  R F1 = rho * un * un + pt - bn2;
+  R F2 = rho * un * v1 - bn * b1;
+  R F3 = rho * un * v2 - bn * b2;
+  R F4 = (ee + pt) * un - vb * bn;
+  R F5 = b1 * un - bn * v1;
+  R F6 = b2 * un - bn * v2;
+  // F*_a = F_a + S_a (U*_a - U_a)
+  const R rsa = rs[side], vsa = vs[side], zsa = zs[side], bysa = bys[side], bzsa = bzs[side];
+  const R esa = es[side];
+  F0 += S * (rsa - rho);
+  F1 += S * (rsa * sm - rho * un);
+  F2 += S * (rsa * vsa - rho * v1);
+  F3 += S * (rsa * zsa - rho * v2);
+  F4 += S * (esa - ee);
+  F5 += S * (bysa - b1);
+  F6 += S * (bzsa - b2);
+  if (dbl) {
+    // double-star states (sqrt(rho*)-weighted, M&K Eq. 59-63); F** = F* + S*(U** - U*)
+    const R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
+    const R isum = Ar<R>::rcp(sqrl + sqrr);
+    const R vss = (sqrl * vs[0] + sqrr * vs[1] + (bys[1] - bys[0]) * sgn) * isum;
+    const R zss = (sqrl * zs[0] + sqrr * zs[1] + (bzs[1] - bzs[0]) * sgn) * isum;
+    const R byss = (sqrl * bys[1] + sqrr * bys[0] + sqrl * sqrr * (vs[1] - vs[0]) * sgn) * isum;
+    const R bzss = (sqrl * bzs[1] + sqrr * bzs[0] + sqrl * sqrr * (zs[1] - zs[0]) * sgn) * isum;
+    const R vbsa = sm * bn + vsa * bysa + zsa * bzsa;
+    const R vbss = sm * bn + vss * byss + zss * bzss;
+    const R sq = side ? sqrr : sqrl;
+    const R ess = side ? esa + sq * (vbsa - vbss) * sgn : esa - sq * (vbsa - vbss) * sgn;
+    F2 += Ss * (rsa * vss - rsa * vsa);
+    F3 += Ss * (rsa * zss - rsa * zsa);
+    F4 += Ss * (ess - esa);
+    F5 += Ss * (byss - bysa);
+    F6 += Ss * (bzss - bzsa);
+  }
+  f[0] = F0; f[1] = F1; f[2] = F2; f[3] = F3; f[4] = F4; f[5] = F5; f[6] = F6;
+}
+
+// --------------------------------------------------------- reconstruction ----
+// kappa = 1/3 compressive minmod scheme (Eq. 12-14 read in the standard form that is
+// third-order upwind biased): K1 = 1/6, K2 = 1/3, b = 4.
+template <class R> __device__ __forceinline__ R minmod(R a, R b) {
+  R s = a > R(0) ? R(1) : (a < R(0) ? R(-1) : R(0));
+  R m = Ar<R>::abs_(a) < s * b ? Ar<R>::abs_(a) : s * b;
+  return s * (m > R(0) ? m : R(0));
+}
+
+template <class R>
+__device__ __forceinline__ void kappa_face(R wm1, R w0, R w1, R w2, R& wl, R& wr) {
+  const R K1 = R(1) / R(6), K2 = R(1) / R(3), b = R(4);
+  const R dwm = w0 - wm1, dw0 = w1 - w0, dwp = w2 - w1;
+  wl = w0 + K1 * minmod<R>(dwm, b * dw0) + K2 * minmod<R>(dw0, b * dwm);
+  wr = w1 - K1 * minmod<R>(dwp, b * dw0) - K2 * minmod<R>(dw0, b * dwp);
+}
+
+// --------------------------------------------------------------- sources ----
+template <class R>
+__device__ __forceinline__ void grad_psi(const SourceDev& s, double x, double y, double z, R* g) {
+  g[0] = g[1] = g[2] = R(0);
+  if (s.potential == POT_GAUSS_X) {
+    R u = (R)((x - s.xc) / s.xw);
+    g[0] = (R)s.psi0 * R(2) * u / (R)s.xw * exp(-u * u);
+  } else if (s.potential == POT_LOG_DISC) {
+    R v02 = (R)(s.v0 * s.v0);
+    R q = (R)(x * x + y * y + s.rc * s.rc + z * z);
+    R iq = v02 / q;
+    g[0] = (R)x * iq;
+    g[1] = (R)y * iq;
+    g[2] = (R)z * iq;
+  }
+}
+
+// ---------------------------------------------------------- phase: recovery --
+// W at a (possibly ghost) cell from U via the boundary index maps: Eq. 6 for the
+// cell-centred field, the energy closure after Eq. 3 for p (FP64 in both paths).
+// Returns the CFL limit min_d d/(|v_d| + c_f,d) for interior cells (else +inf).
+template <class R>
+__device__ __forceinline__ double prim_point(const PatchDev& P, const double* __restrict__ U,
+                                             R* __restrict__ W, int i, int j, int k, bool store,
+                                             bool interior) {
+  const int ci = cmap(P, 0, i), cj = cmap(P, 1, j), ck = cmap(P, 2, k);
+  const long long FS = P.FS;
+  const long long c = sidx(P, ci, cj, ck);
+  const double rho = U[c];
+  const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c], e = U[EN * FS + c];
+  const double bx = 0.5 * (U[BXF * FS + sidx(P, fmap(P, 0, i), cj, ck)] +
+                           U[BXF * FS + sidx(P, fmap(P, 0, i + 1), cj, ck)]);
+  const double by = 0.5 * (U[BYF * FS + sidx(P, ci, fmap(P, 1, j), ck)] +
+                           U[BYF * FS + sidx(P, ci, fmap(P, 1, j + 1), ck)]);
+  const double bz = 0.5 * (U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k))] +
+                           U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k + 1))]);
+  const double irho = inv_density<R>(rho);
+  const double kin = 0.5 * (mx * mx + my * my + mz * mz) * irho;
+  const double mag = 0.5 * (bx * bx + by * by + bz * bz);
+  const double p = (P.gamma - 1.0) * (e - kin - mag);
+  const R vx = (R)(mx * irho), vy = (R)(my * irho), vz = (R)(mz * irho);
+  if (store) {
+    const long long q = qidx(P, i, j, k), QS = P.QS;
+    W[q] = (R)rho;
+    W[WVX * QS + q] = vx;
+    W[WVY * QS + q] = vy;
+    W[WVZ * QS + q] = vz;
+    W[WP * QS + q] = (R)p;
+    W[WBX * QS + q] = (R)bx;
+    W[WBY * QS + q] = (R)by;
+    W[WBZ * QS + q] = (R)bz;
+  }
+  double lim = INFINITY;
+  if (interior) {
+    if (!(isfinite(rho) && isfinite(p) && isfinite(e))) {
+      atomicOr(P.err, ERR_NONFINITE);
+    } else if (!(rho > 0.0) || !(p > 0.0)) {
+      atomicOr(P.err, ERR_NEGATIVE);
+    }
+    const R v[3] = {vx, vy, vz};
+    const R b[3] = {(R)bx, (R)by, (R)bz};
+    const R bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!P.act[a]) continue;
+      R cf = fast_speed<R>((R)rho, (R)p, bb, b[a] * b[a], (R)P.gamma);
+      double t = P.d[a] / (double)(Ar<R>::abs_(v[a]) + cf);
+      lim = t < lim ? t : lim;
+    }
+  }
+  return lim;
+}
+
+// ------------------------------------------------------------- phase: flux ----
+// HLLD flux through the D-face at (i, j, k) (face index i-1/2 along D), with
+// donor-cell (ORDER 1) or kappa-scheme (ORDER 2) interface states; the normal field
+// is the face value; a face whose reconstructed rho or p is not positive falls back
+// to the donor-cell states.
+template <class R, int D, int ORDER>
+__device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restrict__ W,
+                                           const double* __restrict__ Ub, R* __restrict__ F,
+                                           int i, int j, int k) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  const long long q = qidx(P, i, j, k), QS = P.QS, st = qstride(P, D);
+  const int comp[7] = {WR, WVX + D, WVX + T1, WVX + T2, WP, WBX + T1, WBX + T2};
+  R wl[7], wr[7];
+  if (ORDER == 1) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      const R* w = W + comp[m] * QS + q;
+      wl[m] = w[-st];
+      wr[m] = w[0];
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      const R* w = W + comp[m] * QS + q;
+      kappa_face<R>(w[-2 * st], w[-st], w[0], w[st], wl[m], wr[m]);
+    }
+    if (!(wl[0] > R(0)) || !(wr[0] > R(0)) || !(wl[4] > R(0)) || !(wr[4] > R(0))) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        const R* w = W + comp[m] * QS + q;
+        wl[m] = w[-st];
+        wr[m] = w[0];
+      }
+    }
+  }
+  int c3[3] = {i, j, k};
+  int s3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s3[a] = (a == D) ? fmap(P, a, c3[a]) : cmap(P, a, c3[a]);
+  const R bn = (R)Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])];
+  R f[7];
+  hlld<R>(wl, wr, bn, (R)P.gamma, f);
+  F[q] = f[0];
+  F[(1 + D) * QS + q] = f[1];
+  F[(1 + T1) * QS + q] = f[2];
+  F[(1 + T2) * QS + q] = f[3];
+  F[4 * QS + q] = f[4];
+  F[5 * QS + q] = f[5];
+  F[6 * QS + q] = f[6];
+}
+
+// -------------------------------------------------------------- phase: EMF ----
+// Corner EMF E_C at edge (A-1/2, B-1/2), (A, B, C) cyclic (Eq. 9-11): mean of the four
+// face EMFs plus upwinded one-sided corrections, the upwind side given by the sign of
+// the Riemann mass flux (average when it is exactly zero); (db/8) * 2/db = 1/4.
+template <class R> __device__ __forceinline__ R upwind(R fr, R left, R right) {
+  return fr > R(0) ? left : (fr < R(0) ? right : R(0.5) * (left + right));
+}
+
+template <class R, int C>
+__device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restrict__ W,
+                                             R* __restrict__ E, int i, int j, int k) {
+  constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+  const long long q = qidx(P, i, j, k), QS = P.QS;
+  const R* FA = (const R*)P.F[A];
+  const R* FB = (const R*)P.F[B];
+  R e;
+  if (P.act[A] && !P.act[B]) {
+    e = -FA[5 * QS + q];
+  } else if (!P.act[A] && P.act[B]) {
+    e = FB[6 * QS + q];
+  } else if (!P.act[A] && !P.act[B]) {
+    return;
+  } else {
+    const long long sa = qstride(P, A), sb = qstride(P, B);
+    const long long oa = q - sa, ob = q - sb, oab = q - sa - sb;
+    const R Ea_b = -FA[5 * QS + q], Ea_bm = -FA[5 * QS + ob];
+    const R Eb_a = FB[6 * QS + q], Eb_am = FB[6 * QS + oa];
+    const R* vA = W + (WVX + A) * QS;
+    const R* vB = W + (WVX + B) * QS;
+    const R* bA = W + (WBX + A) * QS;
+    const R* bB = W + (WBX + B) * QS;
+    const R ec0 = -(vA[q] * bB[q] - vB[q] * bA[q]);
+    const R ec1 = -(vA[oa] * bB[oa] - vB[oa] * bA[oa]);
+    const R ec2 = -(vA[ob] * bB[ob] - vB[ob] * bA[ob]);
+    const R ec3 = -(vA[oab] * bB[oab] - vB[oab] * bA[oab]);
+    const R d_bq = upwind<R>(FA[q], ec1 - Eb_am, ec0 - Eb_a);
+    const R d_b3q = upwind<R>(FA[ob], Eb_am - ec3, Eb_a - ec2);
+    const R d_aq = upwind<R>(FB[q], ec2 - Ea_bm, ec0 - Ea_b);
+    const R d_a3q = upwind<R>(FB[oa], Ea_bm - ec3, Ea_b - ec1);
+    e = R(0.25) * (Ea_b + Ea_bm + Eb_a + Eb_am) + R(0.25) * (d_b3q - d_bq) +
+        R(0.25) * (d_a3q - d_aq);
+  }
+  E[C * QS + q] = e;
+}
+
+template <class R>
+__device__ __forceinline__ void emf_point(const PatchDev& P, const R* __restrict__ W,
+                                          R* __restrict__ E, int i, int j, int k) {
+  // E_x lives on x in [0, nx), E_y on y in [0, ny), E_z on z in [0, nz)
+  if (i < P.n[0]) corner_point<R, 0>(P, W, E, i, j, k);
+  if (j < P.n[1]) corner_point<R, 1>(P, W, E, i, j, k);
+  if (k < P.n[2]) corner_point<R, 2>(P, W, E, i, j, k);
+}
+
+// ----------------------------------------------------------- phase: update ----
+// Eq. 7 for the cell fields (plus h S of Eq. 2 at Usrc) and Eq. 8 (-curl E) for the
+// owned faces: out = base - h (div F) + h S;  B_a -= h [dE_C/db - dE_B/dc].
+template <class R>
+__device__ __forceinline__ void update_point(const PatchDev& P, const double* __restrict__ Ub,
+                                             const double* __restrict__ Us, double* __restrict__ Uo,
+                                             const R* __restrict__ E, R h,
+                                             const SourceDev& src, int i, int j, int k) {
+  const long long s = sidx(P, i, j, k), FS = P.FS;
+  const long long q = qidx(P, i, j, k), QS = P.QS;
+  if (i < P.n[0] && j < P.n[1] && k < P.n[2]) {
+    R div[5] = {R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (!P.act[d]) continue;
+      const R* Fd = (const R*)P.F[d];
+      const long long st = qstride(P, d);
+      const R idd = (R)P.inv_d[d];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) div[f] += (Fd[f * QS + q + st] - Fd[f * QS + q]) * idd;
+    }
+    R g[3];
+    grad_psi<R>(src, P.lo[0] + (i + 0.5) * P.d[0], P.lo[1] + (j + 0.5) * P.d[1],
+                P.lo[2] + (k + 0.5) * P.d[2], g);
+    const R rho = (R)Us[s];
+    const R sm[3] = {-rho * g[0], -rho * g[1], -rho * g[2]};
+    const R se = -((R)Us[MX * FS + s] * g[0] + (R)Us[MY * FS + s] * g[1] + (R)Us[MZ * FS + s] * g[2]);
+    Uo[s] = Ub[s] - (double)(h * div[0]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - (double)(h * div[1 + a]) + (double)(h * sm[a]);
+    Uo[EN * FS + s] = Ub[EN * FS + s] - (double)(h * div[4]) + (double)(h * se);
+  }
+  // faces
+  const int c3[3] = {i, j, k};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    if (!(c3[a] < P.nface[a] && c3[b] < P.n[b] && c3[c] < P.n[c])) continue;
+    R curl = R(0);
+    if (P.act[b]) curl += (E[c * QS + q + qstride(P, b)] - E[c * QS + q]) * (R)P.inv_d[b];
+    if (P.act[c]) curl -= (E[b * QS + q + qstride(P, c)] - E[b * QS + q]) * (R)P.inv_d[c];
+    Uo[(BXF + a) * FS + s] = Ub[(BXF + a) * FS + s] - (double)(h * curl);
+  }
+}
+
+// ------------------------------------------------------------ host format ----
+// Pack/unpack between the dense host format (see mhd.h) and the device layout.
+__device__ __forceinline__ void pack_point(const PatchDev& P, const double* __restrict__ U,
+                                           double* __restrict__ out, long long t) {
+  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+  if (t < 5 * nc) {
+    const int f = (int)(t / nc);
+    long long r = t - f * nc;
+    const int i = (int)(r % P.n[0]);
+    r /= P.n[0];
+    const int j = (int)(r % P.n[1]);
+    const int k = (int)(r / P.n[1]);
+    out[t] = U[f * P.FS + sidx(P, i, j, k)];
+    return;
+  }
+  long long r = t - 5 * nc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int e[3] = {P.n[0], P.n[1], P.n[2]};
+    e[a] += 1;
+    const long long cnt = (long long)e[0] * e[1] * e[2];
+    if (r < cnt) {
+      int c[3];
+      c[0] = (int)(r % e[0]);
+      long long rr = r / e[0];
+      c[1] = (int)(rr % e[1]);
+      c[2] = (int)(rr / e[1]);
+      c[a] = fmap(P, a, c[a]);
+      out[t] = U[(BXF + a) * P.FS + sidx(P, c[0], c[1], c[2])];
+      return;
+    }
+    r -= cnt;
+  }
+}
+
+__device__ __forceinline__ void unpack_point(const PatchDev& P, const double* __restrict__ in,
+                                             double* __restrict__ U, long long t) {
+  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+  if (t < 5 * nc) {
+    const int f = (int)(t / nc);
+    long long r = t - f * nc;
+    const int i = (int)(r % P.n[0]);
+    r /= P.n[0];
+    const int j = (int)(r % P.n[1]);
+    const int k = (int)(r / P.n[1]);
+    U[f * P.FS + sidx(P, i, j, k)] = in[t];
+    return;
+  }
+  long long r = t - 5 * nc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int e[3] = {P.n[0], P.n[1], P.n[2]};
+    e[a] += 1;
+    const long long cnt = (long long)e[0] * e[1] * e[2];
+    if (r < cnt) {
+      int c[3];
+      c[0] = (int)(r % e[0]);
+      long long rr = r / e[0];
+      c[1] = (int)(rr % e[1]);
+      c[2] = (int)(rr / e[1]);
+      U[(BXF + a) * P.FS + sidx(P, c[0], c[1], c[2])] = in[t];
+      return;
+    }
+    r -= cnt;
+  }
+}
+
+// ordered bits of a non-negative double (monotone as unsigned integers)
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+
+}  // namespace mhd

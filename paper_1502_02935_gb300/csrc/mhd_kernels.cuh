@@ -1,0 +1,223 @@
+// mhd_kernels.cuh -- CUDA kernels of the MHD step (one kernel per phase, grid over the
+// phase's index box) and the host-side launch sequence of one van Leer step.
+// Included by one translation unit per precision, which exports a Backend table.
+#pragma once
+#include "mhd_backend.h"
+#include "mhd_device.cuh"
+
+namespace mhd {
+
+constexpr int kBlock = 256;
+
+// index box [lo, lo + ext) per axis; the kernel grid is (ceil(ex*ey/kBlock), ez)
+struct Range {
+  int lo[3];
+  int ext[3];
+};
+
+__device__ __forceinline__ bool range_point(const Range& rg, int& i, int& j, int& k) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long plane = (long long)rg.ext[0] * rg.ext[1];
+  if (r >= plane) return false;
+  const int jj = (int)(r / rg.ext[0]);
+  i = rg.lo[0] + (int)(r - (long long)jj * rg.ext[0]);
+  j = rg.lo[1] + jj;
+  k = rg.lo[2] + (int)blockIdx.y;
+  return true;
+}
+
+__device__ __forceinline__ void block_min_atomic(double v, unsigned long long* slot) {
+  // warp-shuffle minimum, then one ordered-bits atomicMin per block (deterministic)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  __shared__ double red[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w < v ? w : v;
+    }
+    if (lane == 0 && v < INFINITY) atomicMin(slot, dbits(v));
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_prim(PatchDev P, const double* __restrict__ U, Range rg,
+                                                 int store, int want_cfl) {
+  int i, j, k;
+  double lim = INFINITY;
+  if (range_point(rg, i, j, k)) {
+    const bool interior = want_cfl && i >= 0 && i < P.n[0] && j >= 0 && j < P.n[1] && k >= 0 &&
+                          k < P.n[2];
+    lim = prim_point<R>(P, U, (R*)P.W, i, j, k, store != 0, interior);
+  }
+  if (want_cfl) block_min_atomic(lim, P.cfl_min);
+}
+
+template <class R, int D, int ORDER>
+__global__ void __launch_bounds__(kBlock) k_flux(PatchDev P, const double* __restrict__ Ub, Range rg) {
+  int i, j, k;
+  if (!range_point(rg, i, j, k)) return;
+  flux_point<R, D, ORDER>(P, (const R*)P.W, Ub, (R*)P.F[D], i, j, k);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_emf(PatchDev P, Range rg) {
+  int i, j, k;
+  if (!range_point(rg, i, j, k)) return;
+  emf_point<R>(P, (const R*)P.W, (R*)P.E, i, j, k);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_update(PatchDev P, const double* __restrict__ Ub,
+                                                   const double* __restrict__ Us,
+                                                   double* __restrict__ Uo, Range rg, StageArgs a) {
+  const double dt = a.dt_host > 0.0 ? a.dt_host : a.cfl * __longlong_as_double((long long)*P.cfl_min);
+  const R h = (R)(a.stage == 0 ? 0.5 * dt : dt);
+  if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *P.dt_used = dt;
+  int i, j, k;
+  if (!range_point(rg, i, j, k)) return;
+  update_point<R>(P, Ub, Us, Uo, (const R*)P.E, h, a.src, i, j, k);
+}
+
+template <class R>
+__global__ void k_hlld(int n, const double* __restrict__ wl, const double* __restrict__ wr,
+                       const double* __restrict__ bn, double gam, double* __restrict__ flux) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  R a[7], b[7], f[7];
+  const int src[7] = {0, 1, 2, 3, 4, 6, 7};
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    a[m] = (R)wl[8 * q + src[m]];
+    b[m] = (R)wr[8 * q + src[m]];
+  }
+  hlld<R>(a, b, (R)bn[q], (R)gam, f);
+#pragma unroll
+  for (int m = 0; m < 7; ++m) flux[8 * q + src[m]] = (double)f[m];
+  flux[8 * q + 5] = 0.0;
+}
+
+// ------------------------------------------------------------- host side ----
+static inline dim3 grid_of(const Range& rg) {
+  const long long plane = (long long)rg.ext[0] * rg.ext[1];
+  return dim3((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)rg.ext[2], 1);
+}
+
+static inline Range prim_range(const PatchDev& P) {
+  Range r;
+  for (int a = 0; a < 3; ++a) {
+    r.lo[a] = -P.g2[a];
+    r.ext[a] = P.n[a] + 2 * P.g2[a];
+  }
+  return r;
+}
+
+static inline Range interior_range(const PatchDev& P) {
+  Range r;
+  for (int a = 0; a < 3; ++a) {
+    r.lo[a] = 0;
+    r.ext[a] = P.n[a];
+  }
+  return r;
+}
+
+static inline Range flux_range(const PatchDev& P, int d) {
+  Range r;
+  for (int a = 0; a < 3; ++a) {
+    if (a == d) {
+      r.lo[a] = 0;
+      r.ext[a] = P.n[a] + 1;
+    } else if (P.act[a]) {
+      r.lo[a] = -1;
+      r.ext[a] = P.n[a] + 2;
+    } else {
+      r.lo[a] = 0;
+      r.ext[a] = 1;
+    }
+  }
+  return r;
+}
+
+static inline Range edge_range(const PatchDev& P) {
+  Range r;
+  for (int a = 0; a < 3; ++a) {
+    r.lo[a] = 0;
+    r.ext[a] = P.act[a] ? P.n[a] + 1 : 1;
+  }
+  return r;
+}
+
+template <class R>
+static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, long long* launches,
+                       ProfRec* prof) {
+  const double* Usrc = a.stage == 0 ? P.Un : P.Uh;   // state the fluxes are built from
+  double* Uout = a.stage == 0 ? P.Uh : P.Un;         // corrector updates U^n in place
+  const Range pr = prim_range(P);
+  {
+    ProfScope ps(prof, KC_PRIM, s);
+    k_prim<R><<<grid_of(pr), kBlock, 0, s>>>(P, Usrc, pr, 1, a.stage == 0 ? 1 : 0);
+  }
+  int nl = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (!P.act[d]) continue;
+    const Range fr = flux_range(P, d);
+    ProfScope ps(prof, (a.stage == 0 ? KC_FLUX1 : KC_FLUX2) + d, s);
+    if (a.stage == 0) {
+      if (d == 0) k_flux<R, 0, 1><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+      if (d == 1) k_flux<R, 1, 1><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+      if (d == 2) k_flux<R, 2, 1><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+    } else {
+      if (d == 0) k_flux<R, 0, 2><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+      if (d == 1) k_flux<R, 1, 2><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+      if (d == 2) k_flux<R, 2, 2><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+    }
+    ++nl;
+  }
+  const Range er = edge_range(P);
+  {
+    ProfScope ps(prof, KC_EMF, s);
+    k_emf<R><<<grid_of(er), kBlock, 0, s>>>(P, er);
+  }
+  {
+    ProfScope ps(prof, KC_UPDATE, s);
+    k_update<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, Uout, er, a);
+  }
+  nl += 2;
+  *launches += nl;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class R>
+static int issue_cfl(const PatchDev& P, cudaStream_t s, long long* launches) {
+  const Range r = interior_range(P);
+  k_prim<R><<<grid_of(r), kBlock, 0, s>>>(P, P.Un, r, 0, 1);
+  *launches += 1;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class R>
+static int issue_hlld(int n, const double* wl, const double* wr, const double* bn, double gam,
+                      double* flux, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_hlld<R><<<(n + 127) / 128, 128, 0, s>>>(n, wl, wr, bn, gam, flux);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class R> Backend make_backend() {
+  Backend b;
+  b.scratch_elem = sizeof(R);
+  b.stage = &issue_stage<R>;
+  b.cfl = &issue_cfl<R>;
+  b.hlld = &issue_hlld<R>;
+  return b;
+}
+
+}  // namespace mhd

@@ -118,6 +118,56 @@ def faces_from_Az(g: Geom, Az):
     return Bx, By, Bz
 
 
+def faces_from_A(g: Geom, Ax, Ay, Az):
+    """Face fields of B = curl A with A sampled on cell edges: A_x on (x_i, y_{j-1/2},
+    z_{k-1/2}), A_y on (x_{i-1/2}, y_j, z_{k-1/2}), A_z on (x_{i-1/2}, y_{j-1/2}, z_k).
+    Each callable takes broadcastable (x, y, z) arrays.  Exact zero discrete divergence."""
+    xc, yc, zc = g.centres()
+    xf, yf, zf = g.faces()
+    # A_z on (nz, ny+1, nx+1), A_y on (nz+1, ny, nx+1), A_x on (nz+1, ny+1, nx)
+    az = np.broadcast_to(Az(xf[None, None, :], yf[None, :, None], zc[:, None, None]), (g.nz, g.ny + 1, g.nx + 1))
+    ay = np.broadcast_to(Ay(xf[None, None, :], yc[None, :, None], zf[:, None, None]), (g.nz + 1, g.ny, g.nx + 1))
+    ax = np.broadcast_to(Ax(xc[None, None, :], yf[None, :, None], zf[:, None, None]), (g.nz + 1, g.ny + 1, g.nx))
+    Bx = (az[:, 1:, :] - az[:, :-1, :]) / g.dy - (ay[1:, :, :] - ay[:-1, :, :]) / g.dz
+    By = (ax[1:, :, :] - ax[:-1, :, :]) / g.dz - (az[:, :, 1:] - az[:, :, :-1]) / g.dx
+    Bz = (ay[:, :, 1:] - ay[:, :, :-1]) / g.dx - (ax[:, 1:, :] - ax[:, :-1, :]) / g.dy
+    return np.ascontiguousarray(Bx), np.ascontiguousarray(By), np.ascontiguousarray(Bz)
+
+
+def smooth_random(g: Geom, seed: int, bamp: float = 0.5) -> State:
+    """Smooth random positive state (a few low Fourier modes per field) with a field
+    from a random smooth vector potential; used for parity on odd-sized boxes with any
+    boundary conditions."""
+    rng = np.random.default_rng(seed)
+    L = (g.nx * g.dx, g.ny * g.dy, g.nz * g.dz)
+
+    def fld(base, amp):
+        c = rng.normal(size=(4, 3))
+        ph = rng.uniform(0, 2 * np.pi, 4)
+
+        def f(x, y, z):
+            out = base
+            for m in range(4):
+                out = out + amp * c[m, 0] * np.sin(2 * np.pi * (x - g.x0) / L[0] * (1 + m % 2) + ph[m]) \
+                    * np.cos(2 * np.pi * (y - g.y0) / L[1] * (m // 2) + c[m, 1]) \
+                    * np.cos(2 * np.pi * (z - g.z0) / L[2] * (m % 3) + c[m, 2])
+            return out
+        return f
+
+    x, y, z = g.centres()
+    X, Y, Z = x[None, None, :], y[None, :, None], z[:, None, None]
+    rho = fld(1.0, 0.08)(X, Y, Z)
+    p = fld(0.8, 0.06)(X, Y, Z)
+    vx, vy, vz = (fld(0.0, 0.2)(X, Y, Z) for _ in range(3))
+    A = [fld(0.0, bamp * 0.1) for _ in range(3)]
+    B0 = rng.normal(size=3) * bamp
+    Ax = lambda xx, yy, zz: A[0](xx, yy, zz) + B0[1] * zz
+    Ay = lambda xx, yy, zz: A[1](xx, yy, zz) + B0[2] * xx
+    Az = lambda xx, yy, zz: A[2](xx, yy, zz) + B0[0] * yy
+    Bx, By, Bz = faces_from_A(g, Ax, Ay, Az)
+    return state_from_prim(g, rho, vx, vy, vz, p, Bx, By, Bz)
+
+
 # ---------------------------------------------------------------- workloads --
 
 def brio_wu(n: int = 800, axis: int = 0, transverse: int = 1) -> State:

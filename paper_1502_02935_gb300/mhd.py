@@ -1,0 +1,239 @@
+"""ctypes binding of libmhd.so (include/mhd.h).  Argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; if the library is
+missing or cannot load, every entry point raises (there is no fallback).  PyTorch
+is used only to hand device buffers and streams to the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .inputs import Geom, State
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhd.so")
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+FLAG_GRAPH = 1
+FLAG_PERSISTENT = 2
+POT_NONE, POT_GAUSS_X, POT_LOG_DISC = 0, 1, 2
+
+ERRORS = {0: "MHD_OK", -1: "MHD_ERR_ARG", -2: "MHD_ERR_CUDA", -3: "MHD_ERR_NONFINITE",
+          -4: "MHD_ERR_NEGATIVE", -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE", -7: "MHD_ERR_NOMEM"}
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PatchDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("bc", C.c_int * 6), ("gamma", C.c_double)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n_patches", C.c_int), ("patches", C.POINTER(PatchDesc)), ("precision", C.c_int),
+                ("cfl", C.c_double), ("flags", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class SourceDesc(C.Structure):
+    _fields_ = [("potential", C.c_int), ("psi0", C.c_double), ("xc", C.c_double), ("xw", C.c_double),
+                ("v0", C.c_double), ("rc", C.c_double)]
+
+
+class Metrics(C.Structure):
+    _fields_ = [("dt_last", C.c_double), ("sums", C.c_double * 5), ("max_divb", C.c_double),
+                ("error_word", C.c_int)]
+
+
+_lib = None
+
+EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cfl_dt_patches",
+           "mhd_get_state", "mhd_set_state", "mhd_sync", "mhd_get_metrics", "mhd_launch_count",
+           "mhd_last_error", "mhd_destroy", "mhd_riemann_hlld", "mhd_set_profiling", "mhd_get_profile"]
+
+
+def lib():
+    """Load libmhd.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from . import build
+        build.build()
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    L.mhd_init_grid.argtypes = [C.POINTER(vp), C.POINTER(GridDesc), C.POINTER(vp), C.POINTER(vp), ip]
+    L.mhd_set_sources.argtypes = [vp, C.POINTER(SourceDesc)]
+    L.mhd_step.argtypes = [vp, C.c_double]
+    L.mhd_cfl_dt.argtypes = [vp, dp]
+    L.mhd_cfl_dt_patches.argtypes = [vp, dp]
+    L.mhd_get_state.argtypes = [vp, ip, vp, vp, ip]
+    L.mhd_set_state.argtypes = [vp, ip, vp, vp, ip]
+    L.mhd_sync.argtypes = [vp]
+    L.mhd_get_metrics.argtypes = [vp, C.POINTER(Metrics)]
+    L.mhd_launch_count.argtypes = [vp]
+    L.mhd_launch_count.restype = C.c_longlong
+    L.mhd_last_error.argtypes = [vp]
+    L.mhd_last_error.restype = C.c_char_p
+    L.mhd_destroy.argtypes = [vp]
+    L.mhd_destroy.restype = None
+    L.mhd_riemann_hlld.argtypes = [ip, vp, vp, vp, C.c_double, ip, vp, vp]
+    L.mhd_set_profiling.argtypes = [vp, ip]
+    L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
+    for name in EXPORTS:
+        if name not in ("mhd_destroy", "mhd_last_error", "mhd_launch_count"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def patch_desc(g: Geom) -> PatchDesc:
+    d = PatchDesc()
+    d.nx, d.ny, d.nz = g.nx, g.ny, g.nz
+    d.x0, d.y0, d.z0 = g.x0, g.y0, g.z0
+    d.dx, d.dy, d.dz = g.dx, g.dy, g.dz
+    for a in range(6):
+        d.bc[a] = int(g.bc[a])
+    d.gamma = g.gamma
+    return d
+
+
+def _prec(p) -> int:
+    if p in (PREC_FP64, "fp64", "f64"):
+        return PREC_FP64
+    if p in (PREC_MIXED, "mixed", "fp32"):
+        return PREC_MIXED
+    raise ValueError(f"unknown precision {p!r}")
+
+
+class Grid:
+    """A set of independent patches advanced together on one GPU."""
+
+    def __init__(self, states, precision="mixed", cfl: float = 0.4, flags: int = 0, stream=None):
+        if isinstance(states, State):
+            states = [states]
+        self.L = lib()
+        self.geoms = [s.geom for s in states]
+        self.np = len(states)
+        descs = (PatchDesc * self.np)(*[patch_desc(s.geom) for s in states])
+        self._descs = descs
+        gd = GridDesc(self.np, descs, _prec(precision), float(cfl), int(flags),
+                      C.c_void_p(stream if isinstance(stream, int) else (stream or 0)))
+        hostU = [np.ascontiguousarray(s.U, dtype=np.float64) for s in states]
+        hostB = [np.ascontiguousarray(s.faces_flat(), dtype=np.float64) for s in states]
+        Up = (C.c_void_p * self.np)(*[a.ctypes.data for a in hostU])
+        Bp = (C.c_void_p * self.np)(*[a.ctypes.data for a in hostB])
+        h = C.c_void_p()
+        rc = self.L.mhd_init_grid(C.byref(h), C.byref(gd), Up, Bp, 0)
+        if rc != 0:
+            raise MHDError(rc, "mhd_init_grid")
+        self.h = h
+
+    # ---------------------------------------------------------------- calls --
+    def _check(self, rc, what):
+        if rc != 0:
+            raise MHDError(rc, f"{what}: {self.L.mhd_last_error(self.h).decode()}")
+
+    def set_sources(self, potential=POT_NONE, psi0=0.0, xc=0.0, xw=1.0, v0=0.0, rc=0.0):
+        s = SourceDesc(int(potential), psi0, xc, xw, v0, rc)
+        self._check(self.L.mhd_set_sources(self.h, C.byref(s)), "mhd_set_sources")
+
+    def step(self, dt: float = -1.0):
+        self._check(self.L.mhd_step(self.h, float(dt)), "mhd_step")
+
+    def cfl_dt(self) -> float:
+        v = C.c_double()
+        self._check(self.L.mhd_cfl_dt(self.h, C.byref(v)), "mhd_cfl_dt")
+        return v.value
+
+    def cfl_dt_patches(self) -> np.ndarray:
+        out = np.zeros(self.np)
+        self._check(self.L.mhd_cfl_dt_patches(self.h, out.ctypes.data_as(C.POINTER(C.c_double))),
+                    "mhd_cfl_dt_patches")
+        return out
+
+    def get_state(self, patch: int = 0) -> State:
+        g = self.geoms[patch]
+        U = np.empty((5, g.nz, g.ny, g.nx))
+        nb = (g.nx + 1) * g.ny * g.nz + g.nx * (g.ny + 1) * g.nz + g.nx * g.ny * (g.nz + 1)
+        B = np.empty(nb)
+        self._check(self.L.mhd_get_state(self.h, patch, U.ctypes.data, B.ctypes.data, 0), "mhd_get_state")
+        n1 = (g.nx + 1) * g.ny * g.nz
+        n2 = g.nx * (g.ny + 1) * g.nz
+        return State(g, U, B[:n1].reshape(g.nz, g.ny, g.nx + 1).copy(),
+                     B[n1:n1 + n2].reshape(g.nz, g.ny + 1, g.nx).copy(),
+                     B[n1 + n2:].reshape(g.nz + 1, g.ny, g.nx).copy())
+
+    def get_state_ptr(self, patch: int, U_ptr: int, B_ptr: int, on_device: bool):
+        self._check(self.L.mhd_get_state(self.h, patch, U_ptr, B_ptr, int(on_device)), "mhd_get_state")
+
+    def set_state(self, patch: int, st: State):
+        U = np.ascontiguousarray(st.U, dtype=np.float64)
+        B = np.ascontiguousarray(st.faces_flat(), dtype=np.float64)
+        self._check(self.L.mhd_set_state(self.h, patch, U.ctypes.data, B.ctypes.data, 0), "mhd_set_state")
+
+    def set_state_ptr(self, patch: int, U_ptr: int, B_ptr: int, on_device: bool):
+        self._check(self.L.mhd_set_state(self.h, patch, U_ptr, B_ptr, int(on_device)), "mhd_set_state")
+
+    def sync(self):
+        self._check(self.L.mhd_sync(self.h), "mhd_sync")
+
+    def sync_status(self) -> int:
+        return int(self.L.mhd_sync(self.h))
+
+    def metrics(self) -> dict:
+        m = Metrics()
+        self._check(self.L.mhd_get_metrics(self.h, C.byref(m)), "mhd_get_metrics")
+        return {"dt_last": m.dt_last, "sums": list(m.sums), "max_divb": m.max_divb, "error_word": m.error_word}
+
+    KERNEL_CLASSES = ["recovery", "flux1_x", "flux1_y", "flux1_z", "flux2_x", "flux2_y", "flux2_z",
+                      "emf", "update", "cfl"]
+
+    def set_profiling(self, on: bool):
+        self._check(self.L.mhd_set_profiling(self.h, int(on)), "mhd_set_profiling")
+
+    def profile(self) -> dict:
+        n = len(self.KERNEL_CLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_longlong * n)()
+        self._check(self.L.mhd_get_profile(self.h, ms, cnt, n), "mhd_get_profile")
+        return {k: (ms[i], int(cnt[i])) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def launch_count(self) -> int:
+        return int(self.L.mhd_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def riemann_hlld(wl, wr, bn, gamma: float, precision="fp64") -> np.ndarray:
+    """HLLD fluxes of n interfaces computed on the GPU (see mhd_riemann_hlld)."""
+    import torch
+    wl = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(wl), dtype=np.float64)).cuda()
+    wr = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(wr), dtype=np.float64)).cuda()
+    bn = torch.as_tensor(np.ascontiguousarray(np.atleast_1d(bn), dtype=np.float64)).cuda()
+    n = wl.shape[0]
+    out = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib().mhd_riemann_hlld(n, wl.data_ptr(), wr.data_ptr(), bn.data_ptr(), float(gamma),
+                                _prec(precision), out.data_ptr(), stream)
+    if rc != 0:
+        raise MHDError(rc, "mhd_riemann_hlld")
+    return out.cpu().numpy()

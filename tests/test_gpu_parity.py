@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances
+  FP64 path : |gpu - oracle| <= 1e-12 * max(|oracle|, 1e-3 * max|field|) per value, per
+              step (the two evaluate the same formulas in a different operation order;
+              rounding differences are ~1e-16 per operation).
+  mixed path: FP32 bulk arithmetic with FP64 pressure recovery and accumulation.  One
+              step moves U by h * div F with h * |div F| ~ CFL * |U|, so FP32 rounding of
+              the increments gives ~1e-7 relative; the stated bound is MIXED_TOL below,
+              on the same scale.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02935_gb300 import inputs, mhd
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 2e-5
+
+
+def assert_close(got: inputs.State, ref: inputs.State, tol: float, what: str = ""):
+    fields = [("U%d" % f, got.U[f], ref.U[f]) for f in range(5)]
+    fields += [("Bx", got.Bx, ref.Bx), ("By", got.By, ref.By), ("Bz", got.Bz, ref.Bz)]
+    for name, a, b in fields:
+        scale = np.maximum(np.abs(b), 1e-3 * max(np.max(np.abs(b)), 1e-300))
+        err = np.max(np.abs(a - b) / scale)
+        assert err <= tol, f"{what} {name}: max scaled error {err:.3e} > {tol:.1e}"
+
+
+def max_scaled_errors(got, ref):
+    out = {}
+    fields = [("rho", 0), ("mx", 1), ("my", 2), ("mz", 3), ("E", 4)]
+    for name, f in fields:
+        b = ref.U[f]
+        scale = np.maximum(np.abs(b), 1e-3 * max(np.max(np.abs(b)), 1e-300))
+        out[name] = float(np.max(np.abs(got.U[f] - b) / scale))
+    for name in ("Bx", "By", "Bz"):
+        a, b = getattr(got, name), getattr(ref, name)
+        scale = np.maximum(np.abs(b), 1e-3 * max(np.max(np.abs(b)), 1e-300))
+        out[name] = float(np.max(np.abs(a - b) / scale))
+    return out
+
+
+def _geom(n, bc, d=(0.1, 0.11, 0.13), lo=(0.0, 0.0, 0.0), gamma=5.0 / 3.0):
+    return inputs.Geom(n[0], n[1], n[2], lo[0], lo[1], lo[2], d[0], d[1], d[2], bc, gamma)
+
+
+CASES = {
+    "brio_wu_800": lambda: (inputs.brio_wu(800), None),
+    "ryu_jones_400": lambda: (inputs.ryu_jones(400), None),
+    "sod_300_hydro": lambda: (inputs.sod(300), None),
+    "orszag_tang_64x48": lambda: (inputs.orszag_tang(64, 48), None),
+    "turbulence_37x29x23": lambda: (inputs.turbulence((37, 29, 23), seed=5), None),
+    "blast_24": lambda: (inputs.blast(24, (0.3, 0.6, 0.45), (0.6, 0.0, 0.8)), None),
+    "outflow_17x9x5": lambda: (inputs.smooth_random(_geom((17, 9, 5), (1,) * 6), 3), None),
+    "mixed_bc_13x11x6": lambda: (inputs.smooth_random(_geom((13, 11, 6), (1, 1, 0, 0, 1, 1)), 4), None),
+    "disc_gravity_20x18x8": lambda: (
+        inputs.smooth_random(_geom((20, 18, 8), (1,) * 6, d=(0.5, 0.5, 0.25), lo=(-5.0, -4.5, -1.0)), 9),
+        dict(potential=2, v0=1.3, rc=0.5)),
+    "gauss_well_1d_200": lambda: (
+        inputs.smooth_random(_geom((200, 1, 1), (1, 1, 0, 0, 0, 0), d=(0.005, 1.0, 1.0), lo=(-0.5, 0, 0)), 2, 0.0),
+        dict(potential=1, psi0=5.0, xc=0.0, xw=0.1)),
+}
+
+
+def _run_pair(st, src, precision, nsteps, cfl=0.4):
+    g = mhd.Grid(st, precision=precision, cfl=cfl)
+    if src:
+        g.set_sources(**src)
+    ref = st
+    dts = []
+    for _ in range(nsteps):
+        dt = oracle.cfl_dt(ref, cfl)
+        dts.append(dt)
+        g.step(dt)
+        ref = oracle.step(ref, dt, source=src)
+    got = g.get_state(0)
+    g.close()
+    return got, ref, dts
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_one_step_parity(case):
+    st, src = CASES[case]()
+    got, ref, _ = _run_pair(st, src, "fp64", 1)
+    assert_close(got, ref, FP64_TOL, case)
+
+
+@pytest.mark.parametrize("case", ["turbulence_37x29x23", "orszag_tang_64x48", "outflow_17x9x5", "brio_wu_800"])
+def test_fp64_multi_step_parity(case):
+    st, src = CASES[case]()
+    got, ref, _ = _run_pair(st, src, "fp64", 5)
+    assert_close(got, ref, 5 * FP64_TOL, case)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mixed_one_step_parity(case):
+    st, src = CASES[case]()
+    got, ref, _ = _run_pair(st, src, "mixed", 1)
+    assert_close(got, ref, MIXED_TOL, case)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("mixed", 1e-6)])
+def test_cfl_dt_matches_oracle(precision, tol):
+    for case in ("turbulence_37x29x23", "brio_wu_800", "outflow_17x9x5"):
+        st, _ = CASES[case]()
+        g = mhd.Grid(st, precision=precision, cfl=0.4)
+        a = g.cfl_dt()
+        g.close()
+        b = oracle.cfl_dt(st, 0.4)
+        assert abs(a - b) <= tol * b, (case, a, b)
+
+
+def test_device_cfl_step_equals_host_dt_step():
+    """mhd_step(dt <= 0) uses the device CFL limit; it must equal stepping with the
+    dt that mhd_cfl_dt reports."""
+    st = inputs.turbulence((24, 20, 16), seed=3)
+    a = mhd.Grid(st, precision="fp64", cfl=0.4)
+    b = mhd.Grid(st, precision="fp64", cfl=0.4)
+    for _ in range(3):
+        a.step(-1.0)
+        b.step(b.cfl_dt())
+    sa, sb = a.get_state(0), b.get_state(0)
+    assert np.array_equal(sa.U, sb.U) and np.array_equal(sa.Bx, sb.Bx)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_is_bitwise_equal(precision):
+    st = inputs.turbulence((20, 18, 14), seed=8)
+    a = mhd.Grid(st, precision=precision, cfl=0.4, flags=mhd.FLAG_GRAPH)
+    b = mhd.Grid(st, precision=precision, cfl=0.4)
+    for _ in range(4):
+        a.step(-1.0)
+        b.step(-1.0)
+    sa, sb = a.get_state(0), b.get_state(0)
+    for f in ("U", "Bx", "By", "Bz"):
+        assert np.array_equal(getattr(sa, f), getattr(sb, f))
+    assert a.launch_count() > 0
+    a.close()
+    b.close()
+
+
+def test_conservation_and_divb_on_device():
+    """Properties that hold at any size: on a periodic box the FP64 path conserves the
+    totals to roundoff and keeps div B = 0 to roundoff (CT)."""
+    st = inputs.turbulence((48, 40, 36), seed=12)
+    g = mhd.Grid(st, precision="fp64", cfl=0.4)
+    m0 = g.metrics()
+    for _ in range(10):
+        g.step(-1.0)
+    m1 = g.metrics()
+    absU = np.abs(st.U).reshape(5, -1).sum(axis=1)
+    for f in range(5):
+        assert abs(m1["sums"][f] - m0["sums"][f]) <= 2e-13 * absU[f]
+    assert m1["max_divb"] <= 1e-13 * 0.1 * 10
+    g.close()
+
+
+def _subbox(st: inputs.State, c, h):
+    """(2h+1)^3 window of a periodic state centred on cell c, as an outflow patch."""
+    g = st.geom
+    n = (g.nx, g.ny, g.nz)
+    idx = [np.arange(c[a] - h, c[a] + h + 1) % n[a] for a in range(3)]
+    fidx = [np.arange(c[a] - h, c[a] + h + 2) % n[a] for a in range(3)]
+    U = st.U[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+    Bx = st.Bx[idx[2]][:, idx[1]][:, :, fidx[0]]
+    By = st.By[idx[2]][:, fidx[1]][:, :, idx[0]]
+    Bz = st.Bz[fidx[2]][:, idx[1]][:, :, idx[0]]
+    gs = inputs.Geom(2 * h + 1, 2 * h + 1, 2 * h + 1, 0.0, 0.0, 0.0, g.dx, g.dy, g.dz, (1,) * 6, g.gamma)
+    return inputs.State(gs, np.ascontiguousarray(U), np.ascontiguousarray(Bx), np.ascontiguousarray(By),
+                        np.ascontiguousarray(Bz))
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_TOL), ("fp64", FP64_TOL)])
+def test_full_size_turbulence_sampled_parity(precision, tol):
+    """The 256^3 turbulent box in the configuration bench.py times: one step on the GPU,
+    compared at sampled cells with the oracle run on a 11^3 window around each sample
+    (a cell after one step depends only on cells within 3 of it)."""
+    st = inputs.turbulence(256, seed=1502)
+    g = mhd.Grid(st, precision=precision, cfl=0.4, flags=mhd.FLAG_GRAPH)
+    dt = g.cfl_dt()
+    g.step(dt)
+    got = g.get_state(0)
+    g.close()
+    rng = np.random.default_rng(99)
+    h = 5
+    samples = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(12)] + [(0, 0, 0), (255, 255, 255)]
+    scale = np.max(np.abs(st.U).reshape(5, -1), axis=1)
+    for c in samples:
+        sub = _subbox(st, c, h)
+        out = oracle.step(sub, dt)
+        for f in range(5):
+            a = got.U[f, c[2], c[1], c[0]]
+            b = out.U[f, h, h, h]
+            assert abs(a - b) <= tol * max(abs(b), 1e-3 * scale[f]), (c, f, a, b)
+        for name, fi in (("Bx", (c[2], c[1], c[0])), ("By", (c[2], c[1], c[0])), ("Bz", (c[2], c[1], c[0]))):
+            a = getattr(got, name)[fi]
+            b = getattr(out, name)[h, h, h]
+            assert abs(a - b) <= tol * max(abs(b), 1e-3 * 0.1), (c, name, a, b)
+
+
+def test_hlld_device_matches_oracle():
+    rng = np.random.default_rng(4)
+    n = 4000
+    wl = np.zeros((n, 8))
+    wr = np.zeros((n, 8))
+    for w in (wl, wr):
+        w[:, 0] = rng.uniform(0.1, 3.0, n)
+        w[:, 1:4] = rng.normal(0, 1.5, (n, 3))
+        w[:, 4] = rng.uniform(0.01, 3.0, n)
+        w[:, 6:8] = rng.normal(0, 1.0, (n, 2))
+    bn = rng.normal(0, 1.0, n)
+    bn[:200] = 0.0                     # hydro limit
+    wl[200:400, 6:8] = 0.0             # degenerate: Bt = 0 with strong Bn
+    wr[200:400, 6:8] = 0.0
+    bn[200:400] = 3.0
+    wr[400:600] = wl[400:600]          # equal states
+    wl[600:700, 1] = 20.0              # supersonic both ways
+    wr[600:700, 1] = 20.0
+    ref = oracle.hlld(wl, wr, bn, 5.0 / 3.0)
+    got = mhd.riemann_hlld(wl, wr, bn, 5.0 / 3.0, "fp64")
+    scale = np.max(np.abs(ref), axis=1, keepdims=True) + 1e-3
+    assert np.max(np.abs(got - ref) / scale) <= 1e-13
+    got32 = mhd.riemann_hlld(wl, wr, bn, 5.0 / 3.0, "mixed")
+    assert np.max(np.abs(got32 - ref) / scale) <= 2e-5
+
+
+def test_nonfinite_and_negative_inputs_are_reported():
+    """Fault paths on the host side: a NaN or a negative density in the input is flagged
+    by the device error word and returned as a status (no trap, no hang)."""
+    st = inputs.turbulence((16, 16, 16), seed=1)
+    bad = st.copy()
+    bad.U[0, 3, 4, 5] = float("nan")
+    g = mhd.Grid(bad, precision="mixed")
+    g.step(1e-4)
+    assert g.sync_status() == -3
+    g.close()
+    bad = st.copy()
+    bad.U[0, 3, 4, 5] = -1.0
+    g = mhd.Grid(bad, precision="fp64")
+    g.step(1e-4)
+    assert g.sync_status() == -4
+    g.close()
+    with pytest.raises(mhd.MHDError):
+        mhd.Grid(inputs.State(inputs.Geom(0, 4, 4), np.zeros((5, 4, 4, 0)), np.zeros((4, 4, 1)),
+                              np.zeros((4, 5, 0)), np.zeros((5, 4, 0))))
