@@ -199,6 +199,8 @@ static void frame_flux(const double* w, double bn, double gam, double* f) {
   f[7] = b2 * un - bn * v2;
 }
 
+/* flux[5] (the normal-field flux, identically zero) returns the face's mass-flux
+ * scale max(rho_L, rho_R) * max(|S_L|, |S_R|), used by the corner-EMF upwinding. */
 static void hlld(const double* wl, const double* wr, double bn, double gam, double* flux) {
   double UL[8], UR[8], FL[8], FR[8];
   frame_cons(wl, bn, gam, UL);
@@ -216,12 +218,15 @@ static void hlld(const double* wl, const double* wr, double bn, double gam, doub
   double sl = (ul < ur ? ul : ur) - cmax;
   double sr = (ul > ur ? ul : ur) + cmax;
 
+  double sigma = (rl > rr ? rl : rr) * (fabs(sl) > fabs(sr) ? fabs(sl) : fabs(sr));
   if (sl > 0.0) {
     memcpy(flux, FL, sizeof FL);
+    flux[5] = sigma;
     return;
   }
   if (sr < 0.0) {
     memcpy(flux, FR, sizeof FR);
+    flux[5] = sigma;
     return;
   }
 
@@ -314,12 +319,15 @@ static void hlld(const double* wl, const double* wr, double bn, double gam, doub
   } else {
     for (int m = 0; m < 8; ++m) flux[m] = FR[m] + sr * (US[1][m] - UR[m]);
   }
-  flux[5] = 0.0;
+  flux[5] = sigma;
 }
 
 void orc_hlld_batch(int n, const double* wl, const double* wr, const double* bn,
                     double gamma, double* flux) {
-  for (int q = 0; q < n; ++q) hlld(wl + 8 * q, wr + 8 * q, bn[q], gamma, flux + 8 * q);
+  for (int q = 0; q < n; ++q) {
+    hlld(wl + 8 * q, wr + 8 * q, bn[q], gamma, flux + 8 * q);
+    flux[8 * q + 5] = 0.0;
+  }
 }
 
 /* --------------------------------------------------------- reconstruction ----
@@ -420,7 +428,7 @@ static void compute_fluxes(const grid* G, int d, int order, double* const W[NF],
         Fl[MX + t1][o] = f[2];
         Fl[MX + t2][o] = f[3];
         Fl[EN][o] = f[4];
-        Fl[BXF + d][o] = 0.0;
+        Fl[BXF + d][o] = f[5]; /* mass-flux scale (the normal-field flux itself is zero) */
         Fl[BXF + t1][o] = f[6];
         Fl[BXF + t2][o] = f[7];
       }
@@ -436,11 +444,16 @@ static void compute_fluxes(const grid* G, int d, int order, double* const W[NF],
  * Readings: the four face points are the ones that surround the edge; the sign of
  * the corrections is the one for which a flow that varies along one axis only
  * gives back the face EMF exactly; the upwind side in Eq. 11 is chosen by the sign
- * of the Riemann mass flux through that face (average when it is exactly zero).
+ * of the Riemann mass flux F_rho through that face.  Eq. 11's "otherwise" (no
+ * contact motion) is read as |F_rho| <= UPWIND_EPS * sigma, sigma = max(rho_L, rho_R)
+ * max(|S_L|, |S_R|) the face's mass-flux scale: a mass flux that is zero in exact
+ * arithmetic comes out as a few rounding errors of sigma, with either sign.
  * If only one of a, b is active the edge EMF is that axis' face EMF. */
-static double upwind(double fr, double left, double right) {
-  if (fr > 0.0) return left;
-  if (fr < 0.0) return right;
+#define UPWIND_EPS 1e-5
+
+static double upwind(double fr, double sigma, double left, double right) {
+  if (fr > UPWIND_EPS * sigma) return left;
+  if (fr < -UPWIND_EPS * sigma) return right;
   return 0.5 * (left + right);
 }
 
@@ -490,13 +503,17 @@ static void compute_emf(const grid* G, double* const W[NF], double* const Fl[3][
           }
           double da = G->d[a], db = G->d[b];
           /* d/db on a-face (a-1/2, b): between face point b and corner b-1/2 -> (b-1/4) */
-          double dEdb_q = upwind(Fl[a][RHO][o], 2.0 * (ec[1] - Eb_am) / db, 2.0 * (ec[0] - Eb_a) / db);
+          double dEdb_q = upwind(Fl[a][RHO][o], Fl[a][BXF + a][o], 2.0 * (ec[1] - Eb_am) / db,
+                                 2.0 * (ec[0] - Eb_a) / db);
           /* d/db on a-face (a-1/2, b-1): between corner b-1/2 and face point b-1 -> (b-3/4) */
-          double dEdb_3q = upwind(Fl[a][RHO][ob], 2.0 * (Eb_am - ec[3]) / db, 2.0 * (Eb_a - ec[2]) / db);
+          double dEdb_3q = upwind(Fl[a][RHO][ob], Fl[a][BXF + a][ob], 2.0 * (Eb_am - ec[3]) / db,
+                                  2.0 * (Eb_a - ec[2]) / db);
           /* d/da on b-face (a, b-1/2) -> (a-1/4) */
-          double dEda_q = upwind(Fl[b][RHO][o], 2.0 * (ec[2] - Ea_bm) / da, 2.0 * (ec[0] - Ea_b) / da);
+          double dEda_q = upwind(Fl[b][RHO][o], Fl[b][BXF + b][o], 2.0 * (ec[2] - Ea_bm) / da,
+                                 2.0 * (ec[0] - Ea_b) / da);
           /* d/da on b-face (a-1, b-1/2) -> (a-3/4) */
-          double dEda_3q = upwind(Fl[b][RHO][oa], 2.0 * (Ea_bm - ec[3]) / da, 2.0 * (Ea_b - ec[1]) / da);
+          double dEda_3q = upwind(Fl[b][RHO][oa], Fl[b][BXF + b][oa], 2.0 * (Ea_bm - ec[3]) / da,
+                                  2.0 * (Ea_b - ec[1]) / da);
           E[o] = 0.25 * (Ea_b + Ea_bm + Eb_a + Eb_am) + db / 8.0 * (dEdb_3q - dEdb_q) +
                  da / 8.0 * (dEda_3q - dEda_q);
         }

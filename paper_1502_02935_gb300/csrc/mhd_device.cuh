@@ -11,8 +11,9 @@
 //                   share the index i + PX (j + PY k).  No ghost cells: boundary
 //                   conditions are index maps applied on every load.
 //   scratch W, F, E : R, padded by 2 cells on active axes (QX = nx + 4 ...), holding
-//                   primitives W (8), face fluxes F_d (7 per direction: rho, mx, my, mz,
-//                   E, B_t1, B_t2 with (d, t1, t2) cyclic) and edge EMFs (3).
+//                   primitives W (8), face fluxes F_d (8 per direction: rho, mx, my, mz,
+//                   E, B_t1, B_t2 with (d, t1, t2) cyclic, and the face's mass-flux scale
+//                   sigma used by the corner-EMF upwinding) and edge EMFs (3).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -22,7 +23,7 @@ namespace mhd {
 
 enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BXF = 5, BYF = 6, BZF = 7 };
 enum { WR = 0, WVX = 1, WVY = 2, WVZ = 3, WP = 4, WBX = 5, WBY = 6, WBZ = 7 };
-enum { NFLUX = 7 };
+enum { NFLUX = 8 };  // rho, mx, my, mz, E, B_t1, B_t2, mass-flux scale
 enum : int { ERR_NONFINITE = 1, ERR_NEGATIVE = 2, ERR_TIMEOUT = 4 };
 enum { POT_NONE = 0, POT_GAUSS_X = 1, POT_LOG_DISC = 2 };
 
@@ -132,7 +133,8 @@ template <class R> __device__ __forceinline__ R fast_speed(R rho, R p, R bb, R b
 // ------------------------------------------------------------------ HLLD ----
 // Miyoshi & Kusano (2005) HLLD flux, the MHD Riemann solver named in Section 2.1.
 // w = [rho, vn, vt1, vt2, p, Bt1, Bt2] on each side, bn the face-normal field.
-// f = [rho, m_n, m_t1, m_t2, E, Bt1, Bt2] fluxes (Eq. 3 in the interface frame).
+// f = [rho, m_n, m_t1, m_t2, E, Bt1, Bt2] fluxes (Eq. 3 in the interface frame) and
+// f[7] = sigma = max(rho_L, rho_R) max(|S_L|, |S_R|), the face's mass-flux scale.
 template <class R>
 __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f) {
   const R half = R(0.5);
@@ -152,6 +154,7 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   const R sr = (ul > ur ? ul : ur) + cmax;
   const R vbl = ul * bn + vl * byl + zl * bzl;
   const R vbr = ur * bn + vr * byr + zr * bzr;
+  f[7] = (rl > rr ? rl : rr) * (Ar<R>::abs_(sl) > Ar<R>::abs_(sr) ? Ar<R>::abs_(sl) : Ar<R>::abs_(sr));
 
   if (sl > R(0)) {
     f[0] = rl * ul;
@@ -402,7 +405,7 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
 #pragma unroll
   for (int a = 0; a < 3; ++a) s3[a] = (a == D) ? fmap(P, a, c3[a]) : cmap(P, a, c3[a]);
   const R bn = (R)Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])];
-  R f[7];
+  R f[8];
   hlld<R>(wl, wr, bn, (R)P.gamma, f);
   F[q] = f[0];
   F[(1 + D) * QS + q] = f[1];
@@ -411,14 +414,18 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
   F[4 * QS + q] = f[4];
   F[5 * QS + q] = f[5];
   F[6 * QS + q] = f[6];
+  F[7 * QS + q] = f[7];
 }
 
 // -------------------------------------------------------------- phase: EMF ----
 // Corner EMF E_C at edge (A-1/2, B-1/2), (A, B, C) cyclic (Eq. 9-11): mean of the four
 // face EMFs plus upwinded one-sided corrections, the upwind side given by the sign of
-// the Riemann mass flux (average when it is exactly zero); (db/8) * 2/db = 1/4.
-template <class R> __device__ __forceinline__ R upwind(R fr, R left, R right) {
-  return fr > R(0) ? left : (fr < R(0) ? right : R(0.5) * (left + right));
+// the Riemann mass flux F_rho; Eq. 11's "otherwise" is |F_rho| <= 1e-5 sigma (a flux
+// that is zero in exact arithmetic comes out as rounding noise of either sign);
+// (db/8) * 2/db = 1/4.
+template <class R> __device__ __forceinline__ R upwind(R fr, R sigma, R left, R right) {
+  const R t = R(1e-5) * sigma;
+  return fr > t ? left : (fr < -t ? right : R(0.5) * (left + right));
 }
 
 template <class R, int C>
@@ -448,10 +455,12 @@ __device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restr
     const R ec1 = -(vA[oa] * bB[oa] - vB[oa] * bA[oa]);
     const R ec2 = -(vA[ob] * bB[ob] - vB[ob] * bA[ob]);
     const R ec3 = -(vA[oab] * bB[oab] - vB[oab] * bA[oab]);
-    const R d_bq = upwind<R>(FA[q], ec1 - Eb_am, ec0 - Eb_a);
-    const R d_b3q = upwind<R>(FA[ob], Eb_am - ec3, Eb_a - ec2);
-    const R d_aq = upwind<R>(FB[q], ec2 - Ea_bm, ec0 - Ea_b);
-    const R d_a3q = upwind<R>(FB[oa], Ea_bm - ec3, Ea_b - ec1);
+    const R* SA = FA + 7 * QS;
+    const R* SB = FB + 7 * QS;
+    const R d_bq = upwind<R>(FA[q], SA[q], ec1 - Eb_am, ec0 - Eb_a);
+    const R d_b3q = upwind<R>(FA[ob], SA[ob], Eb_am - ec3, Eb_a - ec2);
+    const R d_aq = upwind<R>(FB[q], SB[q], ec2 - Ea_bm, ec0 - Ea_b);
+    const R d_a3q = upwind<R>(FB[oa], SB[oa], Ea_bm - ec3, Ea_b - ec1);
     e = R(0.25) * (Ea_b + Ea_bm + Eb_a + Eb_am) + R(0.25) * (d_b3q - d_bq) +
         R(0.25) * (d_a3q - d_aq);
   }

@@ -92,7 +92,7 @@ __global__ void k_hlld(int n, const double* __restrict__ wl, const double* __res
                        const double* __restrict__ bn, double gam, double* __restrict__ flux) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  R a[7], b[7], f[7];
+  R a[7], b[7], f[8];
   const int src[7] = {0, 1, 2, 3, 4, 6, 7};
 #pragma unroll
   for (int m = 0; m < 7; ++m) {

@@ -1,13 +1,16 @@
 """GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle.
 
-Tolerances
-  FP64 path : |gpu - oracle| <= 1e-12 * max(|oracle|, 1e-3 * max|field|) per value, per
-              step (the two evaluate the same formulas in a different operation order;
-              rounding differences are ~1e-16 per operation).
-  mixed path: FP32 bulk arithmetic with FP64 pressure recovery and accumulation.  One
-              step moves U by h * div F with h * |div F| ~ CFL * |U|, so FP32 rounding of
-              the increments gives ~1e-7 relative; the stated bound is MIXED_TOL below,
-              on the same scale.
+Error scale.  For each field the magnitude M is the maximum of |oracle| over the box;
+for the momentum and the face field, M is taken over all three components (a vector's
+component is compared against the vector's size, not against itself: a component that
+starts at zero would otherwise be judged against its own rounding noise).
+
+  FP64 path : |gpu - oracle| <= 1e-12 * max(|oracle|, 1e-3 M) at every value, every step.
+              The two evaluate the same formulas in a different operation order; each
+              operation differs by ~1e-16.
+  mixed path: max |gpu - oracle| <= MIXED_TOL * M per step.  FP32 bulk arithmetic: the
+              increment h div F of one step is ~CFL |U| and carries ~1e-7 relative
+              rounding; the FP64 recovery and accumulation keep it from growing in |U|.
 """
 from __future__ import annotations
 
@@ -22,30 +25,32 @@ from paper_1502_02935_gb300 import inputs, mhd
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-MIXED_TOL = 2e-5
+MIXED_TOL = 1e-6
 
 
-def assert_close(got: inputs.State, ref: inputs.State, tol: float, what: str = ""):
-    fields = [("U%d" % f, got.U[f], ref.U[f]) for f in range(5)]
-    fields += [("Bx", got.Bx, ref.Bx), ("By", got.By, ref.By), ("Bz", got.Bz, ref.Bz)]
-    for name, a, b in fields:
-        scale = np.maximum(np.abs(b), 1e-3 * max(np.max(np.abs(b)), 1e-300))
-        err = np.max(np.abs(a - b) / scale)
-        assert err <= tol, f"{what} {name}: max scaled error {err:.3e} > {tol:.1e}"
-
-
-def max_scaled_errors(got, ref):
-    out = {}
-    fields = [("rho", 0), ("mx", 1), ("my", 2), ("mz", 3), ("E", 4)]
-    for name, f in fields:
-        b = ref.U[f]
-        scale = np.maximum(np.abs(b), 1e-3 * max(np.max(np.abs(b)), 1e-300))
-        out[name] = float(np.max(np.abs(got.U[f] - b) / scale))
-    for name in ("Bx", "By", "Bz"):
-        a, b = getattr(got, name), getattr(ref, name)
-        scale = np.maximum(np.abs(b), 1e-3 * max(np.max(np.abs(b)), 1e-300))
-        out[name] = float(np.max(np.abs(a - b) / scale))
+def _fields(st):
+    mmag = float(np.max(np.abs(st.U[1:4])))
+    bmag = max(float(np.max(np.abs(st.Bx))), float(np.max(np.abs(st.By))), float(np.max(np.abs(st.Bz))))
+    out = [("rho", st.U[0], float(np.max(np.abs(st.U[0])))), ("mx", st.U[1], mmag), ("my", st.U[2], mmag),
+           ("mz", st.U[3], mmag), ("E", st.U[4], float(np.max(np.abs(st.U[4]))))]
+    out += [(k, getattr(st, k), bmag) for k in ("Bx", "By", "Bz")]
     return out
+
+
+def errors(got: inputs.State, ref: inputs.State):
+    """{field: (pointwise scaled max error, max error / M)}"""
+    res = {}
+    for (name, a, _), (_, b, M) in zip(_fields(got), _fields(ref)):
+        M = max(M, 1e-300)
+        d = np.abs(a - b)
+        res[name] = (float(np.max(d / np.maximum(np.abs(b), 1e-3 * M))), float(np.max(d)) / M)
+    return res
+
+
+def assert_close(got: inputs.State, ref: inputs.State, tol: float, what: str = "", normalized: bool = False):
+    for name, (pw, nm) in errors(got, ref).items():
+        err = nm if normalized else pw
+        assert err <= tol, f"{what} {name}: {'normalized' if normalized else 'pointwise'} error {err:.3e} > {tol:.1e}"
 
 
 def _geom(n, bc, d=(0.1, 0.11, 0.13), lo=(0.0, 0.0, 0.0), gamma=5.0 / 3.0):
@@ -104,7 +109,7 @@ def test_fp64_multi_step_parity(case):
 def test_mixed_one_step_parity(case):
     st, src = CASES[case]()
     got, ref, _ = _run_pair(st, src, "mixed", 1)
-    assert_close(got, ref, MIXED_TOL, case)
+    assert_close(got, ref, MIXED_TOL, case, normalized=True)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("mixed", 1e-6)])
@@ -194,18 +199,19 @@ def test_full_size_turbulence_sampled_parity(precision, tol):
     rng = np.random.default_rng(99)
     h = 5
     samples = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(12)] + [(0, 0, 0), (255, 255, 255)]
-    scale = np.max(np.abs(st.U).reshape(5, -1), axis=1)
+    M = {name: m for name, _, m in _fields(got)}
+    floor = 1e-3 if precision == "fp64" else 1.0
     for c in samples:
         sub = _subbox(st, c, h)
         out = oracle.step(sub, dt)
-        for f in range(5):
+        for f, name in enumerate(("rho", "mx", "my", "mz", "E")):
             a = got.U[f, c[2], c[1], c[0]]
             b = out.U[f, h, h, h]
-            assert abs(a - b) <= tol * max(abs(b), 1e-3 * scale[f]), (c, f, a, b)
-        for name, fi in (("Bx", (c[2], c[1], c[0])), ("By", (c[2], c[1], c[0])), ("Bz", (c[2], c[1], c[0]))):
-            a = getattr(got, name)[fi]
+            assert abs(a - b) <= tol * max(abs(b) if precision == "fp64" else 0.0, floor * M[name]), (c, f, a, b)
+        for name in ("Bx", "By", "Bz"):
+            a = getattr(got, name)[c[2], c[1], c[0]]
             b = getattr(out, name)[h, h, h]
-            assert abs(a - b) <= tol * max(abs(b), 1e-3 * 0.1), (c, name, a, b)
+            assert abs(a - b) <= tol * max(abs(b) if precision == "fp64" else 0.0, floor * M[name]), (c, name, a, b)
 
 
 def test_hlld_device_matches_oracle():
@@ -232,6 +238,8 @@ def test_hlld_device_matches_oracle():
     assert np.max(np.abs(got - ref) / scale) <= 1e-13
     got32 = mhd.riemann_hlld(wl, wr, bn, 5.0 / 3.0, "mixed")
     assert np.max(np.abs(got32 - ref) / scale) <= 2e-5
+    # the mass-flux scale sits in the normal-field slot only inside the step; here it is 0
+    assert np.all(got[:, 5] == 0.0)
 
 
 def test_nonfinite_and_negative_inputs_are_reported():
