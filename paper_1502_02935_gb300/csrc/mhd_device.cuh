@@ -245,8 +245,9 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   R F5 = b1 * un - bn * v1;
   R F6 = b2 * un - bn * v2;
   // F*_a = F_a + S_a (U*_a - U_a)
-  const R rsa = rs[side], vsa = vs[side], zsa = zs[side], bysa = bys[side], bzsa = bzs[side];
-  const R esa = es[side];
+  const R rsa = side ? rs[1] : rs[0], vsa = side ? vs[1] : vs[0], zsa = side ? zs[1] : zs[0];
+  const R bysa = side ? bys[1] : bys[0], bzsa = side ? bzs[1] : bzs[0];
+  const R esa = side ? es[1] : es[0];
   F0 += S * (rsa - rho);
   F1 += S * (rsa * sm - rho * un);
   F2 += S * (rsa * vsa - rho * v1);
@@ -322,17 +323,19 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
   const long long c = sidx(P, ci, cj, ck);
   const double rho = U[c];
   const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c], e = U[EN * FS + c];
-  const double bx = 0.5 * (U[BXF * FS + sidx(P, fmap(P, 0, i), cj, ck)] +
-                           U[BXF * FS + sidx(P, fmap(P, 0, i + 1), cj, ck)]);
-  const double by = 0.5 * (U[BYF * FS + sidx(P, ci, fmap(P, 1, j), ck)] +
-                           U[BYF * FS + sidx(P, ci, fmap(P, 1, j + 1), ck)]);
-  const double bz = 0.5 * (U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k))] +
-                           U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k + 1))]);
+  // sums of the two face values (twice the cell-centred field of Eq. 6)
+  const double sbx = U[BXF * FS + sidx(P, fmap(P, 0, i), cj, ck)] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), cj, ck)];
+  const double sby = U[BYF * FS + sidx(P, ci, fmap(P, 1, j), ck)] + U[BYF * FS + sidx(P, ci, fmap(P, 1, j + 1), ck)];
+  const double sbz = U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k))] + U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k + 1))];
   const double irho = inv_density<R>(rho);
-  const double kin = 0.5 * (mx * mx + my * my + mz * mz) * irho;
-  const double mag = 0.5 * (bx * bx + by * by + bz * bz);
-  const double p = (P.gamma - 1.0) * (e - kin - mag);
-  const R vx = (R)(mx * irho), vy = (R)(my * irho), vz = (R)(mz * irho);
+  const double m2 = mx * mx + my * my + mz * mz;
+  const double b2 = sbx * sbx + sby * sby + sbz * sbz;  // 4 |B_cc|^2
+  const double gm1 = P.gamma - 1.0;
+  // p = (gamma-1) (E - |m|^2/(2 rho) - |B_cc|^2/2), in FP64
+  const double p = gm1 * e - (0.5 * gm1) * (m2 * irho) - (0.125 * gm1) * b2;
+  const R rirho = (R)irho;
+  const R vx = (R)mx * rirho, vy = (R)my * rirho, vz = (R)mz * rirho;
+  const R bx = (R)sbx * R(0.5), by = (R)sby * R(0.5), bz = (R)sbz * R(0.5);
   if (store) {
     const long long q = qidx(P, i, j, k), QS = P.QS;
     W[q] = (R)rho;
@@ -340,9 +343,9 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
     W[WVY * QS + q] = vy;
     W[WVZ * QS + q] = vz;
     W[WP * QS + q] = (R)p;
-    W[WBX * QS + q] = (R)bx;
-    W[WBY * QS + q] = (R)by;
-    W[WBZ * QS + q] = (R)bz;
+    W[WBX * QS + q] = bx;
+    W[WBY * QS + q] = by;
+    W[WBZ * QS + q] = bz;
   }
   double lim = INFINITY;
   if (interior) {
@@ -352,7 +355,7 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
       atomicOr(P.err, ERR_NEGATIVE);
     }
     const R v[3] = {vx, vy, vz};
-    const R b[3] = {(R)bx, (R)by, (R)bz};
+    const R b[3] = {bx, by, bz};
     const R bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -497,17 +500,23 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
 #pragma unroll
       for (int f = 0; f < 5; ++f) div[f] += (Fd[f * QS + q + st] - Fd[f * QS + q]) * idd;
     }
-    R g[3];
-    grad_psi<R>(src, P.lo[0] + (i + 0.5) * P.d[0], P.lo[1] + (j + 0.5) * P.d[1],
-                P.lo[2] + (k + 0.5) * P.d[2], g);
-    const R rho = (R)Us[s];
-    const R sm[3] = {-rho * g[0], -rho * g[1], -rho * g[2]};
-    const R se = -((R)Us[MX * FS + s] * g[0] + (R)Us[MY * FS + s] * g[1] + (R)Us[MZ * FS + s] * g[2]);
     Uo[s] = Ub[s] - (double)(h * div[0]);
+    if (src.potential == POT_NONE) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-      Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - (double)(h * div[1 + a]) + (double)(h * sm[a]);
-    Uo[EN * FS + s] = Ub[EN * FS + s] - (double)(h * div[4]) + (double)(h * se);
+      for (int a = 0; a < 3; ++a) Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - (double)(h * div[1 + a]);
+      Uo[EN * FS + s] = Ub[EN * FS + s] - (double)(h * div[4]);
+    } else {
+      R g[3];
+      grad_psi<R>(src, P.lo[0] + (i + 0.5) * P.d[0], P.lo[1] + (j + 0.5) * P.d[1],
+                  P.lo[2] + (k + 0.5) * P.d[2], g);
+      const R rho = (R)Us[s];
+      const R sm[3] = {-rho * g[0], -rho * g[1], -rho * g[2]};
+      const R se = -((R)Us[MX * FS + s] * g[0] + (R)Us[MY * FS + s] * g[1] + (R)Us[MZ * FS + s] * g[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - (double)(h * div[1 + a]) + (double)(h * sm[a]);
+      Uo[EN * FS + s] = Ub[EN * FS + s] - (double)(h * div[4]) + (double)(h * se);
+    }
   }
   // faces
   const int c3[3] = {i, j, k};
