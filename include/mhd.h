@@ -162,6 +162,30 @@ void mhd_destroy(mhd_ctx* ctx);
 int mhd_riemann_hlld(int n, const double* wl, const double* wr, const double* bn, double gamma,
                      int precision, double* flux, void* stream);
 
+/* Largest patch (nx*ny*nz cells) that mhd_cfl_dt_noalloc accepts. */
+#define MHD_NOALLOC_MAX_CELLS 8388608
+
+/* CFL time step of a state held by the caller, computed without allocating device
+ * memory.  The paper has no counterpart: this exists for callers that cannot allocate
+ * (an application that reserves the whole device through its own memory pool, or a
+ * loop that cannot afford the synchronisation cudaMalloc/cudaFree imply).
+ *   p        : one patch descriptor (boundary conditions are not used).
+ *   cfl      : Courant number, > 0.
+ *   U, Bface : device pointers to the state in the host format above (FP64).
+ *   dt_out   : device pointer; receives cfl * min over cells and active axes of
+ *              d / (|v_d| + c_fast,d), computed in FP64 as mhd_cfl_dt of an FP64 context.
+ *   stream   : cudaStream_t or NULL; the call is asynchronous on it.
+ * Scratch is a fixed 32 KiB __device__ array inside the library, held by every GPU
+ * that loads it until the process exits; the call allocates and frees nothing.
+ * Returns MHD_ERR_ARG for bad arguments or nx*ny*nz > MHD_NOALLOC_MAX_CELLS, and
+ * MHD_ERR_CUDA if a launch fails.  The first call on each device looks up the
+ * scratch array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (e.g. on two streams) race and must be
+ * serialised by the caller. */
+int mhd_cfl_dt_noalloc(const mhd_patch_desc* p, double cfl, const double* U, const double* Bface,
+                       double* dt_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

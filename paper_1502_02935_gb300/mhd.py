@@ -58,7 +58,8 @@ _lib = None
 
 EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cfl_dt_patches",
            "mhd_get_state", "mhd_set_state", "mhd_sync", "mhd_get_metrics", "mhd_launch_count",
-           "mhd_last_error", "mhd_destroy", "mhd_riemann_hlld", "mhd_set_profiling", "mhd_get_profile"]
+           "mhd_last_error", "mhd_destroy", "mhd_riemann_hlld", "mhd_set_profiling", "mhd_get_profile",
+           "mhd_cfl_dt_noalloc"]
 
 
 def lib():
@@ -89,6 +90,7 @@ def lib():
     L.mhd_riemann_hlld.argtypes = [ip, vp, vp, vp, C.c_double, ip, vp, vp]
     L.mhd_set_profiling.argtypes = [vp, ip]
     L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
+    L.mhd_cfl_dt_noalloc.argtypes = [C.POINTER(PatchDesc), C.c_double, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("mhd_destroy", "mhd_last_error", "mhd_launch_count"):
             getattr(L, name).restype = C.c_int
@@ -237,3 +239,12 @@ def riemann_hlld(wl, wr, bn, gamma: float, precision="fp64") -> np.ndarray:
     if rc != 0:
         raise MHDError(rc, "mhd_riemann_hlld")
     return out.cpu().numpy()
+
+
+NOALLOC_MAX_CELLS = 8388608
+
+
+def cfl_dt_noalloc(geom: Geom, cfl: float, U_ptr: int, B_ptr: int, dt_ptr: int, stream: int = 0) -> int:
+    """Call mhd_cfl_dt_noalloc: device pointers in, device pointer out; returns the status."""
+    d = patch_desc(geom)
+    return int(lib().mhd_cfl_dt_noalloc(C.byref(d), float(cfl), U_ptr, B_ptr, dt_ptr, stream))
