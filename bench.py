@@ -41,20 +41,23 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
-# algorithmic work per item of each kernel class ("Roofline"):
-#   flops  : FP32 (mixed) arithmetic of the method per item, FMA counted as 2
-#   bytes  : unique HBM bytes per item (mixed path, FP32 scratch)
+# Algorithmic work per item of each kernel class of the mixed path (counted from the
+# formulas; the design doc section 5 lists the counts):
+#   bound "fp64": FP64 flops of the precision split (recovery, accumulation), FMA = 2
+#   bound "fp32": FP32 flops of reconstruction + HLLD, FMA = 2
+#   bound "hbm" : unique HBM bytes
 KCLASS = {
-    "recovery": dict(bound="hbm", flops=60, bytes=64 + 8 * 4, unit="padded cell"),
-    "flux1_x": dict(bound="alu", flops=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
-    "flux1_y": dict(bound="alu", flops=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
-    "flux1_z": dict(bound="alu", flops=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
-    "flux2_x": dict(bound="alu", flops=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
-    "flux2_y": dict(bound="alu", flops=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
-    "flux2_z": dict(bound="alu", flops=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
-    "emf": dict(bound="hbm", flops=75, bytes=(9 + 6 + 3) * 4, unit="edge point"),
-    "update": dict(bound="hbm", flops=50, bytes=18 * 4 + 64 + 16 + 64, unit="cell"),
+    "recovery": dict(bound="fp64", work=23, unit="padded cell"),
+    "flux1_x": dict(bound="fp32", work=343, unit="face"),
+    "flux1_y": dict(bound="fp32", work=343, unit="face"),
+    "flux1_z": dict(bound="fp32", work=343, unit="face"),
+    "flux2_x": dict(bound="fp32", work=553, unit="face"),
+    "flux2_y": dict(bound="fp32", work=553, unit="face"),
+    "flux2_z": dict(bound="fp32", work=553, unit="face"),
+    "emf": dict(bound="hbm", work=(9 + 6 + 3) * 4, unit="edge point"),
+    "update": dict(bound="fp64", work=8, unit="point"),
 }
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); a DFMA probe measured 1.0
 
 
 def units_per_launch(cls: str, n: int) -> int:
@@ -206,6 +209,104 @@ def timed_steps(grid, steps: int, stream):
     return e0.elapsed_time(e1)
 
 
+def run_batched(args, stream, world=1, rank=0, pg=None):
+    """64 independent periodic blast patches (edges from {32,48,64,96,128} by seed), all
+    advanced in one persistent launch per step under a captured graph, tile shape from the
+    autotuner; each patch on its own CFL dt.  Returns zone-updates/s of the mixed path,
+    beside the same batch stepped with one launch per phase per patch."""
+    import torch
+    from paper_1502_02935_gb300 import inputs, mhd, sharding
+    allst = inputs.blast_batch(64, seed=SEED)
+    mine = sharding.partition([s.geom.ncell for s in allst], world)[rank]
+    sts = [allst[i] for i in mine]  # this rank's share; no data crosses ranks
+    cells = sum(s.geom.ncell for s in allst)
+    out = {"workload": "64 periodic blast patches, edges from {32,48,64,96,128} (seed 1502), gamma=5/3, "
+                       "rho=1, p=0.1 / 10 inside r<0.1, |B|=1/sqrt2 along a seeded direction; mixed path",
+           "cells": cells, "unit": "zone-updates/s"}
+    for name, flags in (("persistent", mhd.FLAG_PERSISTENT | mhd.FLAG_GRAPH), ("per_phase", mhd.FLAG_GRAPH)):
+        g = mhd.Grid(sts, precision="mixed", cfl=CFL, flags=flags, stream=stream.cuda_stream)
+        if flags & mhd.FLAG_PERSISTENT:
+            cache = os.path.join(ROOT, "paper_1502_02935_gb300", "tune_cache.json")
+            out["tile"] = list(g.autotune(cache))
+        for _ in range(args.warmup):
+            g.step(-1.0)
+        torch.cuda.synchronize()
+        l0 = g.launch_count()
+        k = max(3, min(args.steps, 20))
+        barrier(pg)
+        ms = max_over_ranks(pg, timed_steps(g, k, stream))
+        out[name] = {"value": cells * k / (ms / 1e3), "ms_per_step": ms / k, "gpu_launches": g.launch_count() - l0}
+        g.close()
+    out["value"] = out["persistent"]["value"]
+    return out
+
+
+def run_disc(args, stream):
+    """Isolated gas disc (512x512x128 on 40x40x10 kpc, outflow, logarithmic potential in S,
+    toroidal field with beta 10) with the thermal source: the plain FP64 integrator for the
+    first steps (harvesting training pairs), the surrogate trained on the GPU, then the
+    surrogate with per-cell fallback.  Reports the thermal phase's GPU time per step both
+    ways (CUDA events around its kernels), the fallback fraction, and the L1-relative
+    difference in T after the same steps taken with the plain integrator from the same state."""
+    import torch
+    from paper_1502_02935_gb300 import inputs, mhd
+    th = inputs.DISC_THERMAL
+    nx, ny, nz = args.disc
+    st = inputs.disc(nx, ny, nz)
+    out = {"workload": f"disc {nx}x{ny}x{nz} on 40x40x10 kpc, outflow, log potential v0=220 km/s, beta=10, "
+                       "T=1e4 K, thermal source (stand-in cooling table), mixed path",
+           "cells": st.geom.ncell}
+    g = mhd.Grid(st, precision="mixed", cfl=CFL, flags=mhd.FLAG_GRAPH, stream=stream.cuda_stream)
+    g.set_sources(**inputs.DISC_POTENTIAL)
+    g.set_thermal(mhd.THERMAL_PLAIN, **th)
+    harvest_steps = 6
+    g.surrogate_harvest(1 << 21, stride=max(1, st.geom.ncell * harvest_steps // (1 << 21)))
+    g.set_profiling(True)
+    for _ in range(harvest_steps):
+        g.step(-1.0)
+    prof = g.profile()
+    g.set_profiling(False)
+    plain_ms = prof["thermal"][0] / max(prof["thermal"][1], 1)
+    step_ms_plain = sum(v[0] for v in prof.values()) / harvest_steps
+    t0 = time.perf_counter()
+    loss, rows = g.surrogate_train(epochs=40, batch=8192, lr=3e-3, seed=SEED)
+    train_s = time.perf_counter() - t0
+    mid = g.get_state(0)
+    g.set_thermal(mhd.THERMAL_SURROGATE, **th)
+    h = mhd.Grid(mid, precision="mixed", cfl=CFL, flags=mhd.FLAG_GRAPH, stream=stream.cuda_stream)
+    h.set_sources(**inputs.DISC_POTENTIAL)
+    h.set_thermal(mhd.THERMAL_PLAIN, **th)
+    s0 = g.thermal_stats()
+    g.set_profiling(True)
+    k = 5
+    for _ in range(k):
+        g.step(-1.0)
+        h.step(-1.0)
+    prof = g.profile()
+    g.set_profiling(False)
+    s1 = g.thermal_stats()
+    sur_ms = prof["thermal"][0] / max(prof["thermal"][1], 1)
+    step_ms_sur = sum(v[0] for v in prof.values()) / k
+
+    def temperature(x):
+        bx, by, bz = x.bcc()
+        kin = 0.5 * (x.U[1] ** 2 + x.U[2] ** 2 + x.U[3] ** 2) / x.U[0]
+        p = (x.geom.gamma - 1) * (x.U[4] - kin - 0.5 * (bx * bx + by * by + bz * bz))
+        return th["t_per_pr"] * p / x.U[0]
+
+    Ts, Tp = temperature(g.get_state(0)), temperature(h.get_state(0))
+    g.close()
+    h.close()
+    out.update({"thermal_ms_plain": plain_ms, "thermal_ms_surrogate": sur_ms, "thermal_gain": plain_ms / sur_ms,
+                "step_ms_plain": step_ms_plain, "step_ms_surrogate": step_ms_sur,
+                "zone_updates_per_s_plain": st.geom.ncell / (step_ms_plain / 1e3),
+                "zone_updates_per_s_surrogate": st.geom.ncell / (step_ms_sur / 1e3),
+                "fallback_fraction": (s1["fallback"] - s0["fallback"]) / max(1, s1["cells"] - s0["cells"]),
+                "train_rows": rows, "train_loss": loss, "train_s": train_s,
+                "l1_T_vs_plain_after_%d_steps" % k: float(np.mean(np.abs(Ts - Tp)) / np.mean(np.abs(Tp)))})
+    return out
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     from paper_1502_02935_gb300 import inputs, mhd
@@ -242,21 +343,27 @@ def run_ours(args, world, rank, local, pg):
     prof = grid.profile()
     grid.set_profiling(False)
     tot = sum(v[0] for v in prof.values()) or 1.0
-    dom = max((k for k in prof if k in KCLASS), key=lambda k: prof[k][0])
-    dom_ms = prof[dom][0] / max(prof[dom][1], 1)
-    kc = KCLASS[dom]
-    units = units_per_launch(dom, n)
-    clk_mhz = (clk or {}).get("sm_mhz") or sm_max_mhz
-    if kc["bound"] == "alu":
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
-        achieved = kc["flops"] * units / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom,
-                "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max_mhz:.0f} MHz (derived)"}
-    else:
-        achieved = kc["bytes"] * units / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom, "peak_note": f"{peak_kind} hbm_gbs"}
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    roofs = {}
+    for k, kc in KCLASS.items():
+        if not prof.get(k) or not prof[k][1]:
+            continue
+        t = prof[k][0] / prof[k][1] / 1e3  # s per launch
+        units = units_per_launch(k, n)
+        if kc["bound"] == "hbm":
+            ach = kc["work"] * units / t / 1e9
+            roofs[k] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
+        else:
+            peak = FP64_PEAK_TFLOPS if kc["bound"] == "fp64" else fp32_peak
+            ach = kc["work"] * units / t / 1e12
+            roofs[k] = {"bound": "alu", "pipe": kc["bound"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak}
+    dom = max(roofs, key=lambda k: prof[k][0])
+    roof = dict(roofs[dom])
+    roof.update({"traffic": None, "kernel": dom,
+                 "peak_note": ("nominal FP64 1.25 TFLOP/s (recipe); probe measured 1.0" if roof.get("pipe") == "fp64"
+                               else (f"FP32 152 SMs x 128 lanes x 2 x {sm_max_mhz:.0f} MHz (derived)"
+                                     if roof.get("pipe") == "fp32" else f"{peak_kind} hbm_gbs"))})
     shares = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
 
     # plain FP64 path on the same box
@@ -288,6 +395,8 @@ def run_ours(args, world, rank, local, pg):
     e2e_value = zones * ke * world / (ms_e2e / 1e3)
     io_bytes = (U_h.numel() + B_h.numel()) * 8
     grid.close()
+    batched = run_batched(args, stream, world, rank, pg) if args.batched else None
+    disc = run_disc(args, stream) if args.disc else None
 
     if rank != 0:
         return 0
@@ -310,6 +419,9 @@ def run_ours(args, world, rank, local, pg):
         "hbm_alg_frac": value / world * 128.0 / (hbm_peak * 1e9),
         "fp64_path": {"value": fp64_value, "unit": "zone-updates/s", "steps": k64},
         "kernel_shares": shares,
+        "kernel_rooflines": roofs,
+        "batched": batched,
+        "disc_thermal": disc,
         "cpu_baseline": cb,
     }
     print(json.dumps(line), flush=True)
@@ -323,8 +435,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_CELLS, help="cells per axis (default 256)")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 64-patch batched workload")
+    ap.add_argument("--disc", type=int, nargs=3, default=[512, 512, 128],
+                    help="disc workload cells (nx ny nz); 0 0 0 skips it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.disc == [0, 0, 0]:
+        args.disc = None
     world, rank, local, pg = dist_setup()
     try:
         if args.impl == "reference":

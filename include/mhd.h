@@ -63,6 +63,8 @@ enum {
 
 enum { MHD_POT_NONE = 0, MHD_POT_GAUSS_X = 1, MHD_POT_LOG_DISC = 2 };
 
+enum { MHD_THERMAL_OFF = 0, MHD_THERMAL_PLAIN = 1, MHD_THERMAL_SURROGATE = 2 };
+
 /* One rectangular patch.  Axes with n = 1 are trivial (no fluxes along them). */
 typedef struct {
   int nx, ny, nz;
@@ -91,6 +93,24 @@ typedef struct {
   double psi0, xc, xw;
   double v0, rc;
 } mhd_source_desc;
+
+/* Thermal source term (heating and cooling in S of Eq. 2; the thermal module of
+ * Section 3.10), applied operator-split after each step: per interior cell, isochoric
+ *   e = c_e T,   de/dt = (n_H gamma_heat - n_H^2 Lambda(T, z)) / rate_unit,
+ * T = t_per_pr p/rho, n_H = nh_per_rho rho, c_e = rho/(t_per_pr (gamma-1)).  Lambda is a
+ * built-in piecewise power law over 10 K..1e8 K standing in for the paper's tables.
+ * MHD_THERMAL_PLAIN integrates it in FP64 by sub-stepped backward Euler (sub-step change
+ * capped at cap*T, Newton with bisection safeguard); MHD_THERMAL_SURROGATE evaluates the
+ * trained MLP (mhd_surrogate_train) and falls back to the plain integrator per cell. */
+typedef struct {
+  int mode;          /* MHD_THERMAL_* */
+  double gamma_heat; /* heating per hydrogen atom, erg/s */
+  double z;          /* metallicity */
+  double rate_unit;  /* erg cm^-3 s^-1 per code energy density per code time */
+  double cap;        /* largest relative temperature change per sub-step, (0, 1] */
+  double nh_per_rho; /* hydrogen number density [cm^-3] per code density */
+  double t_per_pr;   /* temperature [K] per code p/rho */
+} mhd_thermal_desc;
 
 typedef struct {
   double dt_last;        /* dt used by the last step of patch 0 */
@@ -138,16 +158,65 @@ int mhd_get_metrics(mhd_ctx* ctx, mhd_metrics* out);
  * (graph replays count the kernels inside the graph). */
 long long mhd_launch_count(const mhd_ctx* ctx);
 
+/* Set the thermal source term (default off).  Thermal cells are applied after each step
+ * with that step's dt of the patch. */
+int mhd_set_thermal(mhd_ctx* ctx, const mhd_thermal_desc* th);
+
+/* Thermal counters since the thermal term was first set: out4[0] cells integrated,
+ * [1] backward-Euler sub-steps, [2] cells that hit a sub-step or Newton cap,
+ * [3] surrogate cells that fell back to the plain integrator.  Synchronises. */
+int mhd_thermal_stats(mhd_ctx* ctx, unsigned long long* out4);
+
+/* Surrogate of the thermal source (a 4 -> 64 -> 64 -> 1 tanh network on x = (log10 n_H,
+ * log10 T, log10 dt, Z) mapped to [-1, 1] by the training range, predicting the change of
+ * log10 T over dt; the 64x64 layer on BF16 tensor cores with FP32 accumulation).
+ *
+ * mhd_surrogate_harvest: while the thermal mode is MHD_THERMAL_PLAIN, record training pairs
+ * from the plain integrator into a device ring of `capacity` rows, from about one cell in
+ * `stride` per step (a hash of the cell index salted by the step's dt).  Each sampled cell
+ * gives three rows: the step's dt and, integrated again, dt/3 and 3 dt.  capacity 0 stops.
+ *
+ * mhd_surrogate_train: train on the harvested pairs on the GPU: MSE loss, Adam (beta1 0.9,
+ * beta2 0.999) on FP32 master weights with the learning rate decayed from lr to lr/20 on a
+ * cosine, minibatches of `batch` rows drawn with a hash of (seed, step, row), `epochs`
+ * passes of rows/batch steps, weights initialised from seed.
+ * dmax > 0 is the fallback bound on the predicted |change of log10 T|; dmax <= 0 takes the
+ * largest change in the training set.  loss_out receives the mean squared error of the
+ * last epoch, rows_out the number of training rows (either may be NULL).  Harvesting stops.
+ *
+ * mhd_surrogate_params: copy the FP32 parameters out (4545 floats: W1[64][4], b1[64],
+ * W2[64][64], b2[64], w3[64], b3) and, if range_out is not NULL, 9 floats: the input
+ * offsets lo[4], scales s[4] (x_s = (x - lo) s - 1) and dmax. */
+int mhd_surrogate_harvest(mhd_ctx* ctx, long long capacity, int stride);
+int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double dmax,
+                        double* loss_out, long long* rows_out);
+int mhd_surrogate_params(mhd_ctx* ctx, float* params_out, float* range_out);
+
 /* Per-kernel timing.  While on, every launch is bracketed by a CUDA event pair on the
  * context's stream (steps are not replayed from a graph) and the elapsed times are summed
  * per kernel class: 0 recovery+CFL, 1-3 donor-cell HLLD fluxes x/y/z, 4-6 kappa-scheme
- * HLLD fluxes x/y/z, 7 corner EMFs, 8 update, 9 standalone CFL.  Switching on or off
- * clears the totals. */
+ * HLLD fluxes x/y/z, 7 corner EMFs, 8 update, 9 standalone CFL, 10 persistent step,
+ * 11 thermal source.  Switching on or off clears the totals. */
 int mhd_set_profiling(mhd_ctx* ctx, int on);
 
 /* Totals since profiling was switched on: ms[c] milliseconds and launches[c] launches of
- * class c, for c < n (n >= 10).  Synchronises. */
+ * class c, for c < n (n >= 12).  Synchronises. */
 int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
+
+/* Autotuner of the persistent batched step (context made with MHD_FLAG_PERSISTENT): times
+ * the step for each candidate tile shape (TX x TY points of one z-plane per CTA) and CTA
+ * count per SM, keeps the fastest, and records it in a JSON cache file at cache_path,
+ * keyed by GPU name, precision and patch sizes (NULL: no cache).  force = 0 uses a cached
+ * entry without timing.  The state is restored after the timing runs.  tile_out (may be
+ * NULL) receives TX, TY.  MHD_ERR_STATE without MHD_FLAG_PERSISTENT. */
+int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out);
+
+/* Bounded waits of the persistent step.  limit_ms: the longest a CTA waits at a grid
+ * barrier before it sets the device error word to MHD_ERR_TIMEOUT and the launch ends
+ * (default 2000).  phantom_blocks: CTAs that never arrive but that the barrier also waits
+ * for (default 0; a positive value makes every wait run out, which exercises the timeout
+ * path without faulting or hanging the GPU). */
+int mhd_set_wait_limit(mhd_ctx* ctx, double limit_ms, int phantom_blocks);
 
 const char* mhd_last_error(const mhd_ctx* ctx);
 
@@ -161,6 +230,25 @@ void mhd_destroy(mhd_ctx* ctx);
  * FP64, MHD_PREC_MIXED in FP32 (inputs/outputs stay FP64).  stream may be NULL. */
 int mhd_riemann_hlld(int n, const double* wl, const double* wr, const double* bn, double gamma,
                      int precision, double* flux, void* stream);
+
+/* Unit-level entry for parity tests: the plain FP64 thermal integrator of
+ * MHD_THERMAL_PLAIN on n independent cells (device pointers): temperature T0 [K],
+ * n_H [cm^-3], c_e (code energy density per K), dt (code time) -> T_out, and per-cell
+ * status bits (1 sub-step cap, 2 Newton cap, 4 no bracket; status may be NULL).
+ * d->mode is ignored.  Synchronises stream (NULL allowed). */
+int mhd_thermal_cells(long long n, const double* T0, const double* nh, const double* ce, const double* dt,
+                      const mhd_thermal_desc* d, double* T_out, int* status, void* stream);
+
+/* Unit-level entries for parity tests of the surrogate kernels (device pointers; params
+ * in the layout of mhd_surrogate_params; inputs already in [-1, 1]):
+ * mhd_mlp_forward: y[n] for xs[n][4].
+ * mhd_mlp_grad: gradient (4545 floats) of the mean squared error over rows[n][5]
+ * (x0..x3, target) and the sum of squared errors in *loss_sum.  Synchronise stream. */
+int mhd_mlp_forward(long long n, const float* xs, const float* params, float* y, void* stream);
+/* The same forward pass with the 64x64 layer on tcgen05 tensor cores (TMEM accumulator);
+ * MHD_ERR_TIMEOUT if the bounded wait for the MMA ran out. */
+int mhd_mlp_forward_tc(long long n, const float* xs, const float* params, float* y, void* stream);
+int mhd_mlp_grad(long long n, const float* rows, const float* params, float* grad, float* loss_sum, void* stream);
 
 /* Largest patch (nx*ny*nz cells) that mhd_cfl_dt_noalloc accepts. */
 #define MHD_NOALLOC_MAX_CELLS 8388608

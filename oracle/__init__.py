@@ -75,14 +75,23 @@ def lib():
     return _lib
 
 
+class OrcThermal(C.Structure):
+    _fields_ = [("gamma_heat", C.c_double), ("z", C.c_double), ("rate_unit", C.c_double), ("cap", C.c_double),
+                ("nh_per_rho", C.c_double), ("t_per_pr", C.c_double)]
+
+
 def _bind_thermal(L):
-    if not hasattr(L, "orc_thermal_integrate"):
-        return
     dp = C.POINTER(C.c_double)
-    L.orc_thermal_integrate.argtypes = [C.c_long, dp, dp, dp, C.c_double, dp, C.POINTER(C.c_int)]
-    L.orc_thermal_integrate.restype = C.c_int
+    ip = C.POINTER(C.c_int)
     L.orc_cooling.argtypes = [C.c_long, dp, C.c_double, dp, dp]
+    L.orc_cooling.restype = None
+    L.orc_thermal_cells.argtypes = [C.c_long, dp, dp, dp, dp, C.POINTER(OrcThermal), dp, ip]
+    L.orc_thermal_cells.restype = C.c_int
+    L.orc_thermal_apply.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(OrcThermal), dp, dp, dp, dp,
+                                    C.c_double]
+    L.orc_thermal_apply.restype = C.c_int
     L.orc_mlp_forward.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_mlp_forward.restype = None
     L.orc_mlp_backward.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
     L.orc_mlp_backward.restype = C.c_double
 
@@ -177,3 +186,69 @@ def diagnostics(st):
 
 def set_threads(n: int) -> int:
     return int(lib().orc_set_threads(int(n)))
+
+
+# ----------------------------------------------------------------- thermal ----
+
+def thermal_struct(th: dict) -> OrcThermal:
+    t = OrcThermal()
+    t.gamma_heat = float(th.get("gamma_heat", 2e-26))
+    t.z = float(th.get("z", 0.02))
+    t.rate_unit = float(th["rate_unit"])
+    t.cap = float(th.get("cap", 0.1))
+    t.nh_per_rho = float(th["nh_per_rho"])
+    t.t_per_pr = float(th["t_per_pr"])
+    return t
+
+
+def cooling(T, z: float = 0.02):
+    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    lam = np.empty_like(T)
+    slope = np.empty_like(T)
+    lib().orc_cooling(T.size, _p(T), float(z), _p(lam), _p(slope))
+    return lam, slope
+
+
+def thermal_cells(T0, nh, ce, dt, th: dict):
+    """Backward-Euler thermal integration of independent cells; returns (T, status)."""
+    arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), np.shape(T0))).copy()
+            for a in (T0, nh, ce, dt)]
+    out = np.empty_like(arrs[0])
+    st = np.zeros(arrs[0].shape, dtype=np.int32)
+    t = thermal_struct(th)
+    lib().orc_thermal_cells(out.size, *[_p(a) for a in arrs], C.byref(t), _p(out),
+                            st.ctypes.data_as(C.POINTER(C.c_int)))
+    return out, st
+
+
+def thermal_apply(st, dt: float, th: dict):
+    """Operator-split thermal update of a State (returns a new State and the status bits)."""
+    U, Bx, By, Bz = _copy_state(st)
+    g = st.geom
+    t = thermal_struct(th)
+    rc = lib().orc_thermal_apply(g.nx, g.ny, g.nz, g.gamma, C.byref(t), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
+    return st.replace(U=U), int(rc)
+
+
+# --------------------------------------------------------------------- MLP ----
+HIDDEN = 64
+
+
+def mlp_forward(X, params):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    W1, b1, W2, b2, w3, b3 = [np.ascontiguousarray(params[k], dtype=np.float64) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]
+    Y = np.empty(X.shape[0])
+    lib().orc_mlp_forward(X.shape[0], _p(X), _p(W1), _p(b1), _p(W2), _p(b2), _p(w3), _p(b3), _p(Y))
+    return Y
+
+
+def mlp_backward(X, T, params):
+    """(loss, grads) with grads keyed like params."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    P = {k: np.ascontiguousarray(params[k], dtype=np.float64) for k in ("W1", "b1", "W2", "b2", "w3", "b3")}
+    G = {k: np.zeros_like(v) for k, v in P.items()}
+    loss = lib().orc_mlp_backward(X.shape[0], _p(X), _p(T), _p(P["W1"]), _p(P["b1"]), _p(P["W2"]), _p(P["b2"]),
+                                  _p(P["w3"]), _p(P["b3"]), _p(G["W1"]), _p(G["b1"]), _p(G["W2"]), _p(G["b2"]),
+                                  _p(G["w3"]), _p(G["b3"]))
+    return float(loss), G

@@ -10,9 +10,20 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <fstream>
+#include <map>
+#include <sstream>
+
 #include "mhd.h"
 #include "mhd_backend.h"
 #include "mhd_device.cuh"
+#include "mhd_persistent.cuh"
+#include "mhd_thermal.cuh"
+#include "mhd_thermal_launch.h"
+#include "mhd_mlp.cuh"
+#include "mhd_mlp_launch.h"
+#include <random>
 
 using namespace mhd;
 
@@ -66,6 +77,30 @@ struct mhd_ctx {
   ProfRec prof{};
   double prof_ms[KC_COUNT] = {0};
   long long prof_n[KC_COUNT] = {0};
+  // persistent batched mode
+  bool persistent = false;
+  int TX = 32, TY = 8;
+  double occ = 1.0;
+  int blocks = 0;
+  PatchDev* dP = nullptr;
+  BoxDev* dBox = nullptr;
+  long long* dPre = nullptr;
+  unsigned int* bar = nullptr;
+  double wait_limit_ms = 2000.0;
+  int phantom = 0;
+  ThermalDev thermal{};
+  unsigned long long* therm_stats = nullptr;
+  // surrogate
+  float* mlp = nullptr;  // params | grads | adam m | adam v | loss (4 * kNParam + 1 floats)
+  __nv_bfloat16* w2h = nullptr;
+  float* dataset = nullptr;
+  unsigned long long* ds_count = nullptr;
+  long long ds_cap = 0;
+  MlpDev mdev{};
+  bool trained = false;
+  int* fb_list = nullptr;
+  unsigned long long* fb_count = nullptr;
+  int sms = 152;
   std::string last_error;
 };
 
@@ -96,6 +131,17 @@ static void free_ctx(mhd_ctx* ctx) {
     if (p.state) cudaFree(p.state);
     if (p.scratch) cudaFree(p.scratch);
   }
+  if (ctx->therm_stats) cudaFree(ctx->therm_stats);
+  if (ctx->mlp) cudaFree(ctx->mlp);
+  if (ctx->w2h) cudaFree(ctx->w2h);
+  if (ctx->dataset) cudaFree(ctx->dataset);
+  if (ctx->ds_count) cudaFree(ctx->ds_count);
+  if (ctx->fb_list) cudaFree(ctx->fb_list);
+  if (ctx->fb_count) cudaFree(ctx->fb_count);
+  if (ctx->dP) cudaFree(ctx->dP);
+  if (ctx->dBox) cudaFree(ctx->dBox);
+  if (ctx->dPre) cudaFree(ctx->dPre);
+  if (ctx->bar) cudaFree(ctx->bar);
   if (ctx->cfl_min) cudaFree(ctx->cfl_min);
   if (ctx->dt_used) cudaFree(ctx->dt_used);
   if (ctx->err) cudaFree(ctx->err);
@@ -148,7 +194,131 @@ static int flush_profile(mhd_ctx* ctx) {
   return MHD_OK;
 }
 
+static void drop_graph(mhd_ctx* ctx) {
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+}
+
+// Work tables of the persistent step for tiles of TX x TY points: patches largest first,
+// per patch the five index boxes (recovery, fluxes x/y/z, edges) and per phase the prefix
+// sums of tile counts.  The grid is occ * (max resident CTAs per SM) * SMs.
+static int build_tables(mhd_ctx* ctx, int TX, int TY, double occ) {
+  const int np = ctx->np;
+  std::vector<int> order(np);
+  for (int p = 0; p < np; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return ctx->P[a].ncell > ctx->P[b].ncell; });
+  std::vector<PatchDev> hp(np);
+  std::vector<BoxDev> hb((size_t)np * NBOX);
+  std::vector<long long> pre(3 * (size_t)(np + 1), 0);
+  for (int q = 0; q < np; ++q) {
+    const PatchDev& D = ctx->P[order[q]].dev;
+    hp[q] = D;
+    for (int b = 0; b < NBOX; ++b) {
+      BoxDev& B = hb[(size_t)q * NBOX + b];
+      for (int a = 0; a < 3; ++a) {
+        if (b == BOX_PRIM) {
+          B.lo[a] = -D.g2[a];
+          B.ext[a] = D.n[a] + 2 * D.g2[a];
+        } else if (b == BOX_EDGE) {
+          B.lo[a] = 0;
+          B.ext[a] = D.act[a] ? D.n[a] + 1 : 1;
+        } else {
+          const int d = b - BOX_FLUX0;
+          if (a == d) {
+            B.lo[a] = 0;
+            B.ext[a] = D.n[a] + 1;
+          } else if (D.act[a]) {
+            B.lo[a] = -1;
+            B.ext[a] = D.n[a] + 2;
+          } else {
+            B.lo[a] = 0;
+            B.ext[a] = 1;
+          }
+        }
+      }
+      const bool live = b < BOX_FLUX0 || b == BOX_EDGE || D.act[b - BOX_FLUX0];
+      B.ntx = (B.ext[0] + TX - 1) / TX;
+      B.nty = (B.ext[1] + TY - 1) / TY;
+      B.count = live ? (long long)B.ntx * B.nty * B.ext[2] : 0;
+    }
+    const BoxDev* bx = &hb[(size_t)q * NBOX];
+    pre[0 * (np + 1) + q + 1] = pre[0 * (np + 1) + q] + bx[BOX_PRIM].count;
+    pre[1 * (np + 1) + q + 1] = pre[1 * (np + 1) + q] + bx[1].count + bx[2].count + bx[3].count;
+    pre[2 * (np + 1) + q + 1] = pre[2 * (np + 1) + q] + bx[BOX_EDGE].count;
+  }
+  if (!ctx->dP) {
+    if (cudaMalloc(&ctx->dP, sizeof(PatchDev) * np) != cudaSuccess ||
+        cudaMalloc(&ctx->dBox, sizeof(BoxDev) * NBOX * (size_t)np) != cudaSuccess ||
+        cudaMalloc(&ctx->dPre, sizeof(long long) * 3 * (size_t)(np + 1)) != cudaSuccess ||
+        cudaMalloc(&ctx->bar, 2 * sizeof(unsigned int)) != cudaSuccess)
+      return fail(ctx, MHD_ERR_NOMEM, "persistent tables");
+  }
+  CK(cudaMemcpyAsync(ctx->dP, hp.data(), sizeof(PatchDev) * np, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dBox, hb.data(), sizeof(BoxDev) * hb.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dPre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int per_sm = 0, sms = 0, dev = 0;
+  if (ctx->be.occupancy(TX * TY, &per_sm) || per_sm < 1) return fail(ctx, MHD_ERR_ARG, "tile too large");
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int use = (int)(per_sm * occ + 0.5);
+  if (use < 1) use = 1;
+  ctx->blocks = use * sms;
+  ctx->TX = TX;
+  ctx->TY = TY;
+  ctx->occ = occ;
+  drop_graph(ctx);
+  return MHD_OK;
+}
+
+static int issue_persistent_step(mhd_ctx* ctx, double dt) {
+  CK(cudaMemsetAsync(ctx->cfl_min, 0xFF, sizeof(unsigned long long) * ctx->np, ctx->stream));
+  CK(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned int), ctx->stream));
+  PersistentArgs A{};
+  A.P = ctx->dP;
+  A.box = ctx->dBox;
+  A.pre_prim = ctx->dPre;
+  A.pre_flux = ctx->dPre + (ctx->np + 1);
+  A.pre_edge = ctx->dPre + 2 * (ctx->np + 1);
+  A.np = ctx->np;
+  A.TX = ctx->TX;
+  A.TY = ctx->TY;
+  A.dt_host = dt;
+  A.cfl = ctx->cfl;
+  A.src = ctx->src;
+  A.bar = ctx->bar;
+  A.err = ctx->err;
+  A.limit_ns = (unsigned long long)(ctx->wait_limit_ms * 1e6);
+  A.phantom = ctx->phantom;
+  ProfScope ps(ctx->profiling && ctx->prof.n < ProfRec::kMax ? &ctx->prof : nullptr, KC_PERSISTENT, ctx->stream);
+  if (ctx->be.persistent(A, ctx->blocks, ctx->stream, &ctx->launches))
+    return cuda_fail(ctx, cudaGetLastError(), "persistent launch");
+  return MHD_OK;
+}
+
+static int issue_thermal_all(mhd_ctx* ctx) {
+  if (ctx->thermal.mode == TH_OFF) return MHD_OK;
+  for (auto& p : ctx->P) {
+    ProfScope ps(ctx->profiling && ctx->prof.n < ProfRec::kMax ? &ctx->prof : nullptr, KC_THERMAL, ctx->stream);
+    int rc = ctx->thermal.mode == TH_SURROGATE
+                 ? issue_surrogate(p.dev, ctx->thermal, ctx->mdev, ctx->fb_list, ctx->fb_count, ctx->sms,
+                                   ctx->stream, &ctx->launches)
+                 : issue_thermal(p.dev, ctx->thermal, ctx->stream, &ctx->launches);
+    if (rc) return cuda_fail(ctx, cudaGetLastError(), "thermal launch");
+  }
+  return MHD_OK;
+}
+
 static int issue_step(mhd_ctx* ctx, double dt) {
+  if (ctx->persistent) {
+    int rc = issue_persistent_step(ctx, dt);
+    if (rc == MHD_OK) rc = issue_thermal_all(ctx);
+    if (rc == MHD_OK && ctx->profiling) return flush_profile(ctx);
+    return rc;
+  }
   CK(cudaMemsetAsync(ctx->cfl_min, 0xFF, sizeof(unsigned long long) * ctx->np, ctx->stream));
   StageArgs a{};
   a.dt_host = dt;
@@ -165,6 +335,8 @@ static int issue_step(mhd_ctx* ctx, double dt) {
         return cuda_fail(ctx, cudaGetLastError(), "stage launch");
     }
   }
+  int rc = issue_thermal_all(ctx);
+  if (rc) return rc;
   if (ctx->profiling) return flush_profile(ctx);
   return MHD_OK;
 }
@@ -184,6 +356,12 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
   ctx->flags = g->flags;
   ctx->cfl = g->cfl;
   ctx->be = g->precision == MHD_PREC_FP64 ? backend_fp64() : backend_mixed();
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      ctx->sms = sms;
+  }
   auto bail = [&](int code) {
     free_ctx(ctx);
     return code;
@@ -223,6 +401,11 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
       D.lo[a] = lo[a];
     }
     D.gamma = d.gamma;
+    D.gm1 = d.gamma - 1.0;
+    D.hgm1 = 0.5 * D.gm1;
+    D.egm1 = 0.125 * D.gm1;
+    D.gamma_f = (float)d.gamma;
+    for (int a = 0; a < 3; ++a) D.d_f[a] = (float)dd[a];
     D.PX = (int)round_up(n[0] + 1, 4);
     D.PY = n[1] + 1;
     D.PZ = n[2] + 1;
@@ -262,6 +445,10 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
   for (int p = 0; p < ctx->np; ++p) {
     int rc = mhd_set_state(ctx, p, U0[p], B0[p], on_device);
     if (rc) return bail(rc);
+  }
+  if (g->flags & MHD_FLAG_PERSISTENT) {
+    ctx->persistent = true;
+    if (build_tables(ctx, 32, 8, 1.0)) return bail(MHD_ERR_CUDA);
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(MHD_ERR_CUDA);
   *out = ctx;
@@ -421,6 +608,309 @@ int mhd_get_metrics(mhd_ctx* ctx, mhd_metrics* m) {
 
 long long mhd_launch_count(const mhd_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int mhd_set_thermal(mhd_ctx* ctx, const mhd_thermal_desc* d) {
+  if (!ctx || !d) return MHD_ERR_ARG;
+  if (d->mode != MHD_THERMAL_OFF && d->mode != MHD_THERMAL_PLAIN && d->mode != MHD_THERMAL_SURROGATE)
+    return fail(ctx, MHD_ERR_ARG, "unknown thermal mode");
+  if (d->mode != MHD_THERMAL_OFF &&
+      (!(d->rate_unit > 0.0) || !(d->nh_per_rho > 0.0) || !(d->t_per_pr > 0.0) || !(d->cap > 0.0) ||
+       !(d->cap <= 1.0) || d->gamma_heat < 0.0 || d->z < 0.0))
+    return fail(ctx, MHD_ERR_ARG, "thermal parameters out of range");
+  if (!ctx->therm_stats) {
+    if (cudaMalloc(&ctx->therm_stats, 4 * sizeof(unsigned long long)) != cudaSuccess)
+      return fail(ctx, MHD_ERR_NOMEM, "thermal counters");
+    CK(cudaMemsetAsync(ctx->therm_stats, 0, 4 * sizeof(unsigned long long), ctx->stream));
+  }
+  if (d->mode == MHD_THERMAL_SURROGATE && !ctx->trained)
+    return fail(ctx, MHD_ERR_STATE, "surrogate mode needs a trained network (mhd_surrogate_train)");
+  if (d->mode == MHD_THERMAL_SURROGATE && !ctx->fb_list) {
+    long long maxc = 0;
+    for (auto& p : ctx->P) maxc = p.ncell > maxc ? p.ncell : maxc;
+    if (cudaMalloc(&ctx->fb_list, sizeof(int) * (size_t)maxc) != cudaSuccess ||
+        cudaMalloc(&ctx->fb_count, sizeof(unsigned long long)) != cudaSuccess)
+      return fail(ctx, MHD_ERR_NOMEM, "fallback list");
+  }
+  ctx->thermal.mode = d->mode;
+  ctx->thermal.gamma_heat = d->gamma_heat;
+  ctx->thermal.z = d->z;
+  ctx->thermal.rate_unit = d->rate_unit;
+  ctx->thermal.cap = d->cap;
+  ctx->thermal.nh_per_rho = d->nh_per_rho;
+  ctx->thermal.t_per_pr = d->t_per_pr;
+  ctx->thermal.stats = ctx->therm_stats;
+  drop_graph(ctx);
+  return MHD_OK;
+}
+
+static int ensure_mlp(mhd_ctx* ctx) {
+  if (ctx->mlp) return MHD_OK;
+  if (cudaMalloc(&ctx->mlp, sizeof(float) * (4 * (size_t)kNParam + 1)) != cudaSuccess ||
+      cudaMalloc(&ctx->w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess)
+    return fail(ctx, MHD_ERR_NOMEM, "surrogate parameters");
+  CK(cudaMemsetAsync(ctx->mlp, 0, sizeof(float) * (4 * (size_t)kNParam + 1), ctx->stream));
+  ctx->mdev.p = ctx->mlp;
+  ctx->mdev.W2h = ctx->w2h;
+  return MHD_OK;
+}
+
+int mhd_surrogate_harvest(mhd_ctx* ctx, long long capacity, int stride) {
+  if (!ctx || capacity < 0 || stride < 1) return MHD_ERR_ARG;
+  if (capacity == 0) {
+    ctx->thermal.hv_data = nullptr;
+    drop_graph(ctx);
+    return MHD_OK;
+  }
+  if (ctx->dataset && capacity != ctx->ds_cap) {
+    cudaFree(ctx->dataset);
+    ctx->dataset = nullptr;
+  }
+  if (!ctx->dataset && cudaMalloc(&ctx->dataset, sizeof(float) * 5 * (size_t)capacity) != cudaSuccess)
+    return fail(ctx, MHD_ERR_NOMEM, "harvest buffer");
+  if (!ctx->ds_count && cudaMalloc(&ctx->ds_count, sizeof(unsigned long long)) != cudaSuccess)
+    return fail(ctx, MHD_ERR_NOMEM, "harvest counter");
+  CK(cudaMemsetAsync(ctx->ds_count, 0, sizeof(unsigned long long), ctx->stream));
+  ctx->ds_cap = capacity;
+  ctx->thermal.hv_data = ctx->dataset;
+  ctx->thermal.hv_count = ctx->ds_count;
+  ctx->thermal.hv_cap = capacity;
+  ctx->thermal.hv_stride = stride;
+  drop_graph(ctx);
+  return MHD_OK;
+}
+
+int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double dmax,
+                        double* loss_out, long long* rows_out) {
+  if (!ctx || epochs < 1 || batch < 64 || batch > (1 << 20) || !(lr > 0.0) || seed == 0) return MHD_ERR_ARG;
+  if (!ctx->dataset || !ctx->ds_count) return fail(ctx, MHD_ERR_STATE, "no harvested training pairs");
+  int rc = ensure_mlp(ctx);
+  if (rc) return rc;
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, ctx->ds_count, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const long long rows = (long long)(cnt < (unsigned long long)ctx->ds_cap ? cnt : (unsigned long long)ctx->ds_cap);
+  if (rows < 64) return fail(ctx, MHD_ERR_STATE, "fewer than 64 harvested training pairs");
+  // feature range of the training set (the surrogate's validity domain)
+  std::vector<float> host((size_t)rows * 5);
+  CK(cudaMemcpy(host.data(), ctx->dataset, sizeof(float) * host.size(), cudaMemcpyDeviceToHost));
+  float lo[4], hi[4], ymax = 0.f;
+  for (int f = 0; f < 4; ++f) lo[f] = hi[f] = host[f];
+  for (long long r = 0; r < rows; ++r) {
+    for (int f = 0; f < 4; ++f) {
+      lo[f] = std::min(lo[f], host[r * 5 + f]);
+      hi[f] = std::max(hi[f], host[r * 5 + f]);
+    }
+    ymax = std::max(ymax, std::fabs(host[r * 5 + 4]));
+  }
+  // standardisation range: the training range, widened to at least 0.2 (a fifth of a
+  // decade for the logarithmic features) so that a nearly constant feature such as log dt
+  // is not stretched over [-1, 1]
+  for (int f = 0; f < 4; ++f) {
+    const float wmin = 0.2f, w = hi[f] - lo[f];
+    if (w < wmin) {
+      lo[f] -= 0.5f * (wmin - w);
+      hi[f] += 0.5f * (wmin - w);
+    }
+    ctx->mdev.xlo[f] = lo[f];
+    ctx->mdev.xscale[f] = 2.0f / (hi[f] - lo[f]);
+  }
+  ctx->mdev.dmax = dmax > 0.0 ? (float)dmax : ymax;
+  // initial weights: uniform(-a, a) with a = sqrt(6/(fan_in + fan_out)), seeded
+  std::vector<float> p0(kNParam, 0.f);
+  std::mt19937_64 gen(seed);
+  auto fill = [&](int off, int n, int fin, int fout) {
+    const double a = std::sqrt(6.0 / (fin + fout));
+    std::uniform_real_distribution<double> U(-a, a);
+    for (int q = 0; q < n; ++q) p0[off + q] = (float)U(gen);
+  };
+  fill(kOffW1, kHid * 4, 4, kHid);
+  fill(kOffW2, kHid * kHid, kHid, kHid);
+  fill(kOffW3, kHid, kHid, 1);
+  CK(cudaMemcpyAsync(ctx->mlp, p0.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->mlp + kNParam, 0, sizeof(float) * (3 * (size_t)kNParam + 1), ctx->stream));
+  if (mlp_refresh(ctx->mlp, ctx->w2h, ctx->stream)) return cuda_fail(ctx, cudaGetLastError(), "refresh");
+  float* grad = ctx->mlp + kNParam;
+  float* m = grad + kNParam;
+  float* v = m + kNParam;
+  float* loss = v + kNParam;
+  const long long steps_per_epoch = std::max<long long>(1, rows / batch);
+  const long long total = steps_per_epoch * epochs;
+  for (long long stp = 0; stp < total; ++stp) {
+    CK(cudaMemsetAsync(grad, 0, sizeof(float) * kNParam, ctx->stream));
+    if (stp == total - steps_per_epoch) CK(cudaMemsetAsync(loss, 0, sizeof(float), ctx->stream));
+    // cosine decay of the learning rate from lr to lr/20 over the run
+    const double lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * (double)stp / (double)total)));
+    if (mlp_grad(ctx->mdev, ctx->dataset, rows, seed, stp, batch, grad, loss, ctx->stream) ||
+        mlp_adam(ctx->mlp, grad, m, v, (float)lr_t, stp + 1, ctx->w2h, ctx->stream))
+      return cuda_fail(ctx, cudaGetLastError(), "training launch");
+    ctx->launches += 2;
+  }
+  float lsum = 0.f;
+  CK(cudaMemcpyAsync(&lsum, loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (loss_out) *loss_out = lsum / (double)(steps_per_epoch * batch);
+  if (rows_out) *rows_out = rows;
+  ctx->trained = true;
+  ctx->thermal.hv_data = nullptr;  // harvesting ends with training
+  drop_graph(ctx);
+  return MHD_OK;
+}
+
+int mhd_surrogate_params(mhd_ctx* ctx, float* params_out, float* range_out) {
+  if (!ctx || !params_out) return MHD_ERR_ARG;
+  if (!ctx->mlp) return fail(ctx, MHD_ERR_STATE, "no surrogate");
+  CK(cudaMemcpyAsync(params_out, ctx->mlp, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (range_out) {
+    for (int f = 0; f < 4; ++f) {
+      range_out[f] = ctx->mdev.xlo[f];
+      range_out[4 + f] = ctx->mdev.xscale[f];
+    }
+    range_out[8] = ctx->mdev.dmax;
+  }
+  return MHD_OK;
+}
+
+int mhd_thermal_stats(mhd_ctx* ctx, unsigned long long* out4) {
+  if (!ctx || !out4) return MHD_ERR_ARG;
+  if (!ctx->therm_stats) {
+    for (int q = 0; q < 4; ++q) out4[q] = 0;
+    return MHD_OK;
+  }
+  CK(cudaMemcpyAsync(out4, ctx->therm_stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MHD_OK;
+}
+
+int mhd_set_wait_limit(mhd_ctx* ctx, double limit_ms, int phantom_blocks) {
+  if (!ctx || !(limit_ms > 0.0) || phantom_blocks < 0) return MHD_ERR_ARG;
+  ctx->wait_limit_ms = limit_ms;
+  ctx->phantom = phantom_blocks;
+  drop_graph(ctx);
+  return MHD_OK;
+}
+
+namespace {
+struct TuneEntry {
+  int TX, TY;
+  double occ, ms;
+};
+
+std::map<std::string, TuneEntry> read_cache(const char* path) {
+  std::map<std::string, TuneEntry> m;
+  if (!path) return m;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t a = line.find('"');
+    if (a == std::string::npos) continue;
+    const size_t b = line.find('"', a + 1);
+    const size_t c = line.find("\"TX\":", b);
+    if (b == std::string::npos || c == std::string::npos) continue;
+    TuneEntry e{};
+    if (sscanf(line.c_str() + c, "\"TX\": %d, \"TY\": %d, \"occ\": %lf, \"ms\": %lf", &e.TX, &e.TY, &e.occ,
+               &e.ms) == 4)
+      m[line.substr(a + 1, b - a - 1)] = e;
+  }
+  return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, TuneEntry>& m) {
+  if (!path) return;
+  std::ofstream f(path);
+  f << "{\n";
+  size_t i = 0;
+  for (const auto& kv : m) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "{\"TX\": %d, \"TY\": %d, \"occ\": %.3f, \"ms\": %.6f}", kv.second.TX,
+             kv.second.TY, kv.second.occ, kv.second.ms);
+    f << "\"" << kv.first << "\": " << buf << (++i < m.size() ? ",\n" : "\n");
+  }
+  f << "}\n";
+}
+}  // namespace
+
+int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out) {
+  if (!ctx) return MHD_ERR_ARG;
+  if (!ctx->persistent) return fail(ctx, MHD_ERR_STATE, "autotune needs MHD_FLAG_PERSISTENT");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  std::ostringstream key;
+  key << prop.name << "|" << (ctx->precision == MHD_PREC_FP64 ? "fp64" : "mixed") << "|";
+  for (auto& p : ctx->P) key << p.desc.nx << "x" << p.desc.ny << "x" << p.desc.nz << ",";
+  std::string k = key.str();
+  auto cache = read_cache(cache_path);
+  auto it = cache.find(k);
+  if (!force && it != cache.end()) {
+    int rc = build_tables(ctx, it->second.TX, it->second.TY, it->second.occ);
+    if (tile_out) {
+      tile_out[0] = ctx->TX;
+      tile_out[1] = ctx->TY;
+    }
+    return rc;
+  }
+  // keep the state: every candidate runs the same steps from it
+  std::vector<double*> backup(ctx->np, nullptr);
+  for (int p = 0; p < ctx->np; ++p) {
+    const size_t bytes = sizeof(double) * 8 * (size_t)ctx->P[p].dev.FS;
+    if (cudaMalloc(&backup[p], bytes) != cudaSuccess) {
+      for (auto b : backup)
+        if (b) cudaFree(b);
+      return fail(ctx, MHD_ERR_NOMEM, "autotune backup");
+    }
+    CK(cudaMemcpyAsync(backup[p], ctx->P[p].dev.Un, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  auto restore = [&]() {
+    for (int p = 0; p < ctx->np; ++p)
+      cudaMemcpyAsync(ctx->P[p].dev.Un, backup[p], sizeof(double) * 8 * (size_t)ctx->P[p].dev.FS,
+                      cudaMemcpyDeviceToDevice, ctx->stream);
+  };
+  const int cand[][2] = {{32, 4}, {32, 8}, {64, 4}, {16, 16}, {32, 16}, {64, 8}, {128, 2}, {128, 4}};
+  const double occs[] = {1.0, 0.5};
+  TuneEntry best{32, 8, 1.0, 1e300};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool was_prof = ctx->profiling;
+  ctx->profiling = false;
+  for (auto& c : cand) {
+    for (double oc : occs) {
+      if (build_tables(ctx, c[0], c[1], oc)) continue;
+      restore();
+      if (issue_persistent_step(ctx, -1.0)) continue;
+      CK(cudaEventRecord(e0, ctx->stream));
+      for (int r = 0; r < 3; ++r) issue_persistent_step(ctx, -1.0);
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      int h = 0;
+      CK(cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h) break;
+      if (ms / 3.0 < best.ms) best = TuneEntry{c[0], c[1], oc, ms / 3.0};
+    }
+  }
+  ctx->profiling = was_prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  restore();
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto b : backup) cudaFree(b);
+  int h = 0;
+  CK(cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) return read_error_word(ctx);
+  int rc = build_tables(ctx, best.TX, best.TY, best.occ);
+  if (rc) return rc;
+  cache[k] = best;
+  write_cache(cache_path, cache);
+  if (tile_out) {
+    tile_out[0] = ctx->TX;
+    tile_out[1] = ctx->TY;
+  }
+  return MHD_OK;
+}
+
 int mhd_set_profiling(mhd_ctx* ctx, int on) {
   if (!ctx) return MHD_ERR_ARG;
   if (on && !ctx->profiling) {
@@ -464,6 +954,77 @@ void mhd_destroy(mhd_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   free_ctx(ctx);
+}
+
+static MlpDev unit_mlp(const float* params, __nv_bfloat16* w2h) {
+  MlpDev M{};
+  M.p = params;
+  M.W2h = w2h;
+  for (int f = 0; f < 4; ++f) {
+    M.xlo[f] = -1.0f;  // identity standardisation: inputs are already in [-1, 1]
+    M.xscale[f] = 1.0f;
+  }
+  M.dmax = 1e30f;
+  return M;
+}
+
+int mhd_mlp_forward(long long n, const float* xs, const float* params, float* y, void* stream) {
+  if (n < 0 || !params || (n > 0 && (!xs || !y))) return MHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  static __nv_bfloat16* w2h = nullptr;  // per-process BF16 scratch of the unit entry
+  if (!w2h && cudaMalloc(&w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess) return MHD_ERR_NOMEM;
+  if (mlp_refresh(params, w2h, s) || mlp_forward(n, xs, unit_mlp(params, w2h), y, s)) return MHD_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
+}
+
+int mhd_mlp_forward_tc(long long n, const float* xs, const float* params, float* y, void* stream) {
+  if (n < 0 || !params || (n > 0 && (!xs || !y))) return MHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  static __nv_bfloat16* w2h = nullptr;
+  static int* err = nullptr;
+  if (!w2h && cudaMalloc(&w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess) return MHD_ERR_NOMEM;
+  if (!err && cudaMalloc(&err, sizeof(int)) != cudaSuccess) return MHD_ERR_NOMEM;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (mlp_refresh(params, w2h, s) || mlp_forward_tc(n, xs, params, w2h, y, err, sms, s)) return MHD_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MHD_ERR_CUDA;
+  return h ? MHD_ERR_TIMEOUT : MHD_OK;
+}
+
+int mhd_mlp_grad(long long n, const float* rows, const float* params, float* grad, float* loss_sum, void* stream) {
+  if (n < 1 || n > (1 << 20) || !rows || !params || !grad || !loss_sum) return MHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  static __nv_bfloat16* w2h = nullptr;
+  if (!w2h && cudaMalloc(&w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess) return MHD_ERR_NOMEM;
+  if (cudaMemsetAsync(grad, 0, sizeof(float) * kNParam, s) != cudaSuccess ||
+      cudaMemsetAsync(loss_sum, 0, sizeof(float), s) != cudaSuccess)
+    return MHD_ERR_CUDA;
+  if (mlp_refresh(params, w2h, s) || mlp_grad(unit_mlp(params, w2h), rows, n, 0ull, 0, (int)n, grad, loss_sum, s))
+    return MHD_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
+}
+
+int mhd_thermal_cells(long long n, const double* T0, const double* nh, const double* ce, const double* dt,
+                      const mhd_thermal_desc* d, double* T_out, int* status, void* stream) {
+  if (n < 0 || !d || (n > 0 && (!T0 || !nh || !ce || !dt || !T_out))) return MHD_ERR_ARG;
+  if (!(d->rate_unit > 0.0) || !(d->cap > 0.0) || !(d->cap <= 1.0)) return MHD_ERR_ARG;
+  ThermalDev th{};
+  th.mode = MHD_THERMAL_PLAIN;
+  th.gamma_heat = d->gamma_heat;
+  th.z = d->z;
+  th.rate_unit = d->rate_unit;
+  th.cap = d->cap;
+  th.nh_per_rho = d->nh_per_rho;
+  th.t_per_pr = d->t_per_pr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (issue_thermal_cells(n, T0, nh, ce, dt, th, T_out, status, s)) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  return MHD_OK;
 }
 
 int mhd_riemann_hlld(int n, const double* wl, const double* wr, const double* bn, double gamma,

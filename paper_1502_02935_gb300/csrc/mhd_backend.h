@@ -6,9 +6,11 @@
 namespace mhd {
 struct PatchDev;
 struct StageArgs;
+struct PersistentArgs;
 
 // Optional per-launch CUDA-event pairs recorded on the launching stream.
-enum { KC_PRIM = 0, KC_FLUX1 = 1, KC_FLUX2 = 4, KC_EMF = 7, KC_UPDATE = 8, KC_CFL = 9, KC_COUNT = 10 };
+enum { KC_PRIM = 0, KC_FLUX1 = 1, KC_FLUX2 = 4, KC_EMF = 7, KC_UPDATE = 8, KC_CFL = 9, KC_PERSISTENT = 10,
+       KC_THERMAL = 11, KC_COUNT = 12 };
 struct ProfRec {
   static constexpr int kMax = 64;
   cudaEvent_t a[kMax], b[kMax];
@@ -40,6 +42,9 @@ struct Backend {
   int (*cfl)(const PatchDev&, cudaStream_t, long long* launches);
   int (*hlld)(int n, const double* wl, const double* wr, const double* bn, double gamma,
               double* flux, cudaStream_t s);
+  // one whole step of every patch in one cooperative launch of `blocks` CTAs
+  int (*persistent)(const PersistentArgs&, int blocks, cudaStream_t, long long* launches);
+  int (*occupancy)(int block, int* blocks_per_sm);
 };
 
 Backend backend_fp64();

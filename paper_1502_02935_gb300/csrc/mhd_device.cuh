@@ -38,6 +38,8 @@ struct PatchDev {
   int QX, QY, QZ;
   long long QS;  // scratch field stride
   double d[3], inv_d[3], lo[3], gamma;
+  double gm1, hgm1, egm1;  // gamma - 1, (gamma - 1)/2, (gamma - 1)/8
+  float gamma_f, d_f[3];   // FP32 copies for the mixed path
   double* Un;
   double* Uh;
   void* W;
@@ -95,19 +97,67 @@ __device__ __forceinline__ long long qstride(const PatchDev& P, int a) {
   return a == 0 ? 1LL : (a == 1 ? (long long)P.QX : (long long)P.QX * P.QY);
 }
 
+// ------------------------------------------------- FP32 <-> FP64 on the ALU --
+// On this part FP32<->FP64 conversions issue to the FP64 pipe, which is ~1/64 of the FP32
+// rate and is what bounds the recovery and update phases of the mixed path.  These two
+// conversions are done instead with integer operations on the IEEE-754 fields:
+//   binary32 -> binary64: sign kept, exponent rebiased by 1023 - 127 = 896, mantissa
+//     shifted left by 29 (exact); zero and subnormal floats give a signed zero; inf/NaN kept.
+//   binary64 -> binary32: exponent rebiased by -896, mantissa rounded to 23 bits to nearest
+//     with ties to even (the carry of the rounding may step the exponent, up to inf);
+//     magnitudes below the smallest normal float give a signed zero; inf/NaN kept.
+__device__ __forceinline__ double f2d_alu(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned hi_n = sign | ((e + 896u) << 20) | (m >> 3);
+  const unsigned hi = e == 0u ? sign : (e == 0xFFu ? (sign | 0x7FF00000u | (m >> 3)) : hi_n);
+  const unsigned lo = e == 0u ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_alu(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  const unsigned up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m23 & 1u));
+  const int ef = e - 896;
+  unsigned bits = ((unsigned)ef << 23) + m23 + up;  // a carry out of the mantissa bumps the exponent
+  bits = ef <= 0 ? 0u : (ef >= 255 ? 0x7F800000u : bits);
+  bits = bits > 0x7F800000u ? 0x7F800000u : bits;
+  if (e == 0x7FF) bits = 0x7F800000u | ((((hi & 0xFFFFFu) | lo) != 0u) ? 0x400000u : 0u);
+  return __uint_as_float(sign | bits);
+}
+
 // --------------------------------------------------------------- arithmetic --
 template <class R> struct Ar;
 template <> struct Ar<double> {
+  static __device__ __forceinline__ double from_d(double x) { return x; }
+  static __device__ __forceinline__ double to_d(double x) { return x; }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
   static constexpr double degen = 1e-8;
 };
 template <> struct Ar<float> {
+  static __device__ __forceinline__ float from_d(double x) { return d2f_alu(x); }
+  static __device__ __forceinline__ double to_d(float x) { return f2d_alu(x); }
   static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
   static constexpr float degen = 1e-8f;
+};
+
+// gamma and cell sizes in the bulk type (FP32 copies precomputed on the host)
+template <class R> struct Gam;
+template <> struct Gam<double> {
+  static __device__ __forceinline__ double get(const PatchDev& P) { return P.gamma; }
+  static __device__ __forceinline__ double d(const PatchDev& P, int a) { return P.d[a]; }
+};
+template <> struct Gam<float> {
+  static __device__ __forceinline__ float get(const PatchDev& P) { return P.gamma_f; }
+  static __device__ __forceinline__ float d(const PatchDev& P, int a) { return P.d_f[a]; }
 };
 
 // 1/rho for the FP64 pressure recovery.  FP64 path: IEEE division.  Mixed path: the
@@ -116,7 +166,7 @@ template <> struct Ar<float> {
 template <class R> __device__ __forceinline__ double inv_density(double rho);
 template <> __device__ __forceinline__ double inv_density<double>(double rho) { return 1.0 / rho; }
 template <> __device__ __forceinline__ double inv_density<float>(double rho) {
-  double r = (double)__frcp_rn((float)rho);
+  double r = f2d_alu(__frcp_rn(d2f_alu(rho)));
   double e = fma(-rho, r, 1.0);
   return fma(r, e, r);
 }
@@ -330,40 +380,44 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
   const double irho = inv_density<R>(rho);
   const double m2 = mx * mx + my * my + mz * mz;
   const double b2 = sbx * sbx + sby * sby + sbz * sbz;  // 4 |B_cc|^2
-  const double gm1 = P.gamma - 1.0;
   // p = (gamma-1) (E - |m|^2/(2 rho) - |B_cc|^2/2), in FP64
-  const double p = gm1 * e - (0.5 * gm1) * (m2 * irho) - (0.125 * gm1) * b2;
-  const R rirho = (R)irho;
-  const R vx = (R)mx * rirho, vy = (R)my * rirho, vz = (R)mz * rirho;
-  const R bx = (R)sbx * R(0.5), by = (R)sby * R(0.5), bz = (R)sbz * R(0.5);
+  const double p = P.gm1 * e - P.hgm1 * (m2 * irho) - P.egm1 * b2;
+  const R rirho = Ar<R>::from_d(irho);
+  const R vx = Ar<R>::from_d(mx) * rirho, vy = Ar<R>::from_d(my) * rirho, vz = Ar<R>::from_d(mz) * rirho;
+  const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
+  const R rr = Ar<R>::from_d(rho), pr = Ar<R>::from_d(p);
   if (store) {
     const long long q = qidx(P, i, j, k), QS = P.QS;
-    W[q] = (R)rho;
+    W[q] = rr;
     W[WVX * QS + q] = vx;
     W[WVY * QS + q] = vy;
     W[WVZ * QS + q] = vz;
-    W[WP * QS + q] = (R)p;
+    W[WP * QS + q] = pr;
     W[WBX * QS + q] = bx;
     W[WBY * QS + q] = by;
     W[WBZ * QS + q] = bz;
   }
   double lim = INFINITY;
   if (interior) {
-    if (!(isfinite(rho) && isfinite(p) && isfinite(e))) {
+    // positivity / finiteness on the bulk-type values; CFL arithmetic in the bulk type
+    if (!(isfinite(rr) && isfinite(pr) && isfinite(e))) {
       atomicOr(P.err, ERR_NONFINITE);
-    } else if (!(rho > 0.0) || !(p > 0.0)) {
+    } else if (!(rr > R(0)) || !(pr > R(0))) {
       atomicOr(P.err, ERR_NEGATIVE);
     }
     const R v[3] = {vx, vy, vz};
     const R b[3] = {bx, by, bz};
     const R bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const R gam = Gam<R>::get(P);
+    R lr = R(INFINITY);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (!P.act[a]) continue;
-      R cf = fast_speed<R>((R)rho, (R)p, bb, b[a] * b[a], (R)P.gamma);
-      double t = P.d[a] / (double)(Ar<R>::abs_(v[a]) + cf);
-      lim = t < lim ? t : lim;
+      const R cf = fast_speed<R>(rr, pr, bb, b[a] * b[a], gam);
+      const R t = Gam<R>::d(P, a) / (Ar<R>::abs_(v[a]) + cf);
+      lr = t < lr ? t : lr;
     }
+    lim = (double)lr;
   }
   return lim;
 }
@@ -407,9 +461,9 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
   int s3[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) s3[a] = (a == D) ? fmap(P, a, c3[a]) : cmap(P, a, c3[a]);
-  const R bn = (R)Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])];
+  const R bn = Ar<R>::from_d(Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])]);
   R f[8];
-  hlld<R>(wl, wr, bn, (R)P.gamma, f);
+  hlld<R>(wl, wr, bn, Gam<R>::get(P), f);
   F[q] = f[0];
   F[(1 + D) * QS + q] = f[1];
   F[(1 + T1) * QS + q] = f[2];
@@ -500,11 +554,11 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
 #pragma unroll
       for (int f = 0; f < 5; ++f) div[f] += (Fd[f * QS + q + st] - Fd[f * QS + q]) * idd;
     }
-    Uo[s] = Ub[s] - (double)(h * div[0]);
+    Uo[s] = Ub[s] - Ar<R>::to_d(h * div[0]);
     if (src.potential == POT_NONE) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - (double)(h * div[1 + a]);
-      Uo[EN * FS + s] = Ub[EN * FS + s] - (double)(h * div[4]);
+      for (int a = 0; a < 3; ++a) Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - Ar<R>::to_d(h * div[1 + a]);
+      Uo[EN * FS + s] = Ub[EN * FS + s] - Ar<R>::to_d(h * div[4]);
     } else {
       R g[3];
       grad_psi<R>(src, P.lo[0] + (i + 0.5) * P.d[0], P.lo[1] + (j + 0.5) * P.d[1],
@@ -527,7 +581,7 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
     R curl = R(0);
     if (P.act[b]) curl += (E[c * QS + q + qstride(P, b)] - E[c * QS + q]) * (R)P.inv_d[b];
     if (P.act[c]) curl -= (E[b * QS + q + qstride(P, c)] - E[b * QS + q]) * (R)P.inv_d[c];
-    Uo[(BXF + a) * FS + s] = Ub[(BXF + a) * FS + s] - (double)(h * curl);
+    Uo[(BXF + a) * FS + s] = Ub[(BXF + a) * FS + s] - Ar<R>::to_d(h * curl);
   }
 }
 

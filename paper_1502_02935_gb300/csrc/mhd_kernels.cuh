@@ -4,6 +4,7 @@
 #pragma once
 #include "mhd_backend.h"
 #include "mhd_device.cuh"
+#include "mhd_persistent.cuh"
 
 namespace mhd {
 
@@ -217,6 +218,8 @@ template <class R> Backend make_backend() {
   b.stage = &issue_stage<R>;
   b.cfl = &issue_cfl<R>;
   b.hlld = &issue_hlld<R>;
+  b.persistent = &issue_persistent<R>;
+  b.occupancy = &persistent_occupancy<R>;
   return b;
 }
 

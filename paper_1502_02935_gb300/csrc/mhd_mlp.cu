@@ -1,0 +1,377 @@
+// mhd_mlp.cu -- training and inference kernels of the thermal surrogate (mhd_mlp.cuh).
+//
+// Training: each minibatch row is drawn from the harvested set with a counter-based hash
+// of (seed, step, row); one CTA of 4 warps takes 64 rows, runs the forward pass, the
+// backward pass (the two 64x64 products of the backward pass, dW2 = dz2^T h1 and
+// dh1 = dz2 W2, also on the tensor cores) and adds its gradient contributions into one
+// FP32 gradient block.  Adam then updates the FP32 master weights and refreshes the BF16
+// copy of W2.
+//
+// Inference (thermal mode SURROGATE): per interior cell, features -> network -> change of
+// log10 T; a cell whose standardised features leave [-1, 1] or whose predicted change
+// exceeds the stated bound is appended to a fallback list that the plain FP64 integrator
+// then handles, so the divergent fallback stays out of the network kernel.
+#include <cuda_bf16.h>
+
+#include "mhd_mlp.cuh"
+#include "mhd_mlp_launch.h"
+#include "mhd_thermal.cuh"
+
+namespace mhd {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  // splitmix64 finaliser
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------------- forward --
+// Unit-level forward: standardised inputs xs[n][4] -> y[n].
+__global__ void __launch_bounds__(128) k_mlp_forward(long long n, const float* __restrict__ xs, MlpDev M,
+                                                     float* __restrict__ y) {
+  __shared__ MlpSmem S;
+  mlp_load_weights(S, M);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * 16;
+  for (long long base = (long long)blockIdx.x * kMlpRows; base < n; base += (long long)gridDim.x * kMlpRows) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kMlpRows * 4; q += blockDim.x) {
+      const long long row = base + q / 4;
+      S.x[q] = row < n ? xs[row * 4 + (q & 3)] : 0.f;
+    }
+    __syncthreads();
+    mlp_layer1(S, r0);
+    __syncwarp();
+    float acc[8][4];
+    mlp_layer2(S, r0, acc);
+    float ylo, yhi;
+    mlp_head(S, acc, ylo, yhi);
+    const int g = lane >> 2;
+    if ((lane & 3) == 0) {
+      const long long a = base + r0 + g, b = base + r0 + g + 8;
+      if (a < n) y[a] = ylo;
+      if (b < n) y[b] = yhi;
+    }
+  }
+}
+
+// -------------------------------------------------------------- train step --
+struct TrainSmem {
+  MlpSmem m;
+  __nv_bfloat16 dz2[kMlpRows * kHid];
+  float t[kMlpRows];
+  float red[kHid * 2];
+  float gw1[kHid * 4];
+  float gb1[kHid];
+};
+
+// One minibatch chunk of 64 rows: loss and gradient contributions.  rows == nullptr:
+// rows come from the dataset by hash; else they are given (xs, targets) directly.
+__global__ void __launch_bounds__(128) k_mlp_grad(MlpDev M, const float* __restrict__ data, long long nrows,
+                                                  unsigned long long seed, long long step, int batch,
+                                                  float* __restrict__ grad, float* __restrict__ loss_sum) {
+  __shared__ TrainSmem T;
+  MlpSmem& S = T.m;
+  mlp_load_weights(S, M);
+  for (int q = threadIdx.x; q < kHid * 4; q += blockDim.x) T.gw1[q] = 0.f;
+  for (int q = threadIdx.x; q < kHid; q += blockDim.x) T.gb1[q] = 0.f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * 16;
+  const int g = lane >> 2, t = lane & 3;
+  const long long base = (long long)blockIdx.x * kMlpRows;
+  // gather rows and standardise
+  for (int q = threadIdx.x; q < kMlpRows; q += blockDim.x) {
+    const long long r = base + q;
+    long long src = -1;
+    if (r < batch) src = seed ? (long long)(mix64(seed ^ mix64((unsigned long long)step * 0x100000001ull + r)) %
+                                            (unsigned long long)nrows)
+                              : r;
+    for (int f = 0; f < 4; ++f) S.x[q * 4 + f] = src >= 0 ? mlp_standardize(M, f, data[src * 5 + f]) : 0.f;
+    T.t[q] = src >= 0 ? data[src * 5 + 4] : 0.f;
+  }
+  __syncthreads();
+  mlp_layer1(S, r0);
+  __syncwarp();
+  float acc[8][4];
+  mlp_layer2(S, r0, acc);
+  float ylo, yhi;
+  mlp_head(S, acc, ylo, yhi);  // acc now holds h2
+  const long long ra = base + r0 + g, rb = ra + 8;
+  const float inv_b = 1.0f / (float)batch;
+  const float dya = ra < batch ? 2.0f * (ylo - T.t[r0 + g]) * inv_b : 0.f;
+  const float dyb = rb < batch ? 2.0f * (yhi - T.t[r0 + g + 8]) * inv_b : 0.f;
+  if (t == 0) {
+    float l = 0.f;
+    if (ra < batch) l += (ylo - T.t[r0 + g]) * (ylo - T.t[r0 + g]);
+    if (rb < batch) l += (yhi - T.t[r0 + g + 8]) * (yhi - T.t[r0 + g + 8]);
+    if (l != 0.f) atomicAdd(loss_sum, l);
+  }
+  // output layer: gw3, gb3; dz2 = dy w3 (1 - h2^2)
+  float gb2p[16], gw3p[16];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = nt * 8 + 2 * t + h;
+      const float h2a = acc[nt][h], h2b = acc[nt][2 + h];
+      gw3p[nt * 2 + h] = dya * h2a + dyb * h2b;
+      const float dza = dya * S.w3[c] * (1.f - h2a * h2a);
+      const float dzb = dyb * S.w3[c] * (1.f - h2b * h2b);
+      gb2p[nt * 2 + h] = dza + dzb;
+      T.dz2[(r0 + g) * kHid + c] = __float2bfloat16_rn(dza);
+      T.dz2[(r0 + g + 8) * kHid + c] = __float2bfloat16_rn(dzb);
+    }
+  }
+  // reduce gw3 / gb2 over the 8 row groups of the warp, then across warps
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      gw3p[q] += __shfl_xor_sync(0xffffffffu, gw3p[q], o);
+      gb2p[q] += __shfl_xor_sync(0xffffffffu, gb2p[q], o);
+    }
+  }
+  for (int q = threadIdx.x; q < 2 * kHid; q += blockDim.x) T.red[q] = 0.f;
+  float db3 = t == 0 ? dya + dyb : 0.f;  // the four lanes of a quad hold the same two rows
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) db3 += __shfl_xor_sync(0xffffffffu, db3, o);
+  __syncthreads();
+  if (g == 0) {
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        atomicAdd(&T.red[nt * 8 + 2 * t + h], gw3p[nt * 2 + h]);
+        atomicAdd(&T.red[kHid + nt * 8 + 2 * t + h], gb2p[nt * 2 + h]);
+      }
+  }
+  if (lane == 0) atomicAdd(grad + kOffB3, db3);
+  __syncthreads();
+  for (int q = threadIdx.x; q < kHid; q += blockDim.x) {
+    atomicAdd(grad + kOffW3 + q, T.red[q]);
+    atomicAdd(grad + kOffB2 + q, T.red[kHid + q]);
+  }
+  // dW2[out][in] = sum_rows dz2[row][out] h1[row][in]: warp w takes outputs 16w..16w+15
+  {
+    float gacc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      gacc[nt][0] = gacc[nt][1] = gacc[nt][2] = gacc[nt][3] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        mma_tile(gacc[nt], T.dz2 + ks * 16 * kHid + warp * 16, 1, kHid, S.h1b + ks * 16 * kHid + nt * 8, kHid, 1);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int in = nt * 8 + 2 * t, out = warp * 16 + g;
+      atomicAdd(grad + kOffW2 + out * kHid + in, gacc[nt][0]);
+      atomicAdd(grad + kOffW2 + out * kHid + in + 1, gacc[nt][1]);
+      atomicAdd(grad + kOffW2 + (out + 8) * kHid + in, gacc[nt][2]);
+      atomicAdd(grad + kOffW2 + (out + 8) * kHid + in + 1, gacc[nt][3]);
+    }
+  }
+  // dh1 = dz2 W2 for the warp's rows; dz1 = dh1 (1 - h1^2); gW1, gb1
+  {
+    float dacc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      dacc[nt][0] = dacc[nt][1] = dacc[nt][2] = dacc[nt][3] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        mma_tile(dacc[nt], T.dz2 + r0 * kHid + ks * 16, kHid, 1, S.W2 + ks * 16 * kHid + nt * 8, kHid, 1);
+    }
+    const float* xa = S.x + (r0 + g) * 4;
+    const float* xb = S.x + (r0 + g + 8) * 4;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = nt * 8 + 2 * t + h;
+        const float h1a = S.h1f[(r0 + g) * kHid + c], h1b = S.h1f[(r0 + g + 8) * kHid + c];
+        const float dza = dacc[nt][h] * (1.f - h1a * h1a);
+        const float dzb = dacc[nt][2 + h] * (1.f - h1b * h1b);
+        float gb = dza + dzb;
+        float gw[4] = {dza * xa[0] + dzb * xb[0], dza * xa[1] + dzb * xb[1], dza * xa[2] + dzb * xb[2],
+                       dza * xa[3] + dzb * xb[3]};
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+          gb += __shfl_xor_sync(0xffffffffu, gb, o);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) gw[f] += __shfl_xor_sync(0xffffffffu, gw[f], o);
+        }
+        if (g == 0) {
+          atomicAdd(&T.gb1[c], gb);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) atomicAdd(&T.gw1[c * 4 + f], gw[f]);
+        }
+      }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kHid * 4; q += blockDim.x) atomicAdd(grad + kOffW1 + q, T.gw1[q]);
+  for (int q = threadIdx.x; q < kHid; q += blockDim.x) atomicAdd(grad + kOffB1 + q, T.gb1[q]);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1c, float b2c, __nv_bfloat16* __restrict__ W2h) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= kNParam) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float gq = grad[q];
+  const float mq = b1 * m[q] + (1.f - b1) * gq;
+  const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+  m[q] = mq;
+  v[q] = vq;
+  const float pq = p[q] - lr * (mq / b1c) / (sqrtf(vq / b2c) + eps);
+  p[q] = pq;
+  if (q >= kOffW2 && q < kOffW2 + kHid * kHid) W2h[q - kOffW2] = __float2bfloat16_rn(pq);
+}
+
+__global__ void k_refresh_w2h(const float* __restrict__ p, __nv_bfloat16* __restrict__ W2h) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < kHid * kHid) W2h[q] = __float2bfloat16_rn(p[kOffW2 + q]);
+}
+
+// -------------------------------------------------------- surrogate thermal --
+__device__ __forceinline__ void warp_count(unsigned long long* slot, int v) {
+  const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)v);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(slot, (unsigned long long)tot);
+}
+
+// Per interior cell: network prediction of the change of log10 T over the step, applied
+// to E in FP64; cells outside the training range or over the bound go to the fallback list.
+__global__ void __launch_bounds__(128) k_thermal_surrogate(PatchDev P, ThermalDev th, MlpDev M,
+                                                           int* __restrict__ fb_list,
+                                                           unsigned long long* __restrict__ fb_count) {
+  __shared__ MlpSmem S;
+  __shared__ double sT[kMlpRows], sce[kMlpRows];
+  __shared__ int sok[kMlpRows];
+  mlp_load_weights(S, M);
+  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+  const double dt = *P.dt_used;
+  const float ldt = (float)log10(dt);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * 16;
+  for (long long base = (long long)blockIdx.x * kMlpRows; base < nc; base += (long long)gridDim.x * kMlpRows) {
+    __syncthreads();
+    if (threadIdx.x < kMlpRows) {
+      const int q = threadIdx.x;
+      const long long c = base + q;
+      int ok = 0;
+      float xs[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c < nc) {
+        const int i = (int)(c % P.n[0]);
+        const long long r = c / P.n[0];
+        const int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
+        double T, nh, ce;
+        th_cell(P, th, P.Un, i, j, k, T, nh, ce);
+        sT[q] = T;
+        sce[q] = ce;
+        const float raw[4] = {(float)log10(nh), (float)log10(th_clamp(T)), ldt, (float)th.z};
+        ok = 1;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          xs[f] = mlp_standardize(M, f, raw[f]);
+          if (!(xs[f] >= -1.0f && xs[f] <= 1.0f)) ok = 0;
+        }
+      }
+      sok[q] = c < nc ? ok : -1;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) S.x[q * 4 + f] = xs[f];
+    }
+    __syncthreads();
+    mlp_layer1(S, r0);
+    __syncwarp();
+    float acc[8][4];
+    mlp_layer2(S, r0, acc);
+    float ylo, yhi;
+    mlp_head(S, acc, ylo, yhi);
+    const int g = lane >> 2;
+    int nfb = 0;
+    if ((lane & 3) == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = r0 + g + 8 * h;
+        const float y = h ? yhi : ylo;
+        const long long c = base + q;
+        if (sok[q] < 0) continue;
+        const bool good = sok[q] == 1 && fabsf(y) <= M.dmax && isfinite(y);
+        const int i = (int)(c % P.n[0]);
+        const long long r = c / P.n[0];
+        const int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
+        if (good) {
+          const double T0 = th_clamp(sT[q]);
+          const double T1 = th_clamp(T0 * (double)exp10f(y));
+          P.Un[EN * P.FS + sidx(P, i, j, k)] += sce[q] * (T1 - sT[q]);
+        } else {
+          const unsigned long long slot = atomicAdd(fb_count, 1ull);
+          fb_list[slot] = (int)c;
+          ++nfb;
+        }
+      }
+    }
+    warp_count(th.stats + 3, nfb);
+    warp_count(th.stats + 0, (lane & 3) == 0 ? (int)(base + r0 + g < nc) + (int)(base + r0 + g + 8 < nc) : 0);
+  }
+}
+
+// Plain FP64 integrator on the listed cells (grid-stride over the device-side count).
+__global__ void __launch_bounds__(256) k_thermal_fallback(PatchDev P, ThermalDev th, const int* __restrict__ fb_list,
+                                                          const unsigned long long* __restrict__ fb_count) {
+  const long long n = (long long)*fb_count;
+  const double dt = *P.dt_used;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long c = fb_list[q];
+    const int i = (int)(c % P.n[0]);
+    const long long r = c / P.n[0];
+    const int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
+    double T, nh, ce;
+    th_cell(P, th, P.Un, i, j, k, T, nh, ce);
+    int st, nsub;
+    const double T1 = th_integrate(T, nh, ce, dt, th, &st, &nsub);
+    P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);
+    if (st & (TST_SUBSTEP_CAP | TST_NEWTON_CAP)) atomicAdd(th.stats + 2, 1ull);
+    atomicAdd(th.stats + 1, (unsigned long long)nsub);
+  }
+}
+
+// ------------------------------------------------------------ host side ----
+int mlp_forward(long long n, const float* xs, const MlpDev& M, float* y, cudaStream_t s) {
+  if (n <= 0) return 0;
+  long long blocks = (n + kMlpRows - 1) / kMlpRows;
+  if (blocks > 65535) blocks = 65535;
+  k_mlp_forward<<<(unsigned)blocks, 128, 0, s>>>(n, xs, M, y);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int mlp_grad(const MlpDev& M, const float* data, long long nrows, unsigned long long seed, long long step, int batch,
+             float* grad, float* loss_sum, cudaStream_t s) {
+  const int blocks = (batch + kMlpRows - 1) / kMlpRows;
+  k_mlp_grad<<<blocks, 128, 0, s>>>(M, data, nrows, seed, step, batch, grad, loss_sum);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int mlp_adam(float* p, const float* grad, float* m, float* v, float lr, long long t, __nv_bfloat16* W2h,
+             cudaStream_t s) {
+  const float b1c = 1.f - powf(0.9f, (float)t), b2c = 1.f - powf(0.999f, (float)t);
+  k_adam<<<(kNParam + 255) / 256, 256, 0, s>>>(p, grad, m, v, lr, b1c, b2c, W2h);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int mlp_refresh(const float* p, __nv_bfloat16* W2h, cudaStream_t s) {
+  k_refresh_w2h<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(p, W2h);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
+                    unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches) {
+  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+  if (cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s) != cudaSuccess) return -1;
+  long long blocks = (nc + kMlpRows - 1) / kMlpRows;
+  const long long cap = (long long)sms * 8;
+  if (blocks > cap) blocks = cap;
+  k_thermal_surrogate<<<(unsigned)blocks, 128, 0, s>>>(P, th, M, fb_list, fb_count);
+  k_thermal_fallback<<<(unsigned)(sms * 4), 256, 0, s>>>(P, th, fb_list, fb_count);
+  *launches += 2;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace mhd

@@ -1,0 +1,20 @@
+// mhd_mlp_launch.h -- host entries of the surrogate kernels (mhd_mlp.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace mhd {
+struct PatchDev;
+struct ThermalDev;
+struct MlpDev;
+int mlp_forward(long long n, const float* xs, const MlpDev& M, float* y, cudaStream_t s);
+int mlp_grad(const MlpDev& M, const float* data, long long nrows, unsigned long long seed, long long step, int batch,
+             float* grad, float* loss_sum, cudaStream_t s);
+int mlp_adam(float* p, const float* grad, float* m, float* v, float lr, long long t, __nv_bfloat16* W2h,
+             cudaStream_t s);
+int mlp_refresh(const float* p, __nv_bfloat16* W2h, cudaStream_t s);
+int mlp_forward_tc(long long n, const float* xs, const float* p, const __nv_bfloat16* W2h, float* y, int* err,
+                   int sms, cudaStream_t s);
+int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
+                    unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches);
+}  // namespace mhd

@@ -365,3 +365,38 @@ def alfven_wave(n: int, amp: float = 1e-6, gamma: float = 5.0 / 3.0, polarisatio
     Bx, By, _ = faces_from_Az(g, Az)
     Bz = np.broadcast_to(-math.sqrt(rho0) * amp * sph, (2, n, n)).copy()
     return state_from_prim(g, rho0, 0.0, 0.0, amp * sph, p0, Bx, By, Bz)
+
+
+# Code units of the disc workload: length kpc, velocity km/s (time unit 0.978 Gyr),
+# density unit = the gas mass per hydrogen atom (m_H/0.76) per cm^3.
+#   T = 72.7 K * (p/rho) [mu = 0.6],  n_H = 0.76 rho,
+#   energy-rate unit = 2.2e-14 erg cm^-3 / 3.086e16 s = 7.13e-31 erg cm^-3 s^-1.
+DISC_THERMAL = dict(gamma_heat=2e-26, z=0.02, rate_unit=7.13e-31, cap=0.1, nh_per_rho=0.76, t_per_pr=72.7)
+DISC_POTENTIAL = dict(potential=2, v0=220.0, rc=0.5)
+
+
+def disc(nx: int = 512, ny: int = 512, nz: int = 128, n_h0: float = 5.0, T0: float = 1e4, beta: float = 10.0,
+         v0: float = 220.0, rc: float = 0.5, rd: float = 3.0, z0: float = 0.2, floor: float = 1e-4) -> State:
+    """Isolated gas disc on [-20, 20]^2 x [-5, 5] kpc, outflow on all faces, gamma = 5/3:
+    rho = rho0 exp(-R/rd) sech^2(z/z0) floored at floor*rho0 (rho0 from the central n_H),
+    T = T0, circular velocity v0 R/sqrt(R^2 + rc^2) of Psi = v0^2/2 ln(R^2 + rc^2 + z^2),
+    toroidal field with plasma beta = beta for the unfloored profile, from
+    A_z = -2 rd sqrt(2 (p/rho) rho0/beta) sech(z/z0) (1 - exp(-R/(2 rd))) on z-edges."""
+    L = (40.0, 40.0, 10.0)
+    g = Geom(nx, ny, nz, -20.0, -20.0, -5.0, L[0] / nx, L[1] / ny, L[2] / nz, (1,) * 6, 5.0 / 3.0)
+    u = DISC_THERMAL
+    rho0 = n_h0 / u["nh_per_rho"]
+    pr = T0 / u["t_per_pr"]  # p/rho
+    x, y, z = g.centres()
+    X, Y, Z = x[None, None, :], y[None, :, None], z[:, None, None]
+    R = np.sqrt(X * X + Y * Y)
+    rho = np.maximum(rho0 * np.exp(-R / rd) / np.cosh(Z / z0) ** 2, floor * rho0)
+    vc = v0 * R / np.sqrt(R * R + rc * rc)
+    Rs = np.where(R > 0, R, 1.0)
+    vx = -vc * Y / Rs
+    vy = vc * X / Rs
+    C0 = math.sqrt(2.0 * pr * rho0 / beta)
+    zero = lambda xx, yy, zz: np.zeros(np.broadcast_shapes(np.shape(xx), np.shape(yy), np.shape(zz)))
+    Az = lambda xx, yy, zz: -2.0 * rd * C0 / np.cosh(zz / z0) * (1.0 - np.exp(-np.sqrt(xx * xx + yy * yy) / (2.0 * rd)))
+    Bx, By, Bz = faces_from_A(g, zero, zero, Az)
+    return state_from_prim(g, rho, vx, vy, 0.0, pr * rho, Bx, By, Bz)

@@ -49,6 +49,14 @@ class SourceDesc(C.Structure):
                 ("v0", C.c_double), ("rc", C.c_double)]
 
 
+class ThermalDesc(C.Structure):
+    _fields_ = [("mode", C.c_int), ("gamma_heat", C.c_double), ("z", C.c_double), ("rate_unit", C.c_double),
+                ("cap", C.c_double), ("nh_per_rho", C.c_double), ("t_per_pr", C.c_double)]
+
+
+THERMAL_OFF, THERMAL_PLAIN, THERMAL_SURROGATE = 0, 1, 2
+
+
 class Metrics(C.Structure):
     _fields_ = [("dt_last", C.c_double), ("sums", C.c_double * 5), ("max_divb", C.c_double),
                 ("error_word", C.c_int)]
@@ -59,7 +67,9 @@ _lib = None
 EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cfl_dt_patches",
            "mhd_get_state", "mhd_set_state", "mhd_sync", "mhd_get_metrics", "mhd_launch_count",
            "mhd_last_error", "mhd_destroy", "mhd_riemann_hlld", "mhd_set_profiling", "mhd_get_profile",
-           "mhd_cfl_dt_noalloc"]
+           "mhd_cfl_dt_noalloc", "mhd_autotune", "mhd_set_wait_limit", "mhd_set_thermal",
+           "mhd_thermal_stats", "mhd_thermal_cells", "mhd_surrogate_harvest", "mhd_surrogate_train",
+           "mhd_surrogate_params", "mhd_mlp_forward", "mhd_mlp_grad", "mhd_mlp_forward_tc"]
 
 
 def lib():
@@ -91,6 +101,18 @@ def lib():
     L.mhd_set_profiling.argtypes = [vp, ip]
     L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
     L.mhd_cfl_dt_noalloc.argtypes = [C.POINTER(PatchDesc), C.c_double, vp, vp, vp, vp]
+    L.mhd_autotune.argtypes = [vp, C.c_char_p, ip, C.POINTER(C.c_int)]
+    L.mhd_set_wait_limit.argtypes = [vp, C.c_double, ip]
+    L.mhd_set_thermal.argtypes = [vp, C.POINTER(ThermalDesc)]
+    L.mhd_thermal_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
+    L.mhd_thermal_cells.argtypes = [C.c_longlong, vp, vp, vp, vp, C.POINTER(ThermalDesc), vp, vp, vp]
+    L.mhd_surrogate_harvest.argtypes = [vp, C.c_longlong, ip]
+    L.mhd_surrogate_train.argtypes = [vp, ip, ip, C.c_double, C.c_ulonglong, C.c_double, dp,
+                                      C.POINTER(C.c_longlong)]
+    L.mhd_surrogate_params.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.mhd_mlp_forward.argtypes = [C.c_longlong, vp, vp, vp, vp]
+    L.mhd_mlp_grad.argtypes = [C.c_longlong, vp, vp, vp, vp, vp]
+    L.mhd_mlp_forward_tc.argtypes = [C.c_longlong, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("mhd_destroy", "mhd_last_error", "mhd_launch_count"):
             getattr(L, name).restype = C.c_int
@@ -198,7 +220,42 @@ class Grid:
         return {"dt_last": m.dt_last, "sums": list(m.sums), "max_divb": m.max_divb, "error_word": m.error_word}
 
     KERNEL_CLASSES = ["recovery", "flux1_x", "flux1_y", "flux1_z", "flux2_x", "flux2_y", "flux2_z",
-                      "emf", "update", "cfl"]
+                      "emf", "update", "cfl", "persistent", "thermal"]
+
+    def set_thermal(self, mode, gamma_heat=2e-26, z=0.02, rate_unit=7.13e-31, cap=0.1, nh_per_rho=0.76,
+                    t_per_pr=72.7):
+        d = ThermalDesc(int(mode), gamma_heat, z, rate_unit, cap, nh_per_rho, t_per_pr)
+        self._check(self.L.mhd_set_thermal(self.h, C.byref(d)), "mhd_set_thermal")
+
+    def surrogate_harvest(self, capacity: int, stride: int = 1):
+        self._check(self.L.mhd_surrogate_harvest(self.h, int(capacity), int(stride)), "mhd_surrogate_harvest")
+
+    def surrogate_train(self, epochs=20, batch=4096, lr=3e-3, seed=1502, dmax=0.0):
+        loss = C.c_double()
+        rows = C.c_longlong()
+        self._check(self.L.mhd_surrogate_train(self.h, int(epochs), int(batch), float(lr), int(seed), float(dmax),
+                                               C.byref(loss), C.byref(rows)), "mhd_surrogate_train")
+        return loss.value, rows.value
+
+    def surrogate_params(self):
+        p = (C.c_float * 4545)()
+        r = (C.c_float * 9)()
+        self._check(self.L.mhd_surrogate_params(self.h, p, r), "mhd_surrogate_params")
+        return np.frombuffer(p, dtype=np.float32).copy(), np.frombuffer(r, dtype=np.float32).copy()
+
+    def thermal_stats(self) -> dict:
+        out = (C.c_ulonglong * 4)()
+        self._check(self.L.mhd_thermal_stats(self.h, out), "mhd_thermal_stats")
+        return {"cells": out[0], "substeps": out[1], "capped": out[2], "fallback": out[3]}
+
+    def autotune(self, cache_path=None, force: bool = False):
+        tile = (C.c_int * 2)()
+        path = cache_path.encode() if cache_path else None
+        self._check(self.L.mhd_autotune(self.h, path, int(force), tile), "mhd_autotune")
+        return int(tile[0]), int(tile[1])
+
+    def set_wait_limit(self, limit_ms: float, phantom_blocks: int = 0):
+        self._check(self.L.mhd_set_wait_limit(self.h, float(limit_ms), int(phantom_blocks)), "mhd_set_wait_limit")
 
     def set_profiling(self, on: bool):
         self._check(self.L.mhd_set_profiling(self.h, int(on)), "mhd_set_profiling")
@@ -248,3 +305,65 @@ def cfl_dt_noalloc(geom: Geom, cfl: float, U_ptr: int, B_ptr: int, dt_ptr: int, 
     """Call mhd_cfl_dt_noalloc: device pointers in, device pointer out; returns the status."""
     d = patch_desc(geom)
     return int(lib().mhd_cfl_dt_noalloc(C.byref(d), float(cfl), U_ptr, B_ptr, dt_ptr, stream))
+
+
+def thermal_cells(T0, nh, ce, dt, th: dict):
+    """Plain FP64 thermal integrator on the GPU for independent cells; returns (T, status)."""
+    import torch
+    arr = [torch.as_tensor(np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), np.shape(T0)))).cuda()
+           for a in (T0, nh, ce, dt)]
+    out = torch.empty_like(arr[0])
+    st = torch.zeros(arr[0].shape, dtype=torch.int32, device="cuda")
+    d = ThermalDesc(THERMAL_PLAIN, th.get("gamma_heat", 2e-26), th.get("z", 0.02), th["rate_unit"], th.get("cap", 0.1),
+                    th.get("nh_per_rho", 0.76), th.get("t_per_pr", 72.7))
+    rc = lib().mhd_thermal_cells(out.numel(), *[a.data_ptr() for a in arr], C.byref(d), out.data_ptr(), st.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise MHDError(rc, "mhd_thermal_cells")
+    return out.cpu().numpy(), st.cpu().numpy()
+
+
+MLP_NPARAM = 4545
+
+
+def mlp_unpack(p):
+    """FP32 parameter block -> dict of float64 arrays in the oracle's layout."""
+    p = np.asarray(p, dtype=np.float64)
+    H = 64
+    o = 0
+    out = {}
+    for k, shape in (("W1", (H, 4)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+        n = int(np.prod(shape))
+        out[k] = p[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+def mlp_pack(d) -> np.ndarray:
+    return np.concatenate([np.asarray(d[k], dtype=np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "w3", "b3")])
+
+
+def mlp_forward(xs, params, tcgen05: bool = False) -> np.ndarray:
+    import torch
+    x = torch.as_tensor(np.ascontiguousarray(xs, dtype=np.float32)).cuda()
+    p = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    y = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    fn = lib().mhd_mlp_forward_tc if tcgen05 else lib().mhd_mlp_forward
+    rc = fn(x.shape[0], x.data_ptr(), p.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise MHDError(rc, "mhd_mlp_forward")
+    return y.cpu().numpy()
+
+
+def mlp_grad(xs, targets, params):
+    import torch
+    rows = np.concatenate([np.asarray(xs, dtype=np.float32), np.asarray(targets, dtype=np.float32)[:, None]], axis=1)
+    r = torch.as_tensor(np.ascontiguousarray(rows)).cuda()
+    p = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    rc = lib().mhd_mlp_grad(rows.shape[0], r.data_ptr(), p.data_ptr(), g.data_ptr(), loss.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise MHDError(rc, "mhd_mlp_grad")
+    return float(loss.item()), g.cpu().numpy()

@@ -1,0 +1,87 @@
+"""Batched uneven patches in one persistent launch per step (GPU).
+
+* The persistent step gives bit-for-bit the same state as the per-phase launches
+  (same phase functions, deterministic CFL minimum), with and without graph replay.
+* Every patch keeps its own CFL time step; each patch matches the oracle run with
+  that patch's dt (FP64 path at 1e-12, mixed at the stated bound).
+* The autotuner leaves the state unchanged and returns a tile shape.
+* A barrier wait that cannot complete ends the launch with MHD_ERR_TIMEOUT.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02935_gb300 import inputs, mhd
+from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+def batch():
+    g = lambda n, bc, d=(0.05, 0.06, 0.07): inputs.Geom(n[0], n[1], n[2], 0, 0, 0, d[0], d[1], d[2], bc, 5.0 / 3.0)
+    return [inputs.blast(16, (0.3, 0.6, 0.45), (0.6, 0.0, 0.8)),
+            inputs.turbulence((24, 20, 12), seed=31),
+            inputs.blast(12, (0.5, 0.5, 0.5), (0.0, 0.6, 0.8)),
+            inputs.smooth_random(g((19, 13, 7), (1,) * 6), 32),
+            inputs.orszag_tang(40, 24),
+            inputs.brio_wu(120)]
+
+
+def _all_states(grid, n):
+    return [grid.get_state(p) for p in range(n)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_matches_per_phase_launches(precision):
+    """Same phase functions in two launch schemes: equal up to the rounding of differently
+    contracted FMAs (the compiler may fuse multiply-adds differently in the two kernels)."""
+    sts = batch()
+    a = mhd.Grid(sts, precision=precision, cfl=0.4)
+    b = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_PERSISTENT | mhd.FLAG_GRAPH)
+    for _ in range(3):
+        a.step(-1.0)
+        b.step(-1.0)
+    tol = 3 * FP64_TOL if precision == "fp64" else 1e-6
+    for p, (sa, sb) in enumerate(zip(_all_states(a, len(sts)), _all_states(b, len(sts)))):
+        assert_close(sb, sa, tol, f"patch {p}", normalized=(precision == "mixed"))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
+def test_persistent_per_patch_dt_matches_oracle(precision, tol):
+    sts = batch()
+    g = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_PERSISTENT)
+    dts = g.cfl_dt_patches()
+    g.step(-1.0)
+    for p, st in enumerate(sts):
+        want_dt = oracle.cfl_dt(st, 0.4)
+        assert abs(dts[p] - want_dt) <= (1e-14 if precision == "fp64" else 1e-6) * want_dt
+        ref = oracle.step(st, dts[p])
+        assert_close(g.get_state(p), ref, tol, f"patch {p}", normalized=(precision == "mixed"))
+    g.close()
+
+
+def test_autotune_keeps_state_and_caches(tmp_path):
+    sts = batch()
+    g = mhd.Grid(sts, precision="mixed", cfl=0.4, flags=mhd.FLAG_PERSISTENT | mhd.FLAG_GRAPH)
+    before = _all_states(g, len(sts))
+    cache = str(tmp_path / "tune.json")
+    tx, ty = g.autotune(cache)
+    assert tx * ty in (128, 256, 512)
+    after = _all_states(g, len(sts))
+    for sa, sb in zip(before, after):
+        assert np.array_equal(sa.U, sb.U)
+    assert g.autotune(cache) == (tx, ty)  # served from the cache
+    g.step(-1.0)
+    g.sync()
+    g.close()
+
+
+def test_barrier_timeout_is_reported():
+    sts = batch()[:2]
+    g = mhd.Grid(sts, precision="mixed", cfl=0.4, flags=mhd.FLAG_PERSISTENT)
+    g.set_wait_limit(50.0, phantom_blocks=1)
+    g.step(-1.0)
+    assert g.sync_status() == -5
+    g.close()

@@ -1,0 +1,116 @@
+"""The BF16 tensor-core surrogate of the thermal source (GPU) against the FP64 oracle.
+
+* Forward pass and gradients: the GPU rounds W2 and the hidden activations h1 to BF16
+  (8-bit mantissa) for the tensor-core products and accumulates in FP32.  They are
+  compared with the FP64 oracle evaluated on the same BF16-rounded W2; the stated bound
+  is a relative error of 2e-2 per tensor (norm of the difference over the norm).
+* Surrogate thermal step on the disc: pairs harvested from the plain integrator, trained
+  on the GPU; the surrogate run is judged by the plain-integrator run from the same state.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02935_gb300 import inputs, mhd
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    H = 64
+    return {"W1": rng.normal(0, 0.8, (H, 4)), "b1": rng.normal(0, 0.2, H), "W2": rng.normal(0, 0.25, (H, H)),
+            "b2": rng.normal(0, 0.2, H), "w3": rng.normal(0, 0.3, H), "b3": rng.normal(0, 0.1, 1)}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+def test_mlp_forward_matches_oracle():
+    P = _params(1)
+    flat = mhd.mlp_pack(P)
+    Pr = mhd.mlp_unpack(flat)
+    Pr["W2"] = _bf16(Pr["W2"])
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, (1000, 4)).astype(np.float32)
+    y = mhd.mlp_forward(X, flat)
+    ref = oracle.mlp_forward(X.astype(np.float64), Pr)
+    assert _rel(y, ref) <= 2e-2
+
+
+def test_mlp_forward_tcgen05_matches_mma_sync():
+    """The tcgen05 (TMEM-accumulator) kernel and the warp-level mma.sync kernel multiply the
+    same BF16 operands; they differ only in the FP32 accumulation order."""
+    P = _params(9)
+    flat = mhd.mlp_pack(P)
+    rng = np.random.default_rng(10)
+    X = rng.uniform(-1, 1, (5000, 4)).astype(np.float32)  # several 128-row tiles and a tail
+    y0 = mhd.mlp_forward(X, flat)
+    y1 = mhd.mlp_forward(X, flat, tcgen05=True)
+    assert np.max(np.abs(y1 - y0) / (1.0 + np.abs(y0))) <= 1e-4
+
+
+def test_mlp_gradients_match_oracle():
+    P = _params(3)
+    flat = mhd.mlp_pack(P)
+    Pr = mhd.mlp_unpack(flat)
+    Pr["W2"] = _bf16(Pr["W2"])
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (512, 4)).astype(np.float32)
+    T = rng.normal(0, 0.3, 512).astype(np.float32)
+    loss_sum, g = mhd.mlp_grad(X, T, flat)
+    ref_loss, G = oracle.mlp_backward(X.astype(np.float64), T.astype(np.float64), Pr)
+    assert abs(loss_sum / 512 - ref_loss) <= 2e-2 * ref_loss
+    gd = mhd.mlp_unpack(g)
+    for k in G:
+        assert _rel(gd[k], G[k]) <= 2e-2, (k, _rel(gd[k], G[k]))
+
+
+def _temperature(st, th):
+    bx, by, bz = st.bcc()
+    kin = 0.5 * (st.U[1] ** 2 + st.U[2] ** 2 + st.U[3] ** 2) / st.U[0]
+    p = (st.geom.gamma - 1) * (st.U[4] - kin - 0.5 * (bx * bx + by * by + bz * bz))
+    return th["t_per_pr"] * p / st.U[0]
+
+
+def test_surrogate_thermal_step_on_disc():
+    """Harvest pairs from the plain integrator over 8 steps of a 64x64x24 disc, train on the
+    GPU, then run 5 more steps with the surrogate and, from the same state, 5 steps with the
+    plain integrator; the stated bound is 1e-2 on the L1-relative difference in T."""
+    th = inputs.DISC_THERMAL
+    st = inputs.disc(64, 64, 24)
+    g = mhd.Grid(st, precision="mixed", cfl=0.4)
+    g.set_sources(**inputs.DISC_POTENTIAL)
+    g.set_thermal(mhd.THERMAL_PLAIN, **th)
+    g.surrogate_harvest(1 << 20, stride=1)
+    for _ in range(8):
+        g.step(-1.0)
+    loss, rows = g.surrogate_train(epochs=60, batch=8192, lr=3e-3, seed=1502)
+    print("surrogate training loss", loss, "rows", rows)
+    assert rows >= 8192 and loss < 1e-3, (loss, rows)
+    mid = g.get_state(0)
+    g.set_thermal(mhd.THERMAL_SURROGATE, **th)
+    h = mhd.Grid(mid, precision="mixed", cfl=0.4)
+    h.set_sources(**inputs.DISC_POTENTIAL)
+    h.set_thermal(mhd.THERMAL_PLAIN, **th)
+    s0 = g.thermal_stats()
+    for _ in range(5):
+        g.step(-1.0)
+        h.step(-1.0)
+    sur, plain = g.get_state(0), h.get_state(0)
+    s1 = g.thermal_stats()
+    g.close()
+    h.close()
+    Tp = _temperature(plain, th)
+    Ts = _temperature(sur, th)
+    l1 = float(np.mean(np.abs(Ts - Tp)) / np.mean(np.abs(Tp)))
+    fb = (s1["fallback"] - s0["fallback"]) / max(1, s1["cells"] - s0["cells"])
+    print("surrogate L1(T) vs plain", l1, "fallback fraction", fb)
+    assert l1 <= 1e-2, l1
+    assert fb < 0.5, fb

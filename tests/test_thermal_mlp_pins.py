@@ -1,0 +1,136 @@
+"""Pins of the thermal-source oracle and of the MLP-surrogate oracle (CPU only).
+
+Thermal module: Section 3.10 of arXiv:1502.02935 (heating/cooling in S of Eq. 2).  The
+paper's rate tables are not available; the oracle uses a documented piecewise power-law
+stand-in.  The pins below hold for any such table:
+  * with heating off and T inside one power-law segment, Lambda = C T^a and the isochoric
+    equation dT/dt = -K T^a has the closed form T^(1-a)(t) = T0^(1-a) - (1-a) K t; the
+    sub-stepped backward Euler converges to it at first order in the sub-step cap;
+  * a temperature where n Gamma = n^2 Lambda(T) is a fixed point, and cells relax onto the
+    stable equilibrium from both sides;
+  * the operator-split update changes only E, by exactly the internal energy c_e dT.
+MLP oracle: the backward pass equals central finite differences of the loss, and equals
+torch autograd on the same network (CPU, FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02935_gb300 import inputs
+
+LT = [1.0, 2.0, 3.0, 3.8, 4.0, 4.2, 5.0, 5.4, 6.0, 7.0, 8.0]
+TH = dict(rate_unit=5.4e-31, nh_per_rho=0.76, t_per_pr=72.7, cap=0.1, gamma_heat=2e-26, z=0.02)
+
+
+def test_power_law_cooling_closed_form_first_order():
+    th = dict(TH, gamma_heat=0.0)
+    T0 = 10 ** 5.95
+    lam0, slope = oracle.cooling([T0], th["z"])
+    a = float(slope[0])
+    C = float(lam0[0]) / T0 ** a
+    nh, ce = 1.0, 1.0 / (72.7 * (2.0 / 3.0))
+    K = nh * nh * C / (th["rate_unit"] * ce)
+    T_end = 10 ** 5.7  # inside the segment [10^5.4, 10^6], away from the finite-time collapse
+    t_end = (T0 ** (1 - a) - T_end ** (1 - a)) / ((1 - a) * K)
+    errs = []
+    for cap in (0.1, 0.01, 0.001):
+        T, st = oracle.thermal_cells([T0], [nh], [ce], [t_end], dict(th, cap=cap))
+        assert st[0] == 0
+        errs.append(abs(T[0] - T_end) / T_end)
+    assert errs[0] / errs[1] > 6 and errs[1] / errs[2] > 6, errs
+    assert errs[2] < 2e-3, errs
+
+
+def _equilibrium(nh, th):
+    f = lambda T: nh * th["gamma_heat"] - nh * nh * oracle.cooling([T], th["z"])[0][0]
+    lo, hi = 10 ** 3.0, 10 ** 3.99  # heating wins at lo, cooling at hi (n_H = 1)
+    assert f(lo) > 0 > f(hi)
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        if f(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return math.sqrt(lo * hi)
+
+
+def test_equilibrium_is_fixed_point_and_attracts():
+    nh, ce = 1.0, 1.0 / (72.7 * (2.0 / 3.0))
+    Teq = _equilibrium(nh, TH)
+    T, st = oracle.thermal_cells([Teq], [nh], [ce], [1.0], TH)
+    assert abs(T[0] - Teq) <= 1e-9 * Teq
+    for T0 in (0.7 * Teq, 1.6 * Teq):
+        T, st = oracle.thermal_cells([T0], [nh], [ce], [10.0], TH)
+        assert abs(T[0] - Teq) <= 1e-6 * Teq, (T0, T[0], Teq)
+
+
+def test_thermal_apply_changes_only_internal_energy():
+    st0 = inputs.turbulence((6, 5, 4), seed=3)
+    U = st0.U.copy()
+    U[4] = U[4] * 0.2 + 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0] * 0.8  # cooler gas
+    st0 = st0.replace(U=U)
+    st1, status = oracle.thermal_apply(st0, 1e-3, TH)
+    assert np.array_equal(st1.U[:4], st0.U[:4])
+    g = st0.geom
+
+    def temp(st):
+        bx, by, bz = st.bcc()
+        kin = 0.5 * (st.U[1] ** 2 + st.U[2] ** 2 + st.U[3] ** 2) / st.U[0]
+        p = (g.gamma - 1) * (st.U[4] - kin - 0.5 * (bx * bx + by * by + bz * bz))
+        return TH["t_per_pr"] * p / st.U[0]
+
+    T0, T1 = temp(st0), temp(st1)
+    ce = st0.U[0] / (TH["t_per_pr"] * (g.gamma - 1))
+    Tref, _ = oracle.thermal_cells(T0.ravel(), (TH["nh_per_rho"] * st0.U[0]).ravel(), ce.ravel(),
+                                   np.full(T0.size, 1e-3), TH)
+    assert np.max(np.abs(T1.ravel() - Tref) / Tref) < 1e-9
+
+
+def _params(seed, scale=0.4):
+    rng = np.random.default_rng(seed)
+    H = oracle.HIDDEN
+    return {"W1": rng.normal(0, scale, (H, 4)), "b1": rng.normal(0, 0.1, H), "W2": rng.normal(0, scale / 4, (H, H)),
+            "b2": rng.normal(0, 0.1, H), "w3": rng.normal(0, scale / 4, H), "b3": rng.normal(0, 0.1, 1)}
+
+
+def test_mlp_backward_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (24, 4))
+    T = rng.normal(0, 0.3, 24)
+    P = _params(6)
+    loss, G = oracle.mlp_backward(X, T, P)
+    y = oracle.mlp_forward(X, P)
+    assert abs(loss - np.mean((y - T) ** 2)) < 1e-14
+    h = 1e-6
+    for k in P:
+        flat = P[k].ravel()
+        idx = rng.choice(flat.size, size=min(flat.size, 12), replace=False)
+        for q in idx:
+            Pp = {kk: vv.copy() for kk, vv in P.items()}
+            Pm = {kk: vv.copy() for kk, vv in P.items()}
+            Pp[k].ravel()[q] += h
+            Pm[k].ravel()[q] -= h
+            fd = (oracle.mlp_backward(X, T, Pp)[0] - oracle.mlp_backward(X, T, Pm)[0]) / (2 * h)
+            g = G[k].ravel()[q]
+            assert abs(fd - g) <= 1e-7 * max(abs(g), 1e-3), (k, q, fd, g)
+
+
+def test_mlp_backward_matches_torch_autograd():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-1, 1, (40, 4))
+    T = rng.normal(0, 0.3, 40)
+    P = _params(8)
+    loss, G = oracle.mlp_backward(X, T, P)
+    tp = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in P.items()}
+    x = torch.tensor(X)
+    h1 = torch.tanh(x @ tp["W1"].T + tp["b1"])
+    h2 = torch.tanh(h1 @ tp["W2"].T + tp["b2"])
+    y = h2 @ tp["w3"] + tp["b3"]
+    L = torch.mean((y - torch.tensor(T)) ** 2)
+    L.backward()
+    assert abs(L.item() - loss) < 1e-14
+    for k in P:
+        assert np.max(np.abs(tp[k].grad.numpy() - G[k])) < 1e-13
