@@ -210,13 +210,16 @@ def brio_wu(n: int = 800, axis: int = 0, transverse: int = 1) -> State:
 
 def ryu_jones(n: int = 800) -> State:
     """Ryu-Jones 7-wave Riemann problem (Section 3.5), gamma = 5/3, on [0, 1] with the
-    discontinuity at 0.5 and outflow ends."""
+    discontinuity at 0.5 and outflow ends.  Left: rho 1.08, p 0.95, v (1.2, 0.01, 0.5),
+    B (Bx, 3.6, 2)/sqrt(4 pi); right: rho 1, p 1, v 0, B (Bx, 4, 2)/sqrt(4 pi), with
+    Bx = 2/sqrt(4 pi) (the paper prints 4/sqrt(4 pi); its printed shock Mach numbers
+    belong to Bx = 2/sqrt(4 pi))."""
     g = Geom(n, 1, 1, 0.0, 0.0, 0.0, 1.0 / n, 1.0, 1.0, (1, 1, 0, 0, 0, 0), 5.0 / 3.0)
     x = g.centres()[0]
     left = x < 0.5
     s4 = 1.0 / math.sqrt(4.0 * math.pi)
     sel = lambda a, b: np.where(left, a, b)[None, None, :]
-    Bx = np.full((1, 1, n + 1), 4.0 * s4)
+    Bx = np.full((1, 1, n + 1), 2.0 * s4)
     By = np.broadcast_to(sel(3.6 * s4, 4.0 * s4), (1, 2, n)).copy()
     Bz = np.broadcast_to(sel(2.0 * s4, 2.0 * s4), (2, 1, n)).copy()
     return state_from_prim(g, sel(1.08, 1.0), sel(1.2, 0.0), sel(0.01, 0.0), sel(0.5, 0.0),

@@ -342,3 +342,47 @@ def test_sod_converges_to_exact_solution():
         ex = textbook.exact_riemann_euler((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, x / 0.5)
         errs.append(np.mean(np.abs(out.U[0, 0, 0, :] - ex[0])) * 2.0)
     assert errs[0] > errs[1] > errs[2] and errs[2] < 6e-3, errs
+
+
+def _shock_machs(st):
+    """Mach numbers of the shocks in a 1D profile: shocks are local maxima of -du/dx; the
+    shock speed comes from mass conservation across it, s = [rho u]/[rho], with states a few
+    cells either side; the upstream side is the lower-pressure one; M = |u_up - s| / c with
+    c the fast (first) or slow (second) magnetosonic speed of the upstream state."""
+    U = st.U[:, 0, 0, :]
+    n = U.shape[1]
+    rho, u = U[0], U[1] / U[0]
+    v, w = U[2] / U[0], U[3] / U[0]
+    bx = 0.5 * (st.Bx[0, 0, :-1] + st.Bx[0, 0, 1:])
+    by, bz = st.By[0, 0, :], st.Bz[0, 0, :]
+    g = st.geom.gamma
+    p = (g - 1) * (U[4] - 0.5 * rho * (u * u + v * v + w * w) - 0.5 * (bx * bx + by * by + bz * bz))
+    comp = -np.gradient(u)
+    cand = [i for i in range(3, n - 3) if comp[i] == comp[i - 3:i + 4].max() and comp[i] > 0.01 * comp.max()]
+    out = []
+    for i in sorted(sorted(cand, key=lambda i: -comp[i])[:8]):
+        k = max(6, n // 150)
+        a, b = i - k, i + k
+        if a < 0 or b >= n or abs(rho[b] - rho[a]) < 1e-3:
+            continue
+        s = (rho[b] * u[b] - rho[a] * u[a]) / (rho[b] - rho[a])
+        up = a if p[a] < p[b] else b
+        a2, b2 = g * p[up] / rho[up], (bx[up] ** 2 + by[up] ** 2 + bz[up] ** 2) / rho[up]
+        disc = math.sqrt(max((a2 + b2) ** 2 - 4 * a2 * bx[up] ** 2 / rho[up], 0.0))
+        cf, cs = math.sqrt(0.5 * (a2 + b2 + disc)), math.sqrt(max(0.5 * (a2 + b2 - disc), 0.0))
+        out.append((abs(u[up] - s) / cf, abs(u[up] - s) / cs))
+    return out
+
+
+def test_ryu_jones_shock_mach_numbers():
+    """Section 3.5 prints the Mach numbers of the Ryu-Jones solution: fast shocks 1.22 and
+    1.28, slow shocks 1.09 and 1.07.  The oracle's solution at t = 0.2 (1600 cells) has four
+    shocks; the outer two are fast, the inner two slow; each matches within 1.5%."""
+    gold = json.load(open(os.path.join(GOLDEN, "ryu_jones_mach.json")))
+    out, _ = oracle.run(inputs.ryu_jones(1600), 0.8, gold["t_end"])
+    m = _shock_machs(out)
+    assert len(m) == 4, m
+    fast = sorted([m[0][0], m[3][0]])
+    slow = sorted([m[1][1], m[2][1]])
+    for got, want in zip(fast + slow, sorted(gold["fast"]) + sorted(gold["slow"])):
+        assert abs(got - want) <= 0.015 * want, (fast, slow)
