@@ -180,8 +180,8 @@ int mhd_thermal_stats(mhd_ctx* ctx, unsigned long long* out4);
  * beta2 0.999) on FP32 master weights with the learning rate decayed from lr to lr/20 on a
  * cosine, minibatches of `batch` rows drawn with a hash of (seed, step, row), `epochs`
  * passes of rows/batch steps, weights initialised from seed.
- * dmax > 0 is the fallback bound on the predicted |change of log10 T|; dmax <= 0 takes the
- * largest change in the training set.  loss_out receives the mean squared error of the
+ * dmax > 0 is the fallback bound on the predicted |change of log10 T|; dmax <= 0 takes 1.25
+ * times the largest change in the training set.  loss_out receives the mean squared error of the
  * last epoch, rows_out the number of training rows (either may be NULL).  Harvesting stops.
  *
  * mhd_surrogate_params: copy the FP32 parameters out (4545 floats: W1[64][4], b1[64],

@@ -713,7 +713,7 @@ int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned
     ctx->mdev.xlo[f] = lo[f];
     ctx->mdev.xscale[f] = 2.0f / (hi[f] - lo[f]);
   }
-  ctx->mdev.dmax = dmax > 0.0 ? (float)dmax : ymax;
+  ctx->mdev.dmax = dmax > 0.0 ? (float)dmax : 1.25f * ymax;
   // initial weights: uniform(-a, a) with a = sqrt(6/(fan_in + fan_out)), seeded
   std::vector<float> p0(kNParam, 0.f);
   std::mt19937_64 gen(seed);

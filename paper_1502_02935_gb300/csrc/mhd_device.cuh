@@ -133,6 +133,7 @@ __device__ __forceinline__ float d2f_alu(double d) {
 // --------------------------------------------------------------- arithmetic --
 template <class R> struct Ar;
 template <> struct Ar<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double from_d(double x) { return x; }
   static __device__ __forceinline__ double to_d(double x) { return x; }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
@@ -143,8 +144,26 @@ template <> struct Ar<double> {
 template <> struct Ar<float> {
   static __device__ __forceinline__ float from_d(double x) { return d2f_alu(x); }
   static __device__ __forceinline__ double to_d(float x) { return f2d_alu(x); }
-  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  // single hardware approximations (a few ulp) for the FP32 bulk arithmetic
+  static __device__ __forceinline__ float rcp(float x) {
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return 1.0f / x;
+#endif
+  }
+  static __device__ __forceinline__ float sqrt_(float x) {
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return sqrtf(x);
+#endif
+  }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
   static constexpr float degen = 1e-8f;
 };
@@ -329,10 +348,11 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
 // --------------------------------------------------------- reconstruction ----
 // kappa = 1/3 compressive minmod scheme (Eq. 12-14 read in the standard form that is
 // third-order upwind biased): K1 = 1/6, K2 = 1/3, b = 4.
+// minmod(a, b) = sign(a) max(0, min(|a|, sign(a) b)): the smaller magnitude with a's sign
+// when a and b have the same sign, else 0 (written branch-free)
 template <class R> __device__ __forceinline__ R minmod(R a, R b) {
-  R s = a > R(0) ? R(1) : (a < R(0) ? R(-1) : R(0));
-  R m = Ar<R>::abs_(a) < s * b ? Ar<R>::abs_(a) : s * b;
-  return s * (m > R(0) ? m : R(0));
+  const R m = Ar<R>::abs_(a) < Ar<R>::abs_(b) ? Ar<R>::abs_(a) : Ar<R>::abs_(b);
+  return a * b > R(0) ? copysign(m, a) : R(0);
 }
 
 template <class R>
@@ -414,7 +434,7 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
     for (int a = 0; a < 3; ++a) {
       if (!P.act[a]) continue;
       const R cf = fast_speed<R>(rr, pr, bb, b[a] * b[a], gam);
-      const R t = Gam<R>::d(P, a) / (Ar<R>::abs_(v[a]) + cf);
+      const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::abs_(v[a]) + cf);
       lr = t < lr ? t : lr;
     }
     lim = (double)lr;

@@ -8,9 +8,10 @@
 // copy of W2.
 //
 // Inference (thermal mode SURROGATE): per interior cell, features -> network -> change of
-// log10 T; a cell whose standardised features leave [-1, 1] or whose predicted change
-// exceeds the stated bound is appended to a fallback list that the plain FP64 integrator
-// then handles, so the divergent fallback stays out of the network kernel.
+// log10 T (k_thermal_surrogate_tc in mhd_mlp_tc.cu, on tcgen05; k_thermal_surrogate below is
+// the same step on mma.sync); a cell whose standardised features leave [-1, 1] or whose
+// predicted change exceeds the stated bound is appended to a fallback list that the plain
+// FP64 integrator then handles, so the divergent fallback stays out of the network kernel.
 #include <cuda_bf16.h>
 
 #include "mhd_mlp.cuh"
@@ -368,9 +369,10 @@ int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, in
   long long blocks = (nc + kMlpRows - 1) / kMlpRows;
   const long long cap = (long long)sms * 8;
   if (blocks > cap) blocks = cap;
-  k_thermal_surrogate<<<(unsigned)blocks, 128, 0, s>>>(P, th, M, fb_list, fb_count);
+  (void)blocks;
+  if (issue_surrogate_tc(P, th, M, fb_list, fb_count, sms, s, launches)) return -1;
   k_thermal_fallback<<<(unsigned)(sms * 4), 256, 0, s>>>(P, th, fb_list, fb_count);
-  *launches += 2;
+  *launches += 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

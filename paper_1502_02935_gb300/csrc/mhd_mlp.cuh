@@ -5,8 +5,10 @@
 // y = predicted change of log10 T over dt.
 //
 // The 64x64 layer runs on the tensor cores: BF16 operands (activations h1 and weights W2
-// rounded to BF16), FP32 accumulation, warp-level mma.sync m16n8k16.  The 4-wide input
-// layer and the 64-wide output layer are FP32 FMAs.  Master weights are FP32.
+// rounded to BF16), FP32 accumulation.  Inference in the thermal step uses tcgen05.mma with
+// the accumulator in tensor memory (mhd_mlp_tc.cu); training, whose backward pass needs
+// the transposed products as well, uses warp-level mma.sync m16n8k16 (mhd_mlp.cu).  The
+// 4-wide input layer and the 64-wide output layer are FP32 FMAs.  Master weights are FP32.
 // Parameter block layout (floats): W1[64][4], b1[64], W2[64][64] (row = output), b2[64],
 // w3[64], b3[1].
 #pragma once

@@ -15,6 +15,8 @@ int mlp_adam(float* p, const float* grad, float* m, float* v, float lr, long lon
 int mlp_refresh(const float* p, __nv_bfloat16* W2h, cudaStream_t s);
 int mlp_forward_tc(long long n, const float* xs, const float* p, const __nv_bfloat16* W2h, float* y, int* err,
                    int sms, cudaStream_t s);
+int issue_surrogate_tc(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
+                       unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches);
 int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
                     unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches);
 }  // namespace mhd
