@@ -34,7 +34,8 @@ class OrcPatch(C.Structure):
 
 class OrcSource(C.Structure):
     _fields_ = [("potential", C.c_int), ("psi0", C.c_double), ("xc", C.c_double),
-                ("xw", C.c_double), ("v0", C.c_double), ("rc", C.c_double)]
+                ("xw", C.c_double), ("v0", C.c_double), ("rc", C.c_double),
+                ("rho_floor", C.c_double), ("pr_floor", C.c_double), ("pr_ceil", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -60,7 +61,7 @@ def lib():
             dp = C.POINTER(C.c_double)
             L.orc_step.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp, C.c_double]
             L.orc_step.restype = C.c_int
-            L.orc_cfl_dt.argtypes = [C.POINTER(OrcPatch), dp, dp, dp, dp, C.c_double]
+            L.orc_cfl_dt.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp, C.c_double]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_run.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp,
                                   C.c_double, C.c_double, C.c_int]
@@ -117,7 +118,7 @@ def source_struct(src) -> OrcSource:
     if src is None:
         return s
     s.potential = int(src.get("potential", 0))
-    for k in ("psi0", "xc", "xw", "v0", "rc"):
+    for k in ("psi0", "xc", "xw", "v0", "rc", "rho_floor", "pr_floor", "pr_ceil"):
         setattr(s, k, float(src.get(k, 0.0)))
     return s
 
@@ -129,20 +130,26 @@ def _copy_state(st):
             np.ascontiguousarray(st.Bz, dtype=np.float64).copy())
 
 
-def step(st, dt: float, source=None, nsteps: int = 1):
-    """``nsteps`` van Leer steps of fixed size dt; returns a new State."""
+def step(st, dt: float, source=None, nsteps: int = 1, floored=None):
+    """``nsteps`` van Leer steps of fixed size dt; returns a new State.  If ``floored``
+    is a list, the per-step counts of cells changed by the end-of-step floors are
+    appended to it."""
     L = lib()
     U, Bx, By, Bz = _copy_state(st)
     p, s = patch_struct(st.geom), source_struct(source)
     for _ in range(nsteps):
-        if L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt)) != 0:
+        n = L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
+        if n < 0:
             raise ValueError("orc_step rejected its arguments")
+        if floored is not None:
+            floored.append(int(n))
     return st.replace(U=U, Bx=Bx, By=By, Bz=Bz)
 
 
-def cfl_dt(st, cfl: float) -> float:
+def cfl_dt(st, cfl: float, source=None) -> float:
     U, Bx, By, Bz = _copy_state(st)
-    return float(lib().orc_cfl_dt(C.byref(patch_struct(st.geom)), _p(U), _p(Bx), _p(By), _p(Bz), cfl))
+    return float(lib().orc_cfl_dt(C.byref(patch_struct(st.geom)), C.byref(source_struct(source)),
+                                  _p(U), _p(Bx), _p(By), _p(Bz), cfl))
 
 
 def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None):

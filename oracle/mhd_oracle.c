@@ -45,6 +45,8 @@ typedef struct {
   int per[3];   /* periodic (trivial axes count as periodic with n = 1) */
   double d[3], lo[3], gamma;
   long tot;
+  int floors;                         /* floors on (rho_floor > 0) */
+  double rho_floor, pr_floor, pr_ceil; /* pr_ceil = +inf when no ceiling is set */
 } grid;
 
 static long ix(const grid* G, int i, int j, int k) {
@@ -79,7 +81,24 @@ static int make_grid(const orc_patch* p, grid* G) {
   }
   if (!(p->gamma > 1.0)) return -1;
   G->gamma = p->gamma;
+  G->floors = 0;
+  G->rho_floor = G->pr_floor = 0.0;
+  G->pr_ceil = INFINITY;
   return 0;
+}
+
+/* Floors from the source description (reading: the paper states none). */
+static void set_floors(grid* G, const orc_source* s) {
+  if (!s || !(s->rho_floor > 0.0)) return;
+  G->floors = 1;
+  G->rho_floor = s->rho_floor;
+  G->pr_floor = s->pr_floor > 0.0 ? s->pr_floor : 0.0;
+  G->pr_ceil = s->pr_ceil > 0.0 ? s->pr_ceil : INFINITY;
+}
+
+static double clamp_p(const grid* G, double p, double rho) {
+  double lo = rho * G->pr_floor, hi = rho * G->pr_ceil;
+  return p < lo ? lo : (p > hi ? hi : p);
 }
 
 /* ---------------------------------------------------------------- boundaries --
@@ -118,7 +137,9 @@ static void fill_ghosts(const grid* G, double* const F[NF]) {
 /* ------------------------------------------------------ primitive recovery --
  * Eq. 6: cell-centred B is the mean of the two face values.
  * Text after Eq. 3: E = P/(gamma-1) + rho v^2/2 + B^2/2, so
- * P = (gamma-1) (E - rho v^2/2 - B^2/2). */
+ * P = (gamma-1) (E - rho v^2/2 - B^2/2).
+ * With floors on, rho is raised to rho_floor before v = m/rho, and P is clamped to
+ * [rho pr_floor, rho pr_ceil]. */
 static void cons_to_prim(const grid* G, double* const U[NF], double* const W[NF]) {
   double gm1 = G->gamma - 1.0;
 #pragma omp parallel for schedule(static)
@@ -127,6 +148,7 @@ static void cons_to_prim(const grid* G, double* const U[NF], double* const W[NF]
       for (int i = -G->g[0]; i < G->n[0] + G->g[0]; ++i) {
         long c = ix(G, i, j, k);
         double rho = U[RHO][c];
+        if (G->floors && rho < G->rho_floor) rho = G->rho_floor;
         double vx = U[MX][c] / rho, vy = U[MY][c] / rho, vz = U[MZ][c] / rho;
         double bx = 0.5 * (U[BXF][c] + U[BXF][ix(G, i + 1, j, k)]);
         double by = 0.5 * (U[BYF][c] + U[BYF][ix(G, i, j + 1, k)]);
@@ -137,7 +159,8 @@ static void cons_to_prim(const grid* G, double* const U[NF], double* const W[NF]
         W[WVX][c] = vx;
         W[WVY][c] = vy;
         W[WVZ][c] = vz;
-        W[WP][c] = gm1 * (U[EN][c] - kin - mag);
+        double p = gm1 * (U[EN][c] - kin - mag);
+        W[WP][c] = G->floors ? clamp_p(G, p, rho) : p;
         W[WBX][c] = bx;
         W[WBY][c] = by;
         W[WBZ][c] = bz;
@@ -665,10 +688,42 @@ static int work_alloc(const grid* G, work* w) {
   return 0;
 }
 
+/* End-of-step floors on the conserved state (reading: the paper states none):
+ * rho' = max(rho, rho_floor), momentum kept, P from E with rho' and the cell-centred
+ * field of Eq. 6, clamped to [rho' pr_floor, rho' pr_ceil], and E rebuilt by the
+ * closure after Eq. 3 when rho or P changed.  Returns the number of cells changed. */
+static long floor_state(const grid* G, double* const U[NF]) {
+  if (!G->floors) return 0;
+  double gm1 = G->gamma - 1.0;
+  long count = 0;
+#pragma omp parallel for schedule(static) reduction(+ : count)
+  for (int k = 0; k < G->n[2]; ++k)
+    for (int j = 0; j < G->n[1]; ++j)
+      for (int i = 0; i < G->n[0]; ++i) {
+        long c = ix(G, i, j, k);
+        double rho = U[RHO][c];
+        double rf = rho < G->rho_floor ? G->rho_floor : rho;
+        double m2 = U[MX][c] * U[MX][c] + U[MY][c] * U[MY][c] + U[MZ][c] * U[MZ][c];
+        double bx = 0.5 * (U[BXF][c] + U[BXF][ix(G, i + 1, j, k)]);
+        double by = 0.5 * (U[BYF][c] + U[BYF][ix(G, i, j + 1, k)]);
+        double bz = 0.5 * (U[BZF][c] + U[BZF][ix(G, i, j, k + 1)]);
+        double kin = 0.5 * m2 / rf;
+        double mag = 0.5 * (bx * bx + by * by + bz * bz);
+        double p = gm1 * (U[EN][c] - kin - mag);
+        double pf = clamp_p(G, p, rf);
+        if (rf != rho || pf != p) {
+          U[RHO][c] = rf;
+          U[EN][c] = pf / gm1 + kin + mag;
+          ++count;
+        }
+      }
+  return count;
+}
+
 /* Two-stage van Leer step: donor-cell fluxes and EMFs from W^n give U^{n+1/2}
  * (h = dt/2, S at U^n); kappa-scheme fluxes and EMFs from W^{n+1/2} give U^{n+1}
  * (h = dt, S at U^{n+1/2}), both from the base U^n. */
-static void vl2_step(const grid* G, const orc_source* s, work* w, double dt) {
+static long vl2_step(const grid* G, const orc_source* s, work* w, double dt) {
   fill_ghosts(G, w->Un);
   cons_to_prim(G, w->Un, w->W);
   for (int d = 0; d < 3; ++d)
@@ -686,7 +741,10 @@ static void vl2_step(const grid* G, const orc_source* s, work* w, double dt) {
     w->Un[f] = w->Uo[f];
     w->Uo[f] = t;
   }
-  fill_ghosts(G, w->Un);
+  fill_ghosts(G, w->Un); /* the floors read the high faces of the last interior cells */
+  long floored = floor_state(G, w->Un);
+  if (floored) fill_ghosts(G, w->Un);
+  return floored;
 }
 
 /* Time step from the CFL condition (the paper does not state it; reading:
@@ -716,20 +774,22 @@ int orc_step(const orc_patch* p, const orc_source* s, double* U, double* Bx, dou
   grid G;
   work w;
   if (make_grid(p, &G) || work_alloc(&G, &w)) return -1;
+  set_floors(&G, s);
   const double* Bin[3] = {Bx, By, Bz};
   double* Bout[3] = {Bx, By, Bz};
   load_state(&G, U, Bin, w.Un);
-  vl2_step(&G, s, &w, dt);
+  long floored = vl2_step(&G, s, &w, dt);
   store_state(&G, w.Un, U, Bout);
   free(w.block);
-  return 0;
+  return floored > 2147483647L ? 2147483647 : (int)floored;
 }
 
-double orc_cfl_dt(const orc_patch* p, const double* U, const double* Bx, const double* By,
-                  const double* Bz, double cfl) {
+double orc_cfl_dt(const orc_patch* p, const orc_source* s, const double* U, const double* Bx,
+                  const double* By, const double* Bz, double cfl) {
   grid G;
   work w;
   if (make_grid(p, &G) || work_alloc(&G, &w)) return -1.0;
+  set_floors(&G, s);
   const double* Bin[3] = {Bx, By, Bz};
   load_state(&G, U, Bin, w.Un);
   fill_ghosts(&G, w.Un);
@@ -743,6 +803,7 @@ int orc_run(const orc_patch* p, const orc_source* s, double* U, double* Bx, doub
   grid G;
   work w;
   if (make_grid(p, &G) || work_alloc(&G, &w)) return -1;
+  set_floors(&G, s);
   const double* Bin[3] = {Bx, By, Bz};
   double* Bout[3] = {Bx, By, Bz};
   load_state(&G, U, Bin, w.Un);

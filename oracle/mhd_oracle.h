@@ -37,15 +37,23 @@ typedef struct {
   int potential;
   double psi0, xc, xw; /* Gaussian well Psi = -psi0 exp(-((x-xc)/xw)^2) (bow-shock test) */
   double v0, rc;       /* logarithmic potential Psi = v0^2/2 ln(x^2+y^2+rc^2+z^2) */
+  /* Floors (the paper states none; reading for the disc run).  rho_floor > 0 turns them
+   * on: the primitive recovery uses rho_f = max(rho, rho_floor) and clamps p to
+   * [rho_f pr_floor, rho_f pr_ceil]; after each full step every interior cell gets
+   * rho' = max(rho, rho_floor), momentum kept, p recomputed with rho' and clamped the
+   * same way, E rebuilt from them.  pr_ceil <= 0: no ceiling. */
+  double rho_floor, pr_floor, pr_ceil;
 } orc_source;
 
 /* One van Leer predictor-corrector step of size dt (Eq. 7, Eq. 8).  Arrays are
- * updated in place.  Returns 0, or -1 on bad arguments. */
+ * updated in place.  Returns the number of interior cells the end-of-step floors
+ * changed (0 with floors off), or -1 on bad arguments. */
 int orc_step(const orc_patch* p, const orc_source* s, double* U, double* Bx,
              double* By, double* Bz, double dt);
 
-/* cfl * min over interior cells and active axes of d/(|v_d| + c_f,d). */
-double orc_cfl_dt(const orc_patch* p, const double* U, const double* Bx,
+/* cfl * min over interior cells and active axes of d/(|v_d| + c_f,d), from the
+ * recovered primitives (with the floors of s when s is not NULL). */
+double orc_cfl_dt(const orc_patch* p, const orc_source* s, const double* U, const double* Bx,
                   const double* By, const double* Bz, double cfl);
 
 /* Advance to t_end with CFL steps (the last one clipped so t_end is hit).

@@ -386,3 +386,87 @@ def test_ryu_jones_shock_mach_numbers():
     slow = sorted([m[1][1], m[2][1]])
     for got, want in zip(fast + slow, sorted(gold["fast"]) + sorted(gold["slow"])):
         assert abs(got - want) <= 0.015 * want, (fast, slow)
+
+
+# ----------------------------------------------------------------- floors ----
+# The paper states no floors; the reading taken for the disc run raises rho to
+# rho_floor and clamps p to [rho pr_floor, rho pr_ceil], in the primitive recovery and
+# on the conserved state after each full step (momentum kept, E rebuilt by the closure
+# after Eq. 3).  These pins fix that definition on states where the scheme itself is
+# exact: a uniform primitive state is steady (Eq. 7 and Eq. 8 cancel bit for bit).
+
+def _pressure(st):
+    bx, by, bz = st.bcc()
+    kin = 0.5 * (st.U[1] ** 2 + st.U[2] ** 2 + st.U[3] ** 2) / st.U[0]
+    return (st.geom.gamma - 1.0) * (st.U[4] - kin - 0.5 * (bx * bx + by * by + bz * bz))
+
+
+def test_floors_inactive_are_bitwise_neutral():
+    """Floors that no cell reaches change nothing, bit for bit, and count nothing."""
+    st = inputs.turbulence(12, seed=5)
+    dt = oracle.cfl_dt(st, 0.4)
+    a = oracle.step(st, dt, nsteps=2)
+    counts = []
+    b = oracle.step(st, dt, source={"rho_floor": 1e-12, "pr_floor": 1e-12, "pr_ceil": 1e12}, nsteps=2,
+                    floored=counts)
+    assert counts == [0, 0]
+    for f in ("U", "Bx", "By", "Bz"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))
+    assert oracle.cfl_dt(st, 0.4, source={"rho_floor": 1e-12, "pr_floor": 1e-12}) == dt
+
+
+def test_density_floor_keeps_momentum_and_pressure():
+    """One cell below rho_floor in an otherwise uniform state at rest: the recovery sees
+    a uniform primitive state (so no flux moves anything), and the end-of-step floor
+    raises that cell's rho to rho_floor with its momentum (zero) and pressure kept."""
+    g = inputs.Geom(9, 7, 5, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (0,) * 6, 5.0 / 3.0)
+    st = inputs.uniform(g, 1.0, (0.0, 0.0, 0.0), 0.8, (0.3, -0.2, 0.1))
+    U = st.U.copy()
+    U[0, 2, 3, 4] = 0.5
+    st = st.replace(U=U)
+    counts = []
+    out = oracle.step(st, 0.01, source={"rho_floor": 1.0}, floored=counts)
+    assert counts == [1]
+    assert out.U[0, 2, 3, 4] == 1.0
+    assert np.all(out.U[1:4] == 0.0)
+    assert abs(_pressure(out)[2, 3, 4] - 0.8) <= 1e-15
+    mask = np.ones(U.shape[1:], bool)
+    mask[2, 3, 4] = False
+    assert np.array_equal(out.U[:, mask], st.U[:, mask])
+    for f in ("Bx", "By", "Bz"):
+        assert np.array_equal(getattr(out, f), getattr(st, f))
+
+
+@pytest.mark.parametrize("p0, bounds, want", [(1e-3, {"pr_floor": 0.01}, 0.013),
+                                              (50.0, {"pr_ceil": 10.0}, 13.0)])
+def test_pressure_floor_and_ceiling(p0, bounds, want):
+    """Uniform moving state with p outside [rho pr_floor, rho pr_ceil] (rho = 1.3): every
+    cell ends the step at the bound, with rho and momentum unchanged."""
+    g = inputs.Geom(8, 6, 4, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (0,) * 6, 5.0 / 3.0)
+    st = inputs.uniform(g, 1.3, (0.2, -0.1, 0.3), p0, (0.4, 0.1, -0.2))
+    counts = []
+    out = oracle.step(st, 0.01, source=dict(rho_floor=1e-6, **bounds), floored=counts)
+    assert counts == [g.ncell]
+    assert np.array_equal(out.U[:4], st.U[:4])
+    assert np.max(np.abs(_pressure(out) - want)) <= 1e-13 * want
+
+
+def test_floors_remove_a_negative_pressure_cell():
+    """A cell whose energy gives p < 0: without floors the step keeps a negative pressure;
+    with floors the CFL step is finite and positive, the cell is counted, and every cell
+    ends the step with p >= rho pr_floor."""
+    st = inputs.smooth_random(inputs.Geom(10, 8, 6, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (1,) * 6, 5.0 / 3.0), seed=3)
+    U = st.U.copy()
+    U[4, 3, 4, 5] = 0.0  # no internal energy left: p < 0 from the kinetic and field terms
+    st = st.replace(U=U)
+    assert _pressure(st)[3, 4, 5] < 0.0
+    src = {"rho_floor": 1e-3, "pr_floor": 1e-2}
+    dt = oracle.cfl_dt(st, 0.4, source=src)
+    assert np.isfinite(dt) and dt > 0.0
+    with np.errstate(all="ignore"):
+        bad = oracle.step(st, dt)
+    assert np.nanmin(_pressure(bad)) < 0.0
+    counts = []
+    out = oracle.step(st, dt, source=src, floored=counts)
+    assert np.all(np.isfinite(out.U)) and counts[0] >= 1
+    assert np.all(_pressure(out) >= 1e-2 * out.U[0] * (1.0 - 1e-12))
