@@ -242,25 +242,28 @@ def run_batched(args, stream, world=1, rank=0, pg=None):
 
 def run_disc(args, stream):
     """Isolated gas disc (512x512x128 on 40x40x10 kpc, outflow, logarithmic potential in S,
-    toroidal field with beta 10) with the thermal source: the plain FP64 integrator for the
-    first steps (harvesting training pairs), the surrogate trained on the GPU, then the
-    surrogate with per-cell fallback.  Reports the thermal phase's GPU time per step both
-    ways (CUDA events around its kernels), the fallback fraction, and the L1-relative
-    difference in T after the same steps taken with the plain integrator from the same state."""
+    toroidal field with beta 10, density and temperature floors) with the thermal source:
+    the plain FP64 integrator for the first 50 steps (harvesting training pairs), the
+    surrogate trained on the GPU, then 150 steps of the surrogate with per-cell fallback.
+    Reports the thermal phase's GPU time per step both ways (CUDA events around its kernels),
+    the fallback fraction, and the L1-relative difference in T after the 150 steps against
+    the plain integrator run from the same state."""
     import torch
     from paper_1502_02935_gb300 import inputs, mhd
     th = inputs.DISC_THERMAL
     nx, ny, nz = args.disc
     st = inputs.disc(nx, ny, nz)
+    harvest_steps, k = args.disc_steps
     out = {"workload": f"disc {nx}x{ny}x{nz} on 40x40x10 kpc, outflow, log potential v0=220 km/s, beta=10, "
-                       "T=1e4 K, thermal source (stand-in cooling table), mixed path",
+                       "T=1e4 K, floors rho>=1e-4 rho0 and 10 K<=T<=1e8 K, thermal source (stand-in cooling "
+                       f"table), mixed path, {harvest_steps} plain + {k} surrogate steps",
            "cells": st.geom.ncell}
     g = mhd.Grid(st, precision="mixed", cfl=CFL, flags=mhd.FLAG_GRAPH, stream=stream.cuda_stream)
-    g.set_sources(**inputs.DISC_POTENTIAL)
+    g.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
     g.set_thermal(mhd.THERMAL_PLAIN, **th)
-    harvest_steps = 6
-    # each sampled cell yields three pairs (dt, dt/3, 3 dt): size the stride to fill the ring once
-    g.surrogate_harvest(1 << 21, stride=max(1, 3 * st.geom.ncell * harvest_steps // (1 << 21)))
+    # each sampled cell yields four pairs (its own and three shifted): size the stride to fill
+    # the ring once
+    g.surrogate_harvest(1 << 21, stride=max(1, 4 * st.geom.ncell * harvest_steps // (1 << 21)))
     g.set_profiling(True)
     for _ in range(harvest_steps):
         g.step(-1.0)
@@ -274,11 +277,11 @@ def run_disc(args, stream):
     mid = g.get_state(0)
     g.set_thermal(mhd.THERMAL_SURROGATE, **th)
     h = mhd.Grid(mid, precision="mixed", cfl=CFL, flags=mhd.FLAG_GRAPH, stream=stream.cuda_stream)
-    h.set_sources(**inputs.DISC_POTENTIAL)
+    h.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
     h.set_thermal(mhd.THERMAL_PLAIN, **th)
+    del mid
     s0 = g.thermal_stats()
     g.set_profiling(True)
-    k = 5
     for _ in range(k):
         g.step(-1.0)
         h.step(-1.0)
@@ -294,7 +297,9 @@ def run_disc(args, stream):
         p = (x.geom.gamma - 1) * (x.U[4] - kin - 0.5 * (bx * bx + by * by + bz * bz))
         return th["t_per_pr"] * p / x.U[0]
 
-    Ts, Tp = temperature(g.get_state(0)), temperature(h.get_state(0))
+    Ts = temperature(g.get_state(0))
+    Tp = temperature(h.get_state(0))
+    floored = g.metrics()["floored"]
     g.close()
     h.close()
     out.update({"thermal_ms_plain": plain_ms, "thermal_ms_surrogate": sur_ms, "thermal_gain": plain_ms / sur_ms,
@@ -302,6 +307,7 @@ def run_disc(args, stream):
                 "zone_updates_per_s_plain": st.geom.ncell / (step_ms_plain / 1e3),
                 "zone_updates_per_s_surrogate": st.geom.ncell / (step_ms_sur / 1e3),
                 "fallback_fraction": (s1["fallback"] - s0["fallback"]) / max(1, s1["cells"] - s0["cells"]),
+                "floored_cells_total": floored,
                 "train_rows": rows, "train_loss": loss, "train_s": train_s,
                 "l1_T_vs_plain_after_%d_steps" % k: float(np.mean(np.abs(Ts - Tp)) / np.mean(np.abs(Tp)))})
     return out
@@ -441,6 +447,8 @@ def main():
                     help="skip the 64-patch batched workload")
     ap.add_argument("--disc", type=int, nargs=3, default=[512, 512, 128],
                     help="disc workload cells (nx ny nz); 0 0 0 skips it")
+    ap.add_argument("--disc-steps", dest="disc_steps", type=int, nargs=2, default=[50, 150],
+                    help="disc workload: plain (harvest) steps, then surrogate steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.disc == [0, 0, 0]:

@@ -87,11 +87,18 @@ typedef struct {
 /* External potential entering the source vector S of Eq. 2:
  * S = [0, -rho grad Psi, -rho v . grad Psi, 0, 0, 0].
  *   MHD_POT_GAUSS_X : Psi = -psi0 exp(-((x - xc)/xw)^2)
- *   MHD_POT_LOG_DISC: Psi = v0^2/2 ln(x^2 + y^2 + rc^2 + z^2) */
+ *   MHD_POT_LOG_DISC: Psi = v0^2/2 ln(x^2 + y^2 + rc^2 + z^2)
+ * Floors (the paper states none; rho_floor > 0 turns them on, 0 leaves the step bitwise
+ * unchanged): the primitive recovery uses rho_f = max(rho, rho_floor) and clamps p to
+ * [rho_f pr_floor, rho_f pr_ceil]; after each full step, before the thermal term, every
+ * interior cell gets rho' = max(rho, rho_floor), its momentum kept, p recomputed with rho'
+ * and clamped the same way, and E rebuilt from them; changed cells are counted
+ * (mhd_metrics.floored).  pr_floor <= 0: no pressure floor; pr_ceil <= 0: no ceiling. */
 typedef struct {
   int potential;
   double psi0, xc, xw;
   double v0, rc;
+  double rho_floor, pr_floor, pr_ceil;
 } mhd_source_desc;
 
 /* Thermal source term (heating and cooling in S of Eq. 2; the thermal module of
@@ -117,6 +124,7 @@ typedef struct {
   double sums[5];        /* interior totals of rho, rho v, E over all patches */
   double max_divb;       /* max over cells of |div B| * min(dx) */
   int error_word;        /* sticky device error bits */
+  unsigned long long floored; /* cells changed by the end-of-step floors since init */
 } mhd_metrics;
 
 typedef struct mhd_ctx mhd_ctx; /* opaque, library-owned */
@@ -127,7 +135,7 @@ typedef struct mhd_ctx mhd_ctx; /* opaque, library-owned */
 int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* grid, const double* const* U0,
                   const double* const* Bface0, int on_device);
 
-/* Set the external potential (Eq. 2 source vector).  Default: none. */
+/* Set the external potential (Eq. 2 source vector) and the floors.  Default: none. */
 int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* src);
 
 /* Advance every patch by one van Leer step (Eq. 7, Eq. 8).  dt > 0: that dt for
@@ -168,35 +176,50 @@ int mhd_set_thermal(mhd_ctx* ctx, const mhd_thermal_desc* th);
 int mhd_thermal_stats(mhd_ctx* ctx, unsigned long long* out4);
 
 /* Surrogate of the thermal source (a 4 -> 64 -> 64 -> 1 tanh network on x = (log10 n_H,
- * log10 T, log10 dt, Z) mapped to [-1, 1] by the training range, predicting the change of
- * log10 T over dt; the 64x64 layer on BF16 tensor cores with FP32 accumulation).
+ * log10 T, log10 dt, Z) mapped to [-1, 1] by the training range; the 64x64 layer on BF16
+ * tensor cores with FP32 accumulation).  The network predicts q, the change of log10 T
+ * over dt in units of S = D / (1 + |D|), where D = rate(T) dt / (T ln 10) is the explicit
+ * estimate of the change, rate = (n_H Gamma - n_H^2 Lambda(T, Z)) / (rate_unit c_e), both
+ * evaluated in FP32 at x; the change applied is q S.  (Small changes: S ~ D and the error is
+ * relative to the change; stiff cells: |S| -> 1 and q is the change itself.)  A cell falls
+ * back to the plain integrator when a standardised input leaves [-1, 1], when |q| > qmax,
+ * or when |q S| > dmax or is not finite.  Harvested rows are 6 floats (log10 n_H, log10 T,
+ * log10 dt, Z, q, change) with q clipped to [-8, 8] (q = 1 where S is 0).
  *
  * mhd_surrogate_harvest: while the thermal mode is MHD_THERMAL_PLAIN, record training pairs
  * from the plain integrator into a device ring of `capacity` rows, from about one cell in
  * `stride` per step (a hash of the cell index salted by the step's dt).  Each sampled cell
- * gives three rows: the step's dt and, integrated again, dt/3 and 3 dt.  capacity 0 stops.
+ * gives four rows: its own (n_H, T, dt) pair and three pairs integrated again at n_H, T and dt
+ * each shifted by an independent hashed offset uniform in [-0.5, 0.5] decades (c_e scaled with
+ * n_H), so that the training set covers a neighbourhood of the visited states.  capacity 0
+ * stops.
  *
  * mhd_surrogate_train: train on the harvested pairs on the GPU: MSE loss, Adam (beta1 0.9,
  * beta2 0.999) on FP32 master weights with the learning rate decayed from lr to lr/20 on a
  * cosine, minibatches of `batch` rows drawn with a hash of (seed, step, row), `epochs`
  * passes of rows/batch steps, weights initialised from seed.
- * dmax > 0 is the fallback bound on the predicted |change of log10 T|; dmax <= 0 takes 1.25
- * times the largest change in the training set.  loss_out receives the mean squared error of the
+ * qmax > 0 is the fallback bound on the predicted |q|; qmax <= 0 takes 1.25 times the
+ * largest |q| in the training set.  dmax is 1.25 times the largest |change| there.  loss_out receives the mean squared error of the
  * last epoch, rows_out the number of training rows (either may be NULL).  Harvesting stops.
  *
  * mhd_surrogate_params: copy the FP32 parameters out (4545 floats: W1[64][4], b1[64],
- * W2[64][64], b2[64], w3[64], b3) and, if range_out is not NULL, 9 floats: the input
- * offsets lo[4], scales s[4] (x_s = (x - lo) s - 1) and dmax. */
+ * W2[64][64], b2[64], w3[64], b3) and, if range_out is not NULL, 10 floats: the input
+ * offsets lo[4], scales s[4] (x_s = (x - lo) s - 1), qmax and dmax.
+ *
+ * mhd_surrogate_rows: copy up to max_rows harvested rows (6 floats each, in ring order) to
+ * the host buffer rows_out; count_out (may be NULL) receives the number of rows held.
+ * MHD_ERR_STATE if harvesting was never set up.  Synchronises the context's stream. */
 int mhd_surrogate_harvest(mhd_ctx* ctx, long long capacity, int stride);
-int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double dmax,
+int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double qmax,
                         double* loss_out, long long* rows_out);
 int mhd_surrogate_params(mhd_ctx* ctx, float* params_out, float* range_out);
+int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long long* count_out);
 
 /* Per-kernel timing.  While on, every launch is bracketed by a CUDA event pair on the
  * context's stream (steps are not replayed from a graph) and the elapsed times are summed
  * per kernel class: 0 recovery+CFL, 1-3 donor-cell HLLD fluxes x/y/z, 4-6 kappa-scheme
  * HLLD fluxes x/y/z, 7 corner EMFs, 8 update, 9 standalone CFL, 10 persistent step,
- * 11 thermal source.  Switching on or off clears the totals. */
+ * 11 thermal source, 12 end-of-step floors.  Switching on or off clears the totals. */
 int mhd_set_profiling(mhd_ctx* ctx, int on);
 
 /* Totals since profiling was switched on: ms[c] milliseconds and launches[c] launches of
@@ -242,8 +265,9 @@ int mhd_thermal_cells(long long n, const double* T0, const double* nh, const dou
 /* Unit-level entries for parity tests of the surrogate kernels (device pointers; params
  * in the layout of mhd_surrogate_params; inputs already in [-1, 1]):
  * mhd_mlp_forward: y[n] for xs[n][4].
- * mhd_mlp_grad: gradient (4545 floats) of the mean squared error over rows[n][5]
- * (x0..x3, target) and the sum of squared errors in *loss_sum.  Synchronise stream. */
+ * mhd_mlp_grad: gradient (4545 floats) of the mean squared error over rows[n][6] in the
+ * harvested-row layout (x0..x3, target, one column the gradient ignores) and the sum of
+ * squared errors in *loss_sum.  Synchronise stream. */
 int mhd_mlp_forward(long long n, const float* xs, const float* params, float* y, void* stream);
 /* The same forward pass with the 64x64 layer on tcgen05 tensor cores (TMEM accumulator);
  * MHD_ERR_TIMEOUT if the bounded wait for the MMA ran out. */

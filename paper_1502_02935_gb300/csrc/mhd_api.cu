@@ -51,6 +51,20 @@ __global__ void k_unpack(PatchDev P, const double* __restrict__ in, double* __re
     unpack_point(P, in, U, t);
 }
 
+// End-of-step floors over the interior cells of one patch; changed cells are counted.
+__global__ void __launch_bounds__(256) k_floor(PatchDev P) {
+  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+  unsigned changed = 0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % P.n[0]);
+    const long long r = c / P.n[0];
+    changed += (unsigned)floor_point(P, P.Un, i, (int)(r % P.n[1]), (int)(r / P.n[1]));
+  }
+  const unsigned tot = __reduce_add_sync(0xffffffffu, changed);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.floored, (unsigned long long)tot);
+}
+
 unsigned grid_for(long long n) {
   long long b = (n + 255) / 256;
   return (unsigned)(b < 1 ? 1 : (b > 65535LL * 32 ? 65535LL * 32 : b));
@@ -67,6 +81,7 @@ struct mhd_ctx {
   Backend be{};
   SourceDev src{};
   unsigned long long* cfl_min = nullptr;
+  unsigned long long* floored = nullptr;  // end-of-step floor count
   double* dt_used = nullptr;
   int* err = nullptr;
   double* staging = nullptr;
@@ -143,6 +158,7 @@ static void free_ctx(mhd_ctx* ctx) {
   if (ctx->dPre) cudaFree(ctx->dPre);
   if (ctx->bar) cudaFree(ctx->bar);
   if (ctx->cfl_min) cudaFree(ctx->cfl_min);
+  if (ctx->floored) cudaFree(ctx->floored);
   if (ctx->dt_used) cudaFree(ctx->dt_used);
   if (ctx->err) cudaFree(ctx->err);
   if (ctx->staging) cudaFree(ctx->staging);
@@ -312,9 +328,24 @@ static int issue_thermal_all(mhd_ctx* ctx) {
   return MHD_OK;
 }
 
+static int issue_floors(mhd_ctx* ctx) {
+  for (auto& p : ctx->P) {
+    if (!p.dev.floors) continue;
+    ProfScope ps(ctx->profiling && ctx->prof.n < ProfRec::kMax ? &ctx->prof : nullptr, KC_FLOOR, ctx->stream);
+    const long long nc = (long long)p.dev.n[0] * p.dev.n[1] * p.dev.n[2];
+    long long blocks = (nc + 255) / 256;
+    if (blocks > (long long)ctx->sms * 8) blocks = (long long)ctx->sms * 8;
+    k_floor<<<(unsigned)blocks, 256, 0, ctx->stream>>>(p.dev);
+    ctx->launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "floor launch");
+  }
+  return MHD_OK;
+}
+
 static int issue_step(mhd_ctx* ctx, double dt) {
   if (ctx->persistent) {
     int rc = issue_persistent_step(ctx, dt);
+    if (rc == MHD_OK) rc = issue_floors(ctx);
     if (rc == MHD_OK) rc = issue_thermal_all(ctx);
     if (rc == MHD_OK && ctx->profiling) return flush_profile(ctx);
     return rc;
@@ -335,7 +366,8 @@ static int issue_step(mhd_ctx* ctx, double dt) {
         return cuda_fail(ctx, cudaGetLastError(), "stage launch");
     }
   }
-  int rc = issue_thermal_all(ctx);
+  int rc = issue_floors(ctx);
+  if (rc == MHD_OK) rc = issue_thermal_all(ctx);
   if (rc) return rc;
   if (ctx->profiling) return flush_profile(ctx);
   return MHD_OK;
@@ -374,9 +406,11 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
   }
   if (cudaMalloc(&ctx->cfl_min, sizeof(unsigned long long) * ctx->np) != cudaSuccess ||
       cudaMalloc(&ctx->dt_used, sizeof(double) * ctx->np) != cudaSuccess ||
-      cudaMalloc(&ctx->err, sizeof(int)) != cudaSuccess)
+      cudaMalloc(&ctx->err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->floored, sizeof(unsigned long long)) != cudaSuccess)
     return bail(MHD_ERR_NOMEM);
   cudaMemset(ctx->err, 0, sizeof(int));
+  cudaMemset(ctx->floored, 0, sizeof(unsigned long long));
   cudaMemset(ctx->dt_used, 0, sizeof(double) * ctx->np);
   long long max_dense = 0;
   ctx->P.resize(ctx->np);
@@ -439,6 +473,10 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     D.dt_used = ctx->dt_used + p;
     D.err = ctx->err;
     D.index = p;
+    D.floors = 0;
+    D.rho_floor = D.pr_floor = 0.0;
+    D.pr_ceil = INFINITY;
+    D.floored = ctx->floored;
   }
   if (cudaMalloc(&ctx->staging, sizeof(double) * (size_t)max_dense) != cudaSuccess)
     return bail(MHD_ERR_NOMEM);
@@ -466,6 +504,18 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
   ctx->src.xw = s->xw;
   ctx->src.v0 = s->v0;
   ctx->src.rc = s->rc;
+  if (!(s->rho_floor >= 0.0) || !std::isfinite(s->rho_floor) || !std::isfinite(s->pr_floor) ||
+      std::isnan(s->pr_ceil))
+    return fail(ctx, MHD_ERR_ARG, "floors must be finite and rho_floor >= 0");
+  if (s->rho_floor > 0.0 && s->pr_ceil > 0.0 && s->pr_floor > s->pr_ceil)
+    return fail(ctx, MHD_ERR_ARG, "pr_floor above pr_ceil");
+  for (auto& p : ctx->P) {
+    p.dev.floors = s->rho_floor > 0.0;
+    p.dev.rho_floor = s->rho_floor > 0.0 ? s->rho_floor : 0.0;
+    p.dev.pr_floor = s->rho_floor > 0.0 && s->pr_floor > 0.0 ? s->pr_floor : 0.0;
+    p.dev.pr_ceil = s->rho_floor > 0.0 && s->pr_ceil > 0.0 ? s->pr_ceil : INFINITY;
+  }
+  if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   if (ctx->gexec) {  // sources are baked into captured launches
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
@@ -567,6 +617,7 @@ int mhd_get_metrics(mhd_ctx* ctx, mhd_metrics* m) {
   memset(m, 0, sizeof(*m));
   CK(cudaMemcpyAsync(&m->dt_last, ctx->dt_used, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&m->error_word, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&m->floored, ctx->floored, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int p = 0; p < ctx->np; ++p) {
     PatchHost& H = ctx->P[p];
@@ -664,7 +715,7 @@ int mhd_surrogate_harvest(mhd_ctx* ctx, long long capacity, int stride) {
     cudaFree(ctx->dataset);
     ctx->dataset = nullptr;
   }
-  if (!ctx->dataset && cudaMalloc(&ctx->dataset, sizeof(float) * 5 * (size_t)capacity) != cudaSuccess)
+  if (!ctx->dataset && cudaMalloc(&ctx->dataset, sizeof(float) * kHvCols * (size_t)capacity) != cudaSuccess)
     return fail(ctx, MHD_ERR_NOMEM, "harvest buffer");
   if (!ctx->ds_count && cudaMalloc(&ctx->ds_count, sizeof(unsigned long long)) != cudaSuccess)
     return fail(ctx, MHD_ERR_NOMEM, "harvest counter");
@@ -678,7 +729,20 @@ int mhd_surrogate_harvest(mhd_ctx* ctx, long long capacity, int stride) {
   return MHD_OK;
 }
 
-int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double dmax,
+int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long long* count_out) {
+  if (!ctx || max_rows < 0 || (max_rows > 0 && !rows_out)) return MHD_ERR_ARG;
+  if (!ctx->dataset || !ctx->ds_count) return fail(ctx, MHD_ERR_STATE, "no harvest buffer");
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, ctx->ds_count, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const long long held = (long long)(cnt < (unsigned long long)ctx->ds_cap ? cnt : (unsigned long long)ctx->ds_cap);
+  const long long n = held < max_rows ? held : max_rows;
+  if (n > 0) CK(cudaMemcpy(rows_out, ctx->dataset, sizeof(float) * kHvCols * (size_t)n, cudaMemcpyDeviceToHost));
+  if (count_out) *count_out = held;
+  return MHD_OK;
+}
+
+int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double qmax,
                         double* loss_out, long long* rows_out) {
   if (!ctx || epochs < 1 || batch < 64 || batch > (1 << 20) || !(lr > 0.0) || seed == 0) return MHD_ERR_ARG;
   if (!ctx->dataset || !ctx->ds_count) return fail(ctx, MHD_ERR_STATE, "no harvested training pairs");
@@ -690,16 +754,17 @@ int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned
   const long long rows = (long long)(cnt < (unsigned long long)ctx->ds_cap ? cnt : (unsigned long long)ctx->ds_cap);
   if (rows < 64) return fail(ctx, MHD_ERR_STATE, "fewer than 64 harvested training pairs");
   // feature range of the training set (the surrogate's validity domain)
-  std::vector<float> host((size_t)rows * 5);
+  std::vector<float> host((size_t)rows * kHvCols);
   CK(cudaMemcpy(host.data(), ctx->dataset, sizeof(float) * host.size(), cudaMemcpyDeviceToHost));
-  float lo[4], hi[4], ymax = 0.f;
+  float lo[4], hi[4], qabs = 0.f, dabs = 0.f;
   for (int f = 0; f < 4; ++f) lo[f] = hi[f] = host[f];
   for (long long r = 0; r < rows; ++r) {
     for (int f = 0; f < 4; ++f) {
-      lo[f] = std::min(lo[f], host[r * 5 + f]);
-      hi[f] = std::max(hi[f], host[r * 5 + f]);
+      lo[f] = std::min(lo[f], host[r * kHvCols + f]);
+      hi[f] = std::max(hi[f], host[r * kHvCols + f]);
     }
-    ymax = std::max(ymax, std::fabs(host[r * 5 + 4]));
+    qabs = std::max(qabs, std::fabs(host[r * kHvCols + 4]));
+    dabs = std::max(dabs, std::fabs(host[r * kHvCols + 5]));
   }
   // standardisation range: the training range, widened to at least 0.2 (a fifth of a
   // decade for the logarithmic features) so that a nearly constant feature such as log dt
@@ -713,7 +778,8 @@ int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned
     ctx->mdev.xlo[f] = lo[f];
     ctx->mdev.xscale[f] = 2.0f / (hi[f] - lo[f]);
   }
-  ctx->mdev.dmax = dmax > 0.0 ? (float)dmax : 1.25f * ymax;
+  ctx->mdev.qmax = qmax > 0.0 ? (float)qmax : 1.25f * qabs;
+  ctx->mdev.dmax = 1.25f * dabs;
   // initial weights: uniform(-a, a) with a = sqrt(6/(fan_in + fan_out)), seeded
   std::vector<float> p0(kNParam, 0.f);
   std::mt19937_64 gen(seed);
@@ -765,7 +831,8 @@ int mhd_surrogate_params(mhd_ctx* ctx, float* params_out, float* range_out) {
       range_out[f] = ctx->mdev.xlo[f];
       range_out[4 + f] = ctx->mdev.xscale[f];
     }
-    range_out[8] = ctx->mdev.dmax;
+    range_out[8] = ctx->mdev.qmax;
+    range_out[9] = ctx->mdev.dmax;
   }
   return MHD_OK;
 }
@@ -964,6 +1031,7 @@ static MlpDev unit_mlp(const float* params, __nv_bfloat16* w2h) {
     M.xlo[f] = -1.0f;  // identity standardisation: inputs are already in [-1, 1]
     M.xscale[f] = 1.0f;
   }
+  M.qmax = 1e30f;
   M.dmax = 1e30f;
   return M;
 }

@@ -10,7 +10,7 @@ struct PersistentArgs;
 
 // Optional per-launch CUDA-event pairs recorded on the launching stream.
 enum { KC_PRIM = 0, KC_FLUX1 = 1, KC_FLUX2 = 4, KC_EMF = 7, KC_UPDATE = 8, KC_CFL = 9, KC_PERSISTENT = 10,
-       KC_THERMAL = 11, KC_COUNT = 12 };
+       KC_THERMAL = 11, KC_FLOOR = 12, KC_COUNT = 13 };
 struct ProfRec {
   static constexpr int kMax = 64;
   cudaEvent_t a[kMax], b[kMax];

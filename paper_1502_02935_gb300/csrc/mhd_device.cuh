@@ -49,6 +49,10 @@ struct PatchDev {
   double* dt_used;
   int* err;
   int index;
+  // floors (off unless floors != 0): rho >= rho_floor, rho pr_floor <= p <= rho pr_ceil
+  int floors;
+  double rho_floor, pr_floor, pr_ceil;
+  unsigned long long* floored;  // count of cells changed by the end-of-step floors
 };
 
 struct SourceDev {
@@ -391,7 +395,8 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
   const int ci = cmap(P, 0, i), cj = cmap(P, 1, j), ck = cmap(P, 2, k);
   const long long FS = P.FS;
   const long long c = sidx(P, ci, cj, ck);
-  const double rho = U[c];
+  double rho = U[c];
+  if (P.floors && rho < P.rho_floor) rho = P.rho_floor;
   const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c], e = U[EN * FS + c];
   // sums of the two face values (twice the cell-centred field of Eq. 6)
   const double sbx = U[BXF * FS + sidx(P, fmap(P, 0, i), cj, ck)] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), cj, ck)];
@@ -400,8 +405,12 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
   const double irho = inv_density<R>(rho);
   const double m2 = mx * mx + my * my + mz * mz;
   const double b2 = sbx * sbx + sby * sby + sbz * sbz;  // 4 |B_cc|^2
-  // p = (gamma-1) (E - |m|^2/(2 rho) - |B_cc|^2/2), in FP64
-  const double p = P.gm1 * e - P.hgm1 * (m2 * irho) - P.egm1 * b2;
+  // p = (gamma-1) (E - |m|^2/(2 rho) - |B_cc|^2/2), in FP64, clamped when floors are on
+  double p = P.gm1 * e - P.hgm1 * (m2 * irho) - P.egm1 * b2;
+  if (P.floors) {
+    const double lo = rho * P.pr_floor, hi = rho * P.pr_ceil;
+    p = p < lo ? lo : (p > hi ? hi : p);  // a NaN passes through to the finiteness check
+  }
   const R rirho = Ar<R>::from_d(irho);
   const R vx = Ar<R>::from_d(mx) * rirho, vy = Ar<R>::from_d(my) * rirho, vz = Ar<R>::from_d(mz) * rirho;
   const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
@@ -440,6 +449,30 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
     lim = (double)lr;
   }
   return lim;
+}
+
+// ----------------------------------------------------------- end-of-step floors --
+// Interior cell (i, j, k) of the new state: rho' = max(rho, rho_floor), momentum kept,
+// p from E with rho' and the cell-centred field of Eq. 6, clamped to
+// [rho' pr_floor, rho' pr_ceil], and E rebuilt by the energy closure (text after Eq. 3)
+// when rho or p changed.  Returns 1 for a changed cell.  (The paper states no floors.)
+__device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict__ U, int i, int j, int k) {
+  const long long FS = P.FS, c = sidx(P, i, j, k);
+  const double rho = U[c];
+  const double rf = rho < P.rho_floor ? P.rho_floor : rho;
+  const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c];
+  const double bx = 0.5 * (U[BXF * FS + c] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)]);
+  const double by = 0.5 * (U[BYF * FS + c] + U[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)]);
+  const double bz = 0.5 * (U[BZF * FS + c] + U[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))]);
+  const double kin = 0.5 * (mx * mx + my * my + mz * mz) / rf;
+  const double mag = 0.5 * (bx * bx + by * by + bz * bz);
+  const double p = P.gm1 * (U[EN * FS + c] - kin - mag);
+  const double lo = rf * P.pr_floor, hi = rf * P.pr_ceil;
+  const double pf = p < lo ? lo : (p > hi ? hi : p);
+  if (rf == rho && pf == p) return 0;
+  U[c] = rf;
+  U[EN * FS + c] = pf / P.gm1 + kin + mag;
+  return 1;
 }
 
 // ------------------------------------------------------------- phase: flux ----

@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(128) k_mlp_grad(MlpDev M, const float* __restr
     if (r < batch) src = seed ? (long long)(mix64(seed ^ mix64((unsigned long long)step * 0x100000001ull + r)) %
                                             (unsigned long long)nrows)
                               : r;
-    for (int f = 0; f < 4; ++f) S.x[q * 4 + f] = src >= 0 ? mlp_standardize(M, f, data[src * 5 + f]) : 0.f;
-    T.t[q] = src >= 0 ? data[src * 5 + 4] : 0.f;
+    for (int f = 0; f < 4; ++f) S.x[q * 4 + f] = src >= 0 ? mlp_standardize(M, f, data[src * kHvCols + f]) : 0.f;
+    T.t[q] = src >= 0 ? data[src * kHvCols + 4] : 0.f;
   }
   __syncthreads();
   mlp_layer1(S, r0);
@@ -233,87 +233,6 @@ __global__ void k_refresh_w2h(const float* __restrict__ p, __nv_bfloat16* __rest
 }
 
 // -------------------------------------------------------- surrogate thermal --
-__device__ __forceinline__ void warp_count(unsigned long long* slot, int v) {
-  const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)v);
-  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(slot, (unsigned long long)tot);
-}
-
-// Per interior cell: network prediction of the change of log10 T over the step, applied
-// to E in FP64; cells outside the training range or over the bound go to the fallback list.
-__global__ void __launch_bounds__(128) k_thermal_surrogate(PatchDev P, ThermalDev th, MlpDev M,
-                                                           int* __restrict__ fb_list,
-                                                           unsigned long long* __restrict__ fb_count) {
-  __shared__ MlpSmem S;
-  __shared__ double sT[kMlpRows], sce[kMlpRows];
-  __shared__ int sok[kMlpRows];
-  mlp_load_weights(S, M);
-  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
-  const double dt = *P.dt_used;
-  const float ldt = (float)log10(dt);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * 16;
-  for (long long base = (long long)blockIdx.x * kMlpRows; base < nc; base += (long long)gridDim.x * kMlpRows) {
-    __syncthreads();
-    if (threadIdx.x < kMlpRows) {
-      const int q = threadIdx.x;
-      const long long c = base + q;
-      int ok = 0;
-      float xs[4] = {0.f, 0.f, 0.f, 0.f};
-      if (c < nc) {
-        const int i = (int)(c % P.n[0]);
-        const long long r = c / P.n[0];
-        const int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
-        double T, nh, ce;
-        th_cell(P, th, P.Un, i, j, k, T, nh, ce);
-        sT[q] = T;
-        sce[q] = ce;
-        const float raw[4] = {(float)log10(nh), (float)log10(th_clamp(T)), ldt, (float)th.z};
-        ok = 1;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          xs[f] = mlp_standardize(M, f, raw[f]);
-          if (!(xs[f] >= -1.0f && xs[f] <= 1.0f)) ok = 0;
-        }
-      }
-      sok[q] = c < nc ? ok : -1;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) S.x[q * 4 + f] = xs[f];
-    }
-    __syncthreads();
-    mlp_layer1(S, r0);
-    __syncwarp();
-    float acc[8][4];
-    mlp_layer2(S, r0, acc);
-    float ylo, yhi;
-    mlp_head(S, acc, ylo, yhi);
-    const int g = lane >> 2;
-    int nfb = 0;
-    if ((lane & 3) == 0) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int q = r0 + g + 8 * h;
-        const float y = h ? yhi : ylo;
-        const long long c = base + q;
-        if (sok[q] < 0) continue;
-        const bool good = sok[q] == 1 && fabsf(y) <= M.dmax && isfinite(y);
-        const int i = (int)(c % P.n[0]);
-        const long long r = c / P.n[0];
-        const int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
-        if (good) {
-          const double T0 = th_clamp(sT[q]);
-          const double T1 = th_clamp(T0 * (double)exp10f(y));
-          P.Un[EN * P.FS + sidx(P, i, j, k)] += sce[q] * (T1 - sT[q]);
-        } else {
-          const unsigned long long slot = atomicAdd(fb_count, 1ull);
-          fb_list[slot] = (int)c;
-          ++nfb;
-        }
-      }
-    }
-    warp_count(th.stats + 3, nfb);
-    warp_count(th.stats + 0, (lane & 3) == 0 ? (int)(base + r0 + g < nc) + (int)(base + r0 + g + 8 < nc) : 0);
-  }
-}
-
 // Plain FP64 integrator on the listed cells (grid-stride over the device-side count).
 __global__ void __launch_bounds__(256) k_thermal_fallback(PatchDev P, ThermalDev th, const int* __restrict__ fb_list,
                                                           const unsigned long long* __restrict__ fb_count) {
@@ -364,12 +283,7 @@ int mlp_refresh(const float* p, __nv_bfloat16* W2h, cudaStream_t s) {
 
 int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
                     unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches) {
-  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
   if (cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s) != cudaSuccess) return -1;
-  long long blocks = (nc + kMlpRows - 1) / kMlpRows;
-  const long long cap = (long long)sms * 8;
-  if (blocks > cap) blocks = cap;
-  (void)blocks;
   if (issue_surrogate_tc(P, th, M, fb_list, fb_count, sms, s, launches)) return -1;
   k_thermal_fallback<<<(unsigned)(sms * 4), 256, 0, s>>>(P, th, fb_list, fb_count);
   *launches += 1;

@@ -2,7 +2,8 @@
 //
 //   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = w3 . h2 + b3,
 // x = (log10 n_H, log10 T, log10 dt, Z) mapped to [-1, 1] by the training range,
-// y = predicted change of log10 T over dt.
+// y = q, the change of log10 T over dt in units of the saturated explicit estimate
+// S = th_scale(th_dlin(x)) (mhd_thermal.cuh); the change applied is q S.
 //
 // The 64x64 layer runs on the tensor cores: BF16 operands (activations h1 and weights W2
 // rounded to BF16), FP32 accumulation.  Inference in the thermal step uses tcgen05.mma with
@@ -27,7 +28,8 @@ struct MlpDev {
   const float* p;            // FP32 parameter block
   const __nv_bfloat16* W2h;  // BF16 copy of W2 [64][64]
   float xlo[4], xscale[4];   // x_s = (x - xlo) * xscale - 1
-  float dmax;                // fallback when |y| > dmax
+  float qmax;                // fallback when |y| > qmax
+  float dmax;                // or when the change |y S| > dmax (or is not finite)
 };
 
 __device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {

@@ -210,20 +210,22 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
   uint32_t phase = 0;
   const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
   const double dt = *P.dt_used;
-  const float ldt = (float)log10(dt);
+  const float ldt = log10f((float)dt);
+  const DlinConst dc = th_dlin_const(th, P.gm1);
   for (long long base = (long long)blockIdx.x * kTcRows; base < nc; base += (long long)gridDim.x * kTcRows) {
     const long long c = base + threadIdx.x;
     int i = 0, j = 0, k = 0;
     bool inrange = false;
     double T = 0.0, nh = 0.0, ce = 0.0;
-    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    float x[4] = {0.f, 0.f, 0.f, 0.f}, dl = 0.f;
     if (c < nc) {
       i = (int)(c % P.n[0]);
       const long long r = c / P.n[0];
       j = (int)(r % P.n[1]);
       k = (int)(r / P.n[1]);
       th_cell(P, th, P.Un, i, j, k, T, nh, ce);
-      const float raw[4] = {(float)log10(nh), (float)log10(th_clamp(T)), ldt, (float)th.z};
+      const float raw[4] = {log10f((float)nh), log10f((float)th_clamp(T)), ldt, (float)th.z};
+      dl = th_scale(th_dlin(dc, raw[0], raw[1], raw[2]));
       inrange = true;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
@@ -241,9 +243,10 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
     int fb = 0, live = 0;
     if (c < nc) {
       live = 1;
-      if (inrange && fabsf(y) <= M.dmax && isfinite(y)) {
+      const float d = y * dl;  // predicted change of log10 T
+      if (inrange && fabsf(y) <= M.qmax && fabsf(d) <= M.dmax) {
         const double T0 = th_clamp(T);
-        const double T1 = th_clamp(T0 * (double)exp10f(y));
+        const double T1 = th_clamp(T0 * (double)exp10f(d));
         P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);
       } else {
         fb_list[atomicAdd(fb_count, 1ull)] = (int)c;

@@ -376,6 +376,10 @@ def alfven_wave(n: int, amp: float = 1e-6, gamma: float = 5.0 / 3.0, polarisatio
 #   energy-rate unit = 2.2e-14 erg cm^-3 / 3.086e16 s = 7.13e-31 erg cm^-3 s^-1.
 DISC_THERMAL = dict(gamma_heat=2e-26, z=0.02, rate_unit=7.13e-31, cap=0.1, nh_per_rho=0.76, t_per_pr=72.7)
 DISC_POTENTIAL = dict(potential=2, v0=220.0, rc=0.5)
+# floors of the disc run: rho >= 1e-4 of the central density (the initial floor of
+# disc() at its default n_H = 5 cm^-3) and 10 K <= T <= 1e8 K as bounds on p/rho
+DISC_FLOORS = dict(rho_floor=1e-4 * (5.0 / DISC_THERMAL["nh_per_rho"]), pr_floor=10.0 / DISC_THERMAL["t_per_pr"],
+                   pr_ceil=1e8 / DISC_THERMAL["t_per_pr"])
 
 
 def disc(nx: int = 512, ny: int = 512, nz: int = 128, n_h0: float = 5.0, T0: float = 1e4, beta: float = 10.0,

@@ -46,7 +46,8 @@ class GridDesc(C.Structure):
 
 class SourceDesc(C.Structure):
     _fields_ = [("potential", C.c_int), ("psi0", C.c_double), ("xc", C.c_double), ("xw", C.c_double),
-                ("v0", C.c_double), ("rc", C.c_double)]
+                ("v0", C.c_double), ("rc", C.c_double), ("rho_floor", C.c_double), ("pr_floor", C.c_double),
+                ("pr_ceil", C.c_double)]
 
 
 class ThermalDesc(C.Structure):
@@ -59,7 +60,7 @@ THERMAL_OFF, THERMAL_PLAIN, THERMAL_SURROGATE = 0, 1, 2
 
 class Metrics(C.Structure):
     _fields_ = [("dt_last", C.c_double), ("sums", C.c_double * 5), ("max_divb", C.c_double),
-                ("error_word", C.c_int)]
+                ("error_word", C.c_int), ("floored", C.c_ulonglong)]
 
 
 _lib = None
@@ -69,7 +70,8 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_last_error", "mhd_destroy", "mhd_riemann_hlld", "mhd_set_profiling", "mhd_get_profile",
            "mhd_cfl_dt_noalloc", "mhd_autotune", "mhd_set_wait_limit", "mhd_set_thermal",
            "mhd_thermal_stats", "mhd_thermal_cells", "mhd_surrogate_harvest", "mhd_surrogate_train",
-           "mhd_surrogate_params", "mhd_mlp_forward", "mhd_mlp_grad", "mhd_mlp_forward_tc"]
+           "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
+           "mhd_mlp_forward_tc"]
 
 
 def lib():
@@ -110,6 +112,7 @@ def lib():
     L.mhd_surrogate_train.argtypes = [vp, ip, ip, C.c_double, C.c_ulonglong, C.c_double, dp,
                                       C.POINTER(C.c_longlong)]
     L.mhd_surrogate_params.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.mhd_surrogate_rows.argtypes = [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
     L.mhd_mlp_forward.argtypes = [C.c_longlong, vp, vp, vp, vp]
     L.mhd_mlp_grad.argtypes = [C.c_longlong, vp, vp, vp, vp, vp]
     L.mhd_mlp_forward_tc.argtypes = [C.c_longlong, vp, vp, vp, vp]
@@ -167,8 +170,9 @@ class Grid:
         if rc != 0:
             raise MHDError(rc, f"{what}: {self.L.mhd_last_error(self.h).decode()}")
 
-    def set_sources(self, potential=POT_NONE, psi0=0.0, xc=0.0, xw=1.0, v0=0.0, rc=0.0):
-        s = SourceDesc(int(potential), psi0, xc, xw, v0, rc)
+    def set_sources(self, potential=POT_NONE, psi0=0.0, xc=0.0, xw=1.0, v0=0.0, rc=0.0, rho_floor=0.0,
+                    pr_floor=0.0, pr_ceil=0.0):
+        s = SourceDesc(int(potential), psi0, xc, xw, v0, rc, rho_floor, pr_floor, pr_ceil)
         self._check(self.L.mhd_set_sources(self.h, C.byref(s)), "mhd_set_sources")
 
     def step(self, dt: float = -1.0):
@@ -217,10 +221,11 @@ class Grid:
     def metrics(self) -> dict:
         m = Metrics()
         self._check(self.L.mhd_get_metrics(self.h, C.byref(m)), "mhd_get_metrics")
-        return {"dt_last": m.dt_last, "sums": list(m.sums), "max_divb": m.max_divb, "error_word": m.error_word}
+        return {"dt_last": m.dt_last, "sums": list(m.sums), "max_divb": m.max_divb, "error_word": m.error_word,
+                "floored": int(m.floored)}
 
     KERNEL_CLASSES = ["recovery", "flux1_x", "flux1_y", "flux1_z", "flux2_x", "flux2_y", "flux2_z",
-                      "emf", "update", "cfl", "persistent", "thermal"]
+                      "emf", "update", "cfl", "persistent", "thermal", "floor"]
 
     def set_thermal(self, mode, gamma_heat=2e-26, z=0.02, rate_unit=7.13e-31, cap=0.1, nh_per_rho=0.76,
                     t_per_pr=72.7):
@@ -230,18 +235,27 @@ class Grid:
     def surrogate_harvest(self, capacity: int, stride: int = 1):
         self._check(self.L.mhd_surrogate_harvest(self.h, int(capacity), int(stride)), "mhd_surrogate_harvest")
 
-    def surrogate_train(self, epochs=20, batch=4096, lr=3e-3, seed=1502, dmax=0.0):
+    def surrogate_train(self, epochs=20, batch=4096, lr=3e-3, seed=1502, qmax=0.0):
         loss = C.c_double()
         rows = C.c_longlong()
-        self._check(self.L.mhd_surrogate_train(self.h, int(epochs), int(batch), float(lr), int(seed), float(dmax),
+        self._check(self.L.mhd_surrogate_train(self.h, int(epochs), int(batch), float(lr), int(seed), float(qmax),
                                                C.byref(loss), C.byref(rows)), "mhd_surrogate_train")
         return loss.value, rows.value
 
     def surrogate_params(self):
         p = (C.c_float * 4545)()
-        r = (C.c_float * 9)()
+        r = (C.c_float * 10)()
         self._check(self.L.mhd_surrogate_params(self.h, p, r), "mhd_surrogate_params")
         return np.frombuffer(p, dtype=np.float32).copy(), np.frombuffer(r, dtype=np.float32).copy()
+
+    def surrogate_rows(self, max_rows: int) -> np.ndarray:
+        """Harvested rows (log10 n_H, log10 T, log10 dt, Z, q, change of log10 T), at most
+        max_rows of them."""
+        buf = np.zeros((max(int(max_rows), 0), 6), dtype=np.float32)
+        held = C.c_longlong()
+        self._check(self.L.mhd_surrogate_rows(self.h, buf.ctypes.data, buf.shape[0], C.byref(held)),
+                    "mhd_surrogate_rows")
+        return buf[:min(buf.shape[0], held.value)].copy()
 
     def thermal_stats(self) -> dict:
         out = (C.c_ulonglong * 4)()
@@ -357,7 +371,8 @@ def mlp_forward(xs, params, tcgen05: bool = False) -> np.ndarray:
 
 def mlp_grad(xs, targets, params):
     import torch
-    rows = np.concatenate([np.asarray(xs, dtype=np.float32), np.asarray(targets, dtype=np.float32)[:, None]], axis=1)
+    t = np.asarray(targets, dtype=np.float32)[:, None]
+    rows = np.concatenate([np.asarray(xs, dtype=np.float32), t, np.zeros_like(t)], axis=1)  # harvested-row layout
     r = torch.as_tensor(np.ascontiguousarray(rows)).cuda()
     p = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float32)).cuda()
     g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")

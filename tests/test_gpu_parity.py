@@ -75,18 +75,20 @@ CASES = {
 }
 
 
-def _run_pair(st, src, precision, nsteps, cfl=0.4):
+def _run_pair(st, src, precision, nsteps, cfl=0.4, counts=None):
     g = mhd.Grid(st, precision=precision, cfl=cfl)
     if src:
         g.set_sources(**src)
     ref = st
-    dts = []
+    dts, floored = [], []
     for _ in range(nsteps):
-        dt = oracle.cfl_dt(ref, cfl)
+        dt = oracle.cfl_dt(ref, cfl, source=src)
         dts.append(dt)
         g.step(dt)
-        ref = oracle.step(ref, dt, source=src)
+        ref = oracle.step(ref, dt, source=src, floored=floored)
     got = g.get_state(0)
+    if counts is not None:
+        counts.extend([g.metrics()["floored"], sum(floored)])
     g.close()
     return got, ref, dts
 
@@ -261,3 +263,75 @@ def test_nonfinite_and_negative_inputs_are_reported():
     with pytest.raises(mhd.MHDError):
         mhd.Grid(inputs.State(inputs.Geom(0, 4, 4), np.zeros((5, 4, 4, 0)), np.zeros((4, 4, 1)),
                               np.zeros((4, 5, 0)), np.zeros((5, 4, 0))))
+
+
+# ----------------------------------------------------------------- floors ----
+
+def _negative_pressure_case():
+    """Smooth outflow box with one cell whose energy leaves p < 0."""
+    st = inputs.smooth_random(_geom((10, 8, 6), (1,) * 6, d=(0.1, 0.1, 0.1)), 3)
+    U = st.U.copy()
+    U[4, 3, 4, 5] = 0.0
+    return st.replace(U=U), {"rho_floor": 1e-3, "pr_floor": 1e-2}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_floors_parity_negative_pressure_cell(precision):
+    """Floors in the recovery and after each step, against the oracle's floors: same
+    state (FP64 bound, or the mixed bound per step) and the same count of floored cells."""
+    st, src = _negative_pressure_case()
+    counts = []
+    got, ref, _ = _run_pair(st, src, precision, 3, counts=counts)
+    if precision == "fp64":
+        assert_close(got, ref, 3 * FP64_TOL, "floors")
+        assert counts[0] == counts[1] and counts[1] >= 1, counts
+    else:
+        assert_close(got, ref, 3 * MIXED_TOL, "floors", normalized=True)
+        assert counts[1] >= 1 and abs(counts[0] - counts[1]) <= 1, counts
+
+
+def test_floors_parity_disc():
+    """Small disc (24 x 24 x 12) with its potential and floors, FP64, three steps.  Cells
+    sitting exactly at the density floor may land either side of it by rounding, so the
+    counts agree to 5 %."""
+    st = inputs.disc(24, 24, 12)
+    src = dict(inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+    counts = []
+    got, ref, _ = _run_pair(st, src, "fp64", 3, counts=counts)
+    assert_close(got, ref, 3 * FP64_TOL, "disc floors")
+    assert counts[1] > 0 and abs(counts[0] - counts[1]) <= 0.05 * counts[1] + 2, counts
+
+
+def test_floors_off_leave_the_step_unchanged():
+    """Floors that no cell reaches leave the device step bit for bit as without them."""
+    st = inputs.turbulence((20, 16, 12), seed=7)
+    a = mhd.Grid(st, precision="fp64", cfl=0.4)
+    b = mhd.Grid(st, precision="fp64", cfl=0.4)
+    b.set_sources(rho_floor=1e-12, pr_floor=1e-12, pr_ceil=1e12)
+    for _ in range(3):
+        a.step(-1.0)
+        b.step(-1.0)
+    sa, sb = a.get_state(0), b.get_state(0)
+    assert np.array_equal(sa.U, sb.U) and np.array_equal(sa.Bz, sb.Bz)
+    assert b.metrics()["floored"] == 0
+    a.close()
+    b.close()
+
+
+def test_disc_with_floors_runs_without_error():
+    """The disc (64 x 64 x 24, mixed path, plain thermal source) reaches negative pressure
+    within a few steps without floors; with them 40 CFL steps complete without a device
+    error, the CFL step stays within a factor 4 of its start, and cells are floored."""
+    st = inputs.disc(64, 64, 24)
+    g = mhd.Grid(st, precision="mixed", cfl=0.4)
+    g.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+    g.set_thermal(mhd.THERMAL_PLAIN, **inputs.DISC_THERMAL)
+    dts = []
+    for _ in range(40):
+        g.step(-1.0)
+        dts.append(g.metrics()["dt_last"])
+    g.sync()
+    m = g.metrics()
+    g.close()
+    assert m["error_word"] == 0 and m["floored"] > 0
+    assert min(dts) >= 0.25 * dts[0], (dts[0], min(dts))

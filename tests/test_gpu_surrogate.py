@@ -79,6 +79,52 @@ def _temperature(st, th):
     return th["t_per_pr"] * p / st.U[0]
 
 
+def test_harvested_labels_match_oracle():
+    """Each harvested row (log10 n_H, log10 T, log10 dt, Z, q, change) is checked against
+    the FP64 oracle: the oracle's integrator gives the change of log10 T from the row's
+    inputs, and its cooling function the explicit estimate D = rate dt / (T ln 10); the
+    row's change must match, and q S with S = D / (1 + |D|) must reproduce it.  The inputs
+    are FP32-rounded and D is evaluated in FP32 on the GPU, so the bound is relative 1e-4 on
+    the change plus 1e-5 of the size of the two rate terms (where heating and cooling nearly
+    cancel, D is a small difference of FP32 numbers)."""
+    th = inputs.DISC_THERMAL
+    st = inputs.disc(32, 32, 16)
+    g = mhd.Grid(st, precision="mixed", cfl=0.4)
+    g.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+    g.set_thermal(mhd.THERMAL_PLAIN, **th)
+    g.surrogate_harvest(1 << 16, stride=3)
+    for _ in range(2):
+        g.step(-1.0)
+    rows = g.surrogate_rows(1 << 16).astype(np.float64)
+    g.close()
+    assert rows.shape[1] == 6 and rows.shape[0] >= 4 * 1000 and rows.shape[0] % 4 == 0, rows.shape
+    nh, T, dt = 10.0 ** rows[:, 0], 10.0 ** rows[:, 1], 10.0 ** rows[:, 2]
+    assert np.all(rows[:, 3] == np.float32(th["z"]))
+    # the jittered rows spread about a decade around the visited states
+    grp = rows[:, 1].reshape(-1, 4)
+    spread = grp[:, 1:] - grp[:, :1]
+    assert spread.min() >= -0.501 and spread.max() <= 0.501 and np.ptp(spread) > 0.8, (spread.min(), spread.max())
+    ce = nh / (th["nh_per_rho"] * th["t_per_pr"] * (st.geom.gamma - 1.0))
+    T1, _ = oracle.thermal_cells(T, nh, ce, dt, th)
+    d_ref = np.log10(T1) - np.log10(T)
+    lam, _ = oracle.cooling(T, th["z"])
+    heat = nh * th["gamma_heat"] / (th["rate_unit"] * ce)
+    cool = nh * nh * lam / (th["rate_unit"] * ce)
+    scale = dt / (T * np.log(10.0))
+    D = (heat - cool) * scale
+    S = D / (1.0 + np.abs(D))
+    q = rows[:, 4]
+    tol = 1e-4 * np.abs(d_ref) + 1e-5 * (heat + cool) * scale * (1.0 + np.abs(q)) + 1e-6
+    err = np.abs(rows[:, 5] - d_ref)
+    bad = np.argmax(err / tol)
+    assert np.all(err <= tol), ("change", float(err[bad]), float(tol[bad]), rows[bad])
+    live = np.abs(q) < 7.9  # clipped labels carry no ratio
+    assert live.mean() > 0.99, live.mean()
+    err = np.abs(q * S - d_ref)[live]
+    bad = np.argmax(err / tol[live])
+    assert np.all(err <= tol[live]), ("q", float(err[bad]), float(tol[live][bad]), rows[live][bad])
+
+
 def test_surrogate_thermal_step_on_disc():
     """Harvest pairs from the plain integrator over 8 steps of a 64x64x24 disc, train on the
     GPU, then run 5 more steps with the surrogate and, from the same state, 5 steps with the
@@ -86,7 +132,7 @@ def test_surrogate_thermal_step_on_disc():
     th = inputs.DISC_THERMAL
     st = inputs.disc(64, 64, 24)
     g = mhd.Grid(st, precision="mixed", cfl=0.4)
-    g.set_sources(**inputs.DISC_POTENTIAL)
+    g.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
     g.set_thermal(mhd.THERMAL_PLAIN, **th)
     g.surrogate_harvest(1 << 20, stride=1)
     for _ in range(8):
@@ -97,7 +143,7 @@ def test_surrogate_thermal_step_on_disc():
     mid = g.get_state(0)
     g.set_thermal(mhd.THERMAL_SURROGATE, **th)
     h = mhd.Grid(mid, precision="mixed", cfl=0.4)
-    h.set_sources(**inputs.DISC_POTENTIAL)
+    h.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
     h.set_thermal(mhd.THERMAL_PLAIN, **th)
     s0 = g.thermal_stats()
     for _ in range(5):
