@@ -41,7 +41,8 @@ enum {
   MHD_ERR_ARG = -1,       /* invalid argument (sizes, pointers, combination) */
   MHD_ERR_CUDA = -2,      /* a CUDA runtime call failed */
   MHD_ERR_NONFINITE = -3, /* a non-finite value appeared in the state */
-  MHD_ERR_NEGATIVE = -4,  /* density or pressure <= 0 after recovery */
+  MHD_ERR_NEGATIVE = -4,  /* density or pressure <= 0 after recovery (reported before
+                             MHD_ERR_NONFINITE when both occurred) */
   MHD_ERR_TIMEOUT = -5,   /* a bounded device wait ran out (persistent mode) */
   MHD_ERR_STATE = -6,     /* call not valid in the context's current state */
   MHD_ERR_NOMEM = -7      /* device allocation failed */
@@ -219,7 +220,8 @@ int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long l
  * context's stream (steps are not replayed from a graph) and the elapsed times are summed
  * per kernel class: 0 recovery+CFL, 1-3 donor-cell HLLD fluxes x/y/z, 4-6 kappa-scheme
  * HLLD fluxes x/y/z, 7 corner EMFs, 8 update, 9 standalone CFL, 10 persistent step,
- * 11 thermal source, 12 end-of-step floors.  Switching on or off clears the totals. */
+ * 11 thermal source, 12 end-of-step floors, 13 ghost W fill.  Switching on or off clears
+ * the totals. */
 int mhd_set_profiling(mhd_ctx* ctx, int on);
 
 /* Totals since profiling was switched on: ms[c] milliseconds and launches[c] launches of

@@ -85,8 +85,11 @@ struct mhd_ctx {
   double* dt_used = nullptr;
   int* err = nullptr;
   double* staging = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  long long graph_launches = 0;
+  // captured steps, keyed by buffer parity and whether W of the current state is stored
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long graph_launches[4] = {0, 0, 0, 0};
+  int parity = 0;        // 1: the current state lives in the second state buffer
+  bool w_valid = false;  // W and the CFL slot hold the recovery of the current state
   long long launches = 0;
   bool profiling = false;
   ProfRec prof{};
@@ -136,7 +139,8 @@ static int cuda_fail(mhd_ctx* c, cudaError_t e, const char* where) {
 
 static void free_ctx(mhd_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (auto& g : ctx->gexec)
+    if (g) cudaGraphExecDestroy(g);
   if (ctx->profiling)
     for (int q = 0; q < ProfRec::kMax; ++q) {
       cudaEventDestroy(ctx->prof.a[q]);
@@ -192,8 +196,10 @@ static int read_error_word(mhd_ctx* ctx) {
   CK(cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (h & ERR_TIMEOUT) return fail(ctx, MHD_ERR_TIMEOUT, "a bounded device wait ran out");
-  if (h & ERR_NONFINITE) return fail(ctx, MHD_ERR_NONFINITE, "non-finite value in the state");
+  // a non-positive density or pressure is the usual origin of the non-finite values that
+  // follow it, so it is reported first
   if (h & ERR_NEGATIVE) return fail(ctx, MHD_ERR_NEGATIVE, "density or pressure <= 0");
+  if (h & ERR_NONFINITE) return fail(ctx, MHD_ERR_NONFINITE, "non-finite value in the state");
   return MHD_OK;
 }
 
@@ -211,10 +217,33 @@ static int flush_profile(mhd_ctx* ctx) {
 }
 
 static void drop_graph(mhd_ctx* ctx) {
-  if (ctx->gexec) {
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
+  for (auto& g : ctx->gexec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
   }
+}
+
+// Point every patch's Un at the buffer holding the current state (Uh at the other one).
+static void set_parity(mhd_ctx* ctx, int parity) {
+  ctx->parity = parity;
+  for (auto& H : ctx->P) {
+    double* a = (double*)H.state;
+    double* b = a + 8 * H.dev.FS;
+    H.dev.Un = parity ? b : a;
+    H.dev.Uh = parity ? a : b;
+  }
+}
+
+// Host-side state change of one step: the fused per-phase step leaves the new state in
+// the other buffer with its W stored (unless the thermal term changed E afterwards); the
+// persistent step updates in place and leaves W stale.
+static void step_transition(mhd_ctx* ctx) {
+  if (ctx->persistent) {
+    ctx->w_valid = false;
+    return;
+  }
+  set_parity(ctx, ctx->parity ^ 1);
+  ctx->w_valid = ctx->thermal.mode == TH_OFF;
 }
 
 // Work tables of the persistent step for tiles of TX x TY points: patches largest first,
@@ -317,6 +346,7 @@ static int issue_persistent_step(mhd_ctx* ctx, double dt) {
 
 static int issue_thermal_all(mhd_ctx* ctx) {
   if (ctx->thermal.mode == TH_OFF) return MHD_OK;
+  ctx->w_valid = false;  // E changes after the recovery of the step
   for (auto& p : ctx->P) {
     ProfScope ps(ctx->profiling && ctx->prof.n < ProfRec::kMax ? &ctx->prof : nullptr, KC_THERMAL, ctx->stream);
     int rc = ctx->thermal.mode == TH_SURROGATE
@@ -343,31 +373,41 @@ static int issue_floors(mhd_ctx* ctx) {
 }
 
 static int issue_step(mhd_ctx* ctx, double dt) {
+  ProfRec* prof = ctx->profiling ? &ctx->prof : nullptr;
   if (ctx->persistent) {
     int rc = issue_persistent_step(ctx, dt);
     if (rc == MHD_OK) rc = issue_floors(ctx);
     if (rc == MHD_OK) rc = issue_thermal_all(ctx);
+    step_transition(ctx);
     if (rc == MHD_OK && ctx->profiling) return flush_profile(ctx);
     return rc;
   }
-  CK(cudaMemsetAsync(ctx->cfl_min, 0xFF, sizeof(unsigned long long) * ctx->np, ctx->stream));
+  if (!ctx->w_valid) {
+    CK(cudaMemsetAsync(ctx->cfl_min, 0xFF, sizeof(unsigned long long) * ctx->np, ctx->stream));
+    for (auto& p : ctx->P)
+      if (ctx->be.prim(p.dev, ctx->stream, &ctx->launches, prof))
+        return cuda_fail(ctx, cudaGetLastError(), "recovery launch");
+  }
   StageArgs a{};
   a.dt_host = dt;
   a.cfl = ctx->cfl;
   a.src = ctx->src;
   for (int stage = 0; stage < 2; ++stage) {
     a.stage = stage;
+    // the corrector accumulates the CFL limit of the new state into a reset slot (the
+    // predictor has taken dt from it)
+    if (stage == 1) CK(cudaMemsetAsync(ctx->cfl_min, 0xFF, sizeof(unsigned long long) * ctx->np, ctx->stream));
     for (auto& p : ctx->P) {
       if (ctx->profiling && ctx->prof.n > ProfRec::kMax - 16) {
         int rc = flush_profile(ctx);
         if (rc) return rc;
       }
-      if (ctx->be.stage(p.dev, a, ctx->stream, &ctx->launches, ctx->profiling ? &ctx->prof : nullptr))
+      if (ctx->be.stage(p.dev, a, ctx->stream, &ctx->launches, prof))
         return cuda_fail(ctx, cudaGetLastError(), "stage launch");
     }
   }
-  int rc = issue_floors(ctx);
-  if (rc == MHD_OK) rc = issue_thermal_all(ctx);
+  step_transition(ctx);  // the new state (floors applied) is in what becomes Un
+  int rc = issue_thermal_all(ctx);
   if (rc) return rc;
   if (ctx->profiling) return flush_profile(ctx);
   return MHD_OK;
@@ -439,7 +479,11 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     D.hgm1 = 0.5 * D.gm1;
     D.egm1 = 0.125 * D.gm1;
     D.gamma_f = (float)d.gamma;
-    for (int a = 0; a < 3; ++a) D.d_f[a] = (float)dd[a];
+    for (int a = 0; a < 3; ++a) {
+      D.d_f[a] = (float)dd[a];
+      D.inv_d_f[a] = (float)(1.0 / dd[a]);
+      D.lo_f[a] = (float)lo[a];
+    }
     D.PX = (int)round_up(n[0] + 1, 4);
     D.PY = n[1] + 1;
     D.PZ = n[2] + 1;
@@ -504,6 +548,11 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
   ctx->src.xw = s->xw;
   ctx->src.v0 = s->v0;
   ctx->src.rc = s->rc;
+  ctx->src.psi0_f = (float)s->psi0;
+  ctx->src.xc_f = (float)s->xc;
+  ctx->src.xw_f = (float)s->xw;
+  ctx->src.v0_f = (float)s->v0;
+  ctx->src.rc_f = (float)s->rc;
   if (!(s->rho_floor >= 0.0) || !std::isfinite(s->rho_floor) || !std::isfinite(s->pr_floor) ||
       std::isnan(s->pr_ceil))
     return fail(ctx, MHD_ERR_ARG, "floors must be finite and rho_floor >= 0");
@@ -516,10 +565,8 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
     p.dev.pr_ceil = s->rho_floor > 0.0 && s->pr_ceil > 0.0 ? s->pr_ceil : INFINITY;
   }
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
-  if (ctx->gexec) {  // sources are baked into captured launches
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
+  drop_graph(ctx);  // sources are baked into captured launches
+  ctx->w_valid = false;
   return MHD_OK;
 }
 
@@ -527,7 +574,9 @@ int mhd_step(mhd_ctx* ctx, double dt) {
   if (!ctx) return MHD_ERR_ARG;
   if (!std::isfinite(dt)) return fail(ctx, MHD_ERR_ARG, "dt must be finite");
   if ((ctx->flags & MHD_FLAG_GRAPH) && dt <= 0.0 && !ctx->profiling) {
-    if (!ctx->gexec) {
+    const int key = 2 * ctx->parity + (ctx->w_valid ? 1 : 0);
+    if (!ctx->gexec[key]) {
+      // capturing issues the step's host side once, state change included
       cudaGraph_t graph;
       long long before = ctx->launches;
       CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -535,14 +584,16 @@ int mhd_step(mhd_ctx* ctx, double dt) {
       cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
       if (rc) return rc;
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-      ctx->graph_launches = ctx->launches - before;
+      ctx->graph_launches[key] = ctx->launches - before;
       ctx->launches = before;
-      e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+      e = cudaGraphInstantiate(&ctx->gexec[key], graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    } else {
+      step_transition(ctx);
     }
-    CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-    ctx->launches += ctx->graph_launches;
+    CK(cudaGraphLaunch(ctx->gexec[key], ctx->stream));
+    ctx->launches += ctx->graph_launches[key];
     return MHD_OK;
   }
   return issue_step(ctx, dt);
@@ -603,6 +654,7 @@ int mhd_set_state(mhd_ctx* ctx, int patch, const double* U, const double* B, int
   ctx->launches += 1;
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+  ctx->w_valid = false;
   return MHD_OK;
 }
 

@@ -10,7 +10,7 @@ struct PersistentArgs;
 
 // Optional per-launch CUDA-event pairs recorded on the launching stream.
 enum { KC_PRIM = 0, KC_FLUX1 = 1, KC_FLUX2 = 4, KC_EMF = 7, KC_UPDATE = 8, KC_CFL = 9, KC_PERSISTENT = 10,
-       KC_THERMAL = 11, KC_FLOOR = 12, KC_COUNT = 13 };
+       KC_THERMAL = 11, KC_FLOOR = 12, KC_GHOST = 13, KC_COUNT = 14 };
 struct ProfRec {
   static constexpr int kMax = 64;
   cudaEvent_t a[kMax], b[kMax];
@@ -36,8 +36,10 @@ struct ProfScope {
 
 struct Backend {
   size_t scratch_elem;  // bytes per scratch value (8 for FP64, 4 for the mixed path)
-  // one stage (0 predictor, 1 corrector) of a van Leer step of one patch
+  // one stage (0 predictor, 1 corrector) of a van Leer step of one patch; both write Uh
   int (*stage)(const PatchDev&, const StageArgs&, cudaStream_t, long long* launches, ProfRec* prof);
+  // W and CFL limit of the current state Un (the recovery that starts a step)
+  int (*prim)(const PatchDev&, cudaStream_t, long long* launches, ProfRec* prof);
   // CFL limit of the current state into the patch's cfl_min slot
   int (*cfl)(const PatchDev&, cudaStream_t, long long* launches);
   int (*hlld)(int n, const double* wl, const double* wr, const double* bn, double gamma,

@@ -40,6 +40,7 @@ struct PatchDev {
   double d[3], inv_d[3], lo[3], gamma;
   double gm1, hgm1, egm1;  // gamma - 1, (gamma - 1)/2, (gamma - 1)/8
   float gamma_f, d_f[3];   // FP32 copies for the mixed path
+  float inv_d_f[3], lo_f[3];
   double* Un;
   double* Uh;
   void* W;
@@ -58,6 +59,7 @@ struct PatchDev {
 struct SourceDev {
   int potential;
   double psi0, xc, xw, v0, rc;
+  float psi0_f, xc_f, xw_f, v0_f, rc_f;  // FP32 copies for the mixed path
 };
 
 struct StageArgs {
@@ -143,6 +145,9 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  // explicitly rounded operations (never contracted into an FMA)
+  static __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
   static constexpr double degen = 1e-8;
 };
 template <> struct Ar<float> {
@@ -169,6 +174,8 @@ template <> struct Ar<float> {
   }
   static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
   static constexpr float degen = 1e-8f;
 };
 
@@ -177,10 +184,22 @@ template <class R> struct Gam;
 template <> struct Gam<double> {
   static __device__ __forceinline__ double get(const PatchDev& P) { return P.gamma; }
   static __device__ __forceinline__ double d(const PatchDev& P, int a) { return P.d[a]; }
+  static __device__ __forceinline__ double inv(const PatchDev& P, int a) { return P.inv_d[a]; }
+  static __device__ __forceinline__ double lo(const PatchDev& P, int a) { return P.lo[a]; }
+  static __device__ __forceinline__ void src(const SourceDev& s, double& psi0, double& xc, double& xw, double& v0,
+                                             double& rc) {
+    psi0 = s.psi0, xc = s.xc, xw = s.xw, v0 = s.v0, rc = s.rc;
+  }
 };
 template <> struct Gam<float> {
   static __device__ __forceinline__ float get(const PatchDev& P) { return P.gamma_f; }
   static __device__ __forceinline__ float d(const PatchDev& P, int a) { return P.d_f[a]; }
+  static __device__ __forceinline__ float inv(const PatchDev& P, int a) { return P.inv_d_f[a]; }
+  static __device__ __forceinline__ float lo(const PatchDev& P, int a) { return P.lo_f[a]; }
+  static __device__ __forceinline__ void src(const SourceDev& s, float& psi0, float& xc, float& xw, float& v0,
+                                             float& rc) {
+    psi0 = s.psi0_f, xc = s.xc_f, xw = s.xw_f, v0 = s.v0_f, rc = s.rc_f;
+  }
 };
 
 // 1/rho for the FP64 pressure recovery.  FP64 path: IEEE division.  Mixed path: the
@@ -369,39 +388,41 @@ __device__ __forceinline__ void kappa_face(R wm1, R w0, R w1, R w2, R& wl, R& wr
 
 // --------------------------------------------------------------- sources ----
 template <class R>
-__device__ __forceinline__ void grad_psi(const SourceDev& s, double x, double y, double z, R* g) {
+__device__ __forceinline__ void grad_psi(const SourceDev& s, R x, R y, R z, R* g) {
   g[0] = g[1] = g[2] = R(0);
+  R psi0, xc, xw, v0, rc;
+  Gam<R>::src(s, psi0, xc, xw, v0, rc);
   if (s.potential == POT_GAUSS_X) {
-    R u = (R)((x - s.xc) / s.xw);
-    g[0] = (R)s.psi0 * R(2) * u / (R)s.xw * exp(-u * u);
+    R u = (x - xc) / xw;
+    g[0] = psi0 * R(2) * u / xw * exp(-u * u);
   } else if (s.potential == POT_LOG_DISC) {
-    R v02 = (R)(s.v0 * s.v0);
-    R q = (R)(x * x + y * y + s.rc * s.rc + z * z);
-    R iq = v02 / q;
-    g[0] = (R)x * iq;
-    g[1] = (R)y * iq;
-    g[2] = (R)z * iq;
+    R iq = v0 * v0 / (x * x + y * y + rc * rc + z * z);
+    g[0] = x * iq;
+    g[1] = y * iq;
+    g[2] = z * iq;
   }
 }
 
+// centre of cell i along axis a in the bulk type
+template <class R> __device__ __forceinline__ R centre(const PatchDev& P, int a, int i) {
+  return Gam<R>::lo(P, a) + (R(i) + R(0.5)) * Gam<R>::d(P, a);
+}
+
 // ---------------------------------------------------------- phase: recovery --
-// W at a (possibly ghost) cell from U via the boundary index maps: Eq. 6 for the
-// cell-centred field, the energy closure after Eq. 3 for p (FP64 in both paths).
-// Returns the CFL limit min_d d/(|v_d| + c_f,d) for interior cells (else +inf).
+// exponent test of a double on the integer pipe (not inf, not NaN)
+__device__ __forceinline__ bool finite_d(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7FF00000u) != 0x7FF00000u;
+}
+
+// W of one cell from its conserved values: Eq. 6 for the cell-centred field (sbx, sby, sbz
+// are the sums of the two face values, i.e. twice it), the energy closure after Eq. 3 for p
+// (FP64 in both paths), with the floors when they are on.  Stores W at scratch index q when
+// asked; returns the CFL limit min_d d/(|v_d| + c_f,d) for interior cells (else +inf).
 template <class R>
-__device__ __forceinline__ double prim_point(const PatchDev& P, const double* __restrict__ U,
-                                             R* __restrict__ W, int i, int j, int k, bool store,
-                                             bool interior) {
-  const int ci = cmap(P, 0, i), cj = cmap(P, 1, j), ck = cmap(P, 2, k);
-  const long long FS = P.FS;
-  const long long c = sidx(P, ci, cj, ck);
-  double rho = U[c];
+__device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx, double my, double mz,
+                                            double e, double sbx, double sby, double sbz, R* __restrict__ W,
+                                            long long q, bool store, bool interior) {
   if (P.floors && rho < P.rho_floor) rho = P.rho_floor;
-  const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c], e = U[EN * FS + c];
-  // sums of the two face values (twice the cell-centred field of Eq. 6)
-  const double sbx = U[BXF * FS + sidx(P, fmap(P, 0, i), cj, ck)] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), cj, ck)];
-  const double sby = U[BYF * FS + sidx(P, ci, fmap(P, 1, j), ck)] + U[BYF * FS + sidx(P, ci, fmap(P, 1, j + 1), ck)];
-  const double sbz = U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k))] + U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k + 1))];
   const double irho = inv_density<R>(rho);
   const double m2 = mx * mx + my * my + mz * mz;
   const double b2 = sbx * sbx + sby * sby + sbz * sbz;  // 4 |B_cc|^2
@@ -416,7 +437,7 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
   const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
   const R rr = Ar<R>::from_d(rho), pr = Ar<R>::from_d(p);
   if (store) {
-    const long long q = qidx(P, i, j, k), QS = P.QS;
+    const long long QS = P.QS;
     W[q] = rr;
     W[WVX * QS + q] = vx;
     W[WVY * QS + q] = vy;
@@ -426,10 +447,10 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
     W[WBY * QS + q] = by;
     W[WBZ * QS + q] = bz;
   }
-  double lim = INFINITY;
+  R lim = R(INFINITY);
   if (interior) {
     // positivity / finiteness on the bulk-type values; CFL arithmetic in the bulk type
-    if (!(isfinite(rr) && isfinite(pr) && isfinite(e))) {
+    if (!(isfinite(rr) && isfinite(pr) && finite_d(e))) {
       atomicOr(P.err, ERR_NONFINITE);
     } else if (!(rr > R(0)) || !(pr > R(0))) {
       atomicOr(P.err, ERR_NEGATIVE);
@@ -446,33 +467,59 @@ __device__ __forceinline__ double prim_point(const PatchDev& P, const double* __
       const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::abs_(v[a]) + cf);
       lr = t < lr ? t : lr;
     }
-    lim = (double)lr;
+    lim = lr;
   }
   return lim;
 }
 
+// W at a (possibly ghost) cell from U via the boundary index maps.
+template <class R>
+__device__ __forceinline__ R prim_point(const PatchDev& P, const double* __restrict__ U,
+                                             R* __restrict__ W, int i, int j, int k, bool store,
+                                             bool interior) {
+  const int ci = cmap(P, 0, i), cj = cmap(P, 1, j), ck = cmap(P, 2, k);
+  const long long FS = P.FS;
+  const long long c = sidx(P, ci, cj, ck);
+  const double sbx = U[BXF * FS + sidx(P, fmap(P, 0, i), cj, ck)] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), cj, ck)];
+  const double sby = U[BYF * FS + sidx(P, ci, fmap(P, 1, j), ck)] + U[BYF * FS + sidx(P, ci, fmap(P, 1, j + 1), ck)];
+  const double sbz = U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k))] + U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k + 1))];
+  return prim_core<R>(P, U[c], U[MX * FS + c], U[MY * FS + c], U[MZ * FS + c], U[EN * FS + c], sbx, sby, sbz,
+                      W, qidx(P, i, j, k), store, interior);
+}
+
 // ----------------------------------------------------------- end-of-step floors --
-// Interior cell (i, j, k) of the new state: rho' = max(rho, rho_floor), momentum kept,
-// p from E with rho' and the cell-centred field of Eq. 6, clamped to
+// Interior cell of the new state: rho' = max(rho, rho_floor), momentum kept, p from E with
+// rho' and the cell-centred field of Eq. 6 (face values b*lo, b*hi), clamped to
 // [rho' pr_floor, rho' pr_ceil], and E rebuilt by the energy closure (text after Eq. 3)
 // when rho or p changed.  Returns 1 for a changed cell.  (The paper states no floors.)
-__device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict__ U, int i, int j, int k) {
-  const long long FS = P.FS, c = sidx(P, i, j, k);
-  const double rho = U[c];
+__device__ __forceinline__ int floor_core(const PatchDev& P, double& rho, double mx, double my, double mz,
+                                          double& e, double bxlo, double bxhi, double bylo, double byhi,
+                                          double bzlo, double bzhi) {
   const double rf = rho < P.rho_floor ? P.rho_floor : rho;
-  const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c];
-  const double bx = 0.5 * (U[BXF * FS + c] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)]);
-  const double by = 0.5 * (U[BYF * FS + c] + U[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)]);
-  const double bz = 0.5 * (U[BZF * FS + c] + U[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))]);
+  const double bx = 0.5 * (bxlo + bxhi), by = 0.5 * (bylo + byhi), bz = 0.5 * (bzlo + bzhi);
   const double kin = 0.5 * (mx * mx + my * my + mz * mz) / rf;
   const double mag = 0.5 * (bx * bx + by * by + bz * bz);
-  const double p = P.gm1 * (U[EN * FS + c] - kin - mag);
+  const double p = P.gm1 * (e - kin - mag);
   const double lo = rf * P.pr_floor, hi = rf * P.pr_ceil;
   const double pf = p < lo ? lo : (p > hi ? hi : p);
   if (rf == rho && pf == p) return 0;
-  U[c] = rf;
-  U[EN * FS + c] = pf / P.gm1 + kin + mag;
+  rho = rf;
+  e = pf / P.gm1 + kin + mag;
   return 1;
+}
+
+__device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict__ U, int i, int j, int k) {
+  const long long FS = P.FS, c = sidx(P, i, j, k);
+  double rho = U[c], e = U[EN * FS + c];
+  const int changed = floor_core(P, rho, U[MX * FS + c], U[MY * FS + c], U[MZ * FS + c], e, U[BXF * FS + c],
+                                 U[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)], U[BYF * FS + c],
+                                 U[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)], U[BZF * FS + c],
+                                 U[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))]);
+  if (changed) {
+    U[c] = rho;
+    U[EN * FS + c] = e;
+  }
+  return changed;
 }
 
 // ------------------------------------------------------------- phase: flux ----
@@ -587,6 +634,23 @@ __device__ __forceinline__ void emf_point(const PatchDev& P, const R* __restrict
 }
 
 // ----------------------------------------------------------- phase: update ----
+// New value of the a-face stored at state index sf whose lower-left edge has scratch
+// index q: B_a - h [dE_c/db - dE_b/dc] (Eq. 8), with explicitly rounded operations so that
+// every evaluation of the same face gives the same bits.
+template <class R>
+__device__ __forceinline__ double face_new(const PatchDev& P, const double* __restrict__ Ub,
+                                           const R* __restrict__ E, R h, int a, long long sf, long long q) {
+  const int b = (a + 1) % 3, c = (a + 2) % 3;
+  const long long QS = P.QS;
+  R curl = R(0);
+  if (P.act[b])
+    curl = Ar<R>::mul_rn(Ar<R>::sub_rn(E[c * QS + q + qstride(P, b)], E[c * QS + q]), Gam<R>::inv(P, b));
+  if (P.act[c])
+    curl = Ar<R>::sub_rn(curl, Ar<R>::mul_rn(Ar<R>::sub_rn(E[b * QS + q + qstride(P, c)], E[b * QS + q]),
+                                             Gam<R>::inv(P, c)));
+  return __dsub_rn(Ub[(BXF + a) * P.FS + sf], Ar<R>::to_d(Ar<R>::mul_rn(h, curl)));
+}
+
 // Eq. 7 for the cell fields (plus h S of Eq. 2 at Usrc) and Eq. 8 (-curl E) for the
 // owned faces: out = base - h (div F) + h S;  B_a -= h [dE_C/db - dE_B/dc].
 template <class R>
@@ -603,7 +667,7 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
       if (!P.act[d]) continue;
       const R* Fd = (const R*)P.F[d];
       const long long st = qstride(P, d);
-      const R idd = (R)P.inv_d[d];
+      const R idd = Gam<R>::inv(P, d);
 #pragma unroll
       for (int f = 0; f < 5; ++f) div[f] += (Fd[f * QS + q + st] - Fd[f * QS + q]) * idd;
     }
@@ -614,15 +678,15 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
       Uo[EN * FS + s] = Ub[EN * FS + s] - Ar<R>::to_d(h * div[4]);
     } else {
       R g[3];
-      grad_psi<R>(src, P.lo[0] + (i + 0.5) * P.d[0], P.lo[1] + (j + 0.5) * P.d[1],
-                  P.lo[2] + (k + 0.5) * P.d[2], g);
-      const R rho = (R)Us[s];
+      grad_psi<R>(src, centre<R>(P, 0, i), centre<R>(P, 1, j), centre<R>(P, 2, k), g);
+      const R rho = Ar<R>::from_d(Us[s]);
       const R sm[3] = {-rho * g[0], -rho * g[1], -rho * g[2]};
-      const R se = -((R)Us[MX * FS + s] * g[0] + (R)Us[MY * FS + s] * g[1] + (R)Us[MZ * FS + s] * g[2]);
+      const R se = -(Ar<R>::from_d(Us[MX * FS + s]) * g[0] + Ar<R>::from_d(Us[MY * FS + s]) * g[1] +
+                     Ar<R>::from_d(Us[MZ * FS + s]) * g[2]);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - (double)(h * div[1 + a]) + (double)(h * sm[a]);
-      Uo[EN * FS + s] = Ub[EN * FS + s] - (double)(h * div[4]) + (double)(h * se);
+        Uo[(MX + a) * FS + s] = Ub[(MX + a) * FS + s] - Ar<R>::to_d(h * div[1 + a]) + Ar<R>::to_d(h * sm[a]);
+      Uo[EN * FS + s] = Ub[EN * FS + s] - Ar<R>::to_d(h * div[4]) + Ar<R>::to_d(h * se);
     }
   }
   // faces
@@ -631,10 +695,151 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
   for (int a = 0; a < 3; ++a) {
     const int b = (a + 1) % 3, c = (a + 2) % 3;
     if (!(c3[a] < P.nface[a] && c3[b] < P.n[b] && c3[c] < P.n[c])) continue;
-    R curl = R(0);
-    if (P.act[b]) curl += (E[c * QS + q + qstride(P, b)] - E[c * QS + q]) * (R)P.inv_d[b];
-    if (P.act[c]) curl -= (E[b * QS + q + qstride(P, c)] - E[b * QS + q]) * (R)P.inv_d[c];
-    Uo[(BXF + a) * FS + s] = Ub[(BXF + a) * FS + s] - Ar<R>::to_d(h * curl);
+    Uo[(BXF + a) * FS + s] = face_new<R>(P, Ub, E, h, a, s, q);
+  }
+}
+
+// ------------------------------------------------- fused update and recovery --
+// The fused update of a cell also needs the new values of its upper faces, which the
+// neighbouring cells own and write; it computes them again with face_new, whose explicitly
+// rounded operations make the copy bitwise equal to the owner's value.
+
+// Stage update, then (interior cells) the recovery of the new state: U at cell (i, j, k)
+// and its owned faces as update_point, the end-of-step floors when `last` and the floors
+// are on, and W of the new cell stored at the cell (its ghost images are filled afterwards
+// by ghost_point).  Returns the CFL limit of the new cell (+inf for face-only points);
+// floored cells are added to *nfl.
+template <class R>
+__device__ __forceinline__ R update_fused_point(const PatchDev& P, const double* __restrict__ Ub,
+                                                     const double* __restrict__ Us, double* __restrict__ Uo,
+                                                     const R* __restrict__ E, R h, const SourceDev& src,
+                                                     int i, int j, int k, bool last, int* nfl) {
+  const long long s = sidx(P, i, j, k), FS = P.FS;
+  const long long q = qidx(P, i, j, k), QS = P.QS;
+  const int c3[3] = {i, j, k};
+  if (!(i < P.n[0] && j < P.n[1] && k < P.n[2])) {
+    // owned faces on the extra layer of an outflow axis
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      if (c3[a] < P.nface[a] && c3[b] < P.n[b] && c3[c] < P.n[c])
+        Uo[(BXF + a) * FS + s] = face_new<R>(P, Ub, E, h, a, s, q);
+    }
+    return R(INFINITY);
+  }
+  R div[5] = {R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (!P.act[d]) continue;
+    const R* Fd = (const R*)P.F[d];
+    const long long st = qstride(P, d);
+    const R idd = Gam<R>::inv(P, d);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) div[f] += (Fd[f * QS + q + st] - Fd[f * QS + q]) * idd;
+  }
+  double u[5];
+  u[0] = Ub[s] - Ar<R>::to_d(h * div[0]);
+  if (src.potential == POT_NONE) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[1 + a] = Ub[(MX + a) * FS + s] - Ar<R>::to_d(h * div[1 + a]);
+    u[4] = Ub[EN * FS + s] - Ar<R>::to_d(h * div[4]);
+  } else {
+    R g[3];
+    grad_psi<R>(src, centre<R>(P, 0, i), centre<R>(P, 1, j), centre<R>(P, 2, k), g);
+    const R rho = Ar<R>::from_d(Us[s]);
+    const R sm[3] = {-rho * g[0], -rho * g[1], -rho * g[2]};
+    const R se = -(Ar<R>::from_d(Us[MX * FS + s]) * g[0] + Ar<R>::from_d(Us[MY * FS + s]) * g[1] +
+                     Ar<R>::from_d(Us[MZ * FS + s]) * g[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      u[1 + a] = Ub[(MX + a) * FS + s] - Ar<R>::to_d(h * div[1 + a]) + Ar<R>::to_d(h * sm[a]);
+    u[4] = Ub[EN * FS + s] - Ar<R>::to_d(h * div[4]) + Ar<R>::to_d(h * se);
+  }
+  // new lower (owned) and upper faces
+  double blo[3], bhi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    blo[a] = face_new<R>(P, Ub, E, h, a, s, q);
+    if (P.act[a]) {
+      int cu[3] = {i, j, k};
+      cu[a] = fmap(P, a, c3[a] + 1);
+      bhi[a] = face_new<R>(P, Ub, E, h, a, sidx(P, cu[0], cu[1], cu[2]), q + qstride(P, a));
+    } else {
+      bhi[a] = blo[a];  // a trivial axis: the upper face is the same face
+    }
+  }
+  if (last && P.floors) *nfl += floor_core(P, u[0], u[1], u[2], u[3], u[4], blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2]);
+  Uo[s] = u[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Uo[(MX + a) * FS + s] = u[1 + a];
+  Uo[EN * FS + s] = u[4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Uo[(BXF + a) * FS + s] = blo[a];
+  // recovery of the new cell
+  return prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2],
+                      (R*)P.W, q, true, true);
+}
+
+// Ghost position number t of the padded scratch box (the shell of width g2 around the
+// interior: z-slabs, then y-slabs within the interior planes, then x-slabs), as (i, j, k).
+__device__ __forceinline__ bool ghost_index(const PatchDev& P, long long t, int& i, int& j, int& k) {
+  const int gx = P.g2[0], gy = P.g2[1], gz = P.g2[2];
+  const long long QX = P.QX, QY = P.QY;
+  const long long nzs = 2LL * gz * QX * QY;            // z < 0 or z >= n
+  const long long nys = 2LL * gy * QX * P.n[2];        // interior z, y outside
+  const long long nxs = 2LL * gx * (long long)P.n[1] * P.n[2];  // interior y, z, x outside
+  if (t < nzs) {
+    const int s = (int)(t / (QX * QY));
+    const long long r = t % (QX * QY);
+    i = (int)(r % QX) - gx;
+    j = (int)(r / QX) - gy;
+    k = s < gz ? s - gz : P.n[2] + (s - gz);
+    return true;
+  }
+  t -= nzs;
+  if (t < nys) {
+    const long long per = 2LL * gy * QX;
+    k = (int)(t / per);
+    const long long r = t % per;
+    i = (int)(r % QX) - gx;
+    const int s = (int)(r / QX);
+    j = s < gy ? s - gy : P.n[1] + (s - gy);
+    return true;
+  }
+  t -= nys;
+  if (t < nxs) {
+    const long long per = 2LL * gx;
+    const long long row = t / per;
+    const int s = (int)(t % per);
+    j = (int)(row % P.n[1]);
+    k = (int)(row / P.n[1]);
+    i = s < gx ? s - gx : P.n[0] + (s - gx);
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ long long ghost_count(const PatchDev& P) {
+  return 2LL * P.g2[2] * P.QX * P.QY + 2LL * P.g2[1] * P.QX * P.n[2] + 2LL * P.g2[0] * (long long)P.n[1] * P.n[2];
+}
+
+// W at ghost position (i, j, k) of the current state: a copy of the interior cell it maps to
+// when every axis on which it lies outside is periodic, else the recovery from U as
+// prim_point (an outflow ghost repeats the boundary face in its face sum).
+template <class R>
+__device__ __forceinline__ void ghost_point(const PatchDev& P, const double* __restrict__ U, int i, int j, int k) {
+  const int c3[3] = {i, j, k};
+  bool copy = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if ((c3[a] < 0 || c3[a] >= P.n[a]) && !P.per[a]) copy = false;
+  R* W = (R*)P.W;
+  if (copy) {
+    const long long QS = P.QS, t = qidx(P, i, j, k), q = qidx(P, cmap(P, 0, i), cmap(P, 1, j), cmap(P, 2, k));
+#pragma unroll
+    for (int m = 0; m < 8; ++m) W[m * QS + t] = W[m * QS + q];
+  } else {
+    prim_point<R>(P, U, W, i, j, k, true, false);
   }
 }
 

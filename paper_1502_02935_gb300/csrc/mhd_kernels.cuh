@@ -27,25 +27,27 @@ __device__ __forceinline__ bool range_point(const Range& rg, int& i, int& j, int
   return true;
 }
 
-__device__ __forceinline__ void block_min_atomic(double v, unsigned long long* slot) {
-  // warp-shuffle minimum, then one ordered-bits atomicMin per block (deterministic)
+// Block minimum of v in its own type (FP32 compares on the mixed path), then one
+// ordered-bits atomicMin of its exact double value per block (deterministic).
+template <class T>
+__device__ __forceinline__ void block_min_atomic(T v, unsigned long long* slot) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double w = __shfl_xor_sync(0xffffffffu, v, o);
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
     v = w < v ? w : v;
   }
-  __shared__ double red[kBlock / 32];
+  __shared__ T red[kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : INFINITY;
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(INFINITY);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double w = __shfl_xor_sync(0xffffffffu, v, o);
+      T w = __shfl_xor_sync(0xffffffffu, v, o);
       v = w < v ? w : v;
     }
-    if (lane == 0 && v < INFINITY) atomicMin(slot, dbits(v));
+    if (lane == 0 && v < T(INFINITY)) atomicMin(slot, dbits(Ar<T>::to_d(v)));
   }
 }
 
@@ -53,7 +55,7 @@ template <class R>
 __global__ void __launch_bounds__(kBlock) k_prim(PatchDev P, const double* __restrict__ U, Range rg,
                                                  int store, int want_cfl) {
   int i, j, k;
-  double lim = INFINITY;
+  R lim = R(INFINITY);
   if (range_point(rg, i, j, k)) {
     const bool interior = want_cfl && i >= 0 && i < P.n[0] && j >= 0 && j < P.n[1] && k >= 0 &&
                           k < P.n[2];
@@ -76,16 +78,48 @@ __global__ void __launch_bounds__(kBlock) k_emf(PatchDev P, Range rg) {
   emf_point<R>(P, (const R*)P.W, (R*)P.E, i, j, k);
 }
 
+// Stage update fused with the recovery of the new state (see update_fused_point).  The
+// predictor takes dt from the host or the CFL slot and records it; the corrector reuses the
+// recorded dt and accumulates the CFL limit of the new state into the (reset) slot.
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_update(PatchDev P, const double* __restrict__ Ub,
-                                                   const double* __restrict__ Us,
-                                                   double* __restrict__ Uo, Range rg, StageArgs a) {
-  const double dt = a.dt_host > 0.0 ? a.dt_host : a.cfl * __longlong_as_double((long long)*P.cfl_min);
-  const R h = (R)(a.stage == 0 ? 0.5 * dt : dt);
-  if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *P.dt_used = dt;
-  int i, j, k;
-  if (!range_point(rg, i, j, k)) return;
-  update_point<R>(P, Ub, Us, Uo, (const R*)P.E, h, a.src, i, j, k);
+__global__ void __launch_bounds__(kBlock) k_update_fused(PatchDev P, const double* __restrict__ Ub,
+                                                         const double* __restrict__ Us,
+                                                         double* __restrict__ Uo, Range rg, StageArgs a) {
+  // dt and h once per block
+  __shared__ R sh;
+  if (threadIdx.x == 0) {
+    double dt;
+    if (a.stage == 0) {
+      dt = a.dt_host > 0.0 ? a.dt_host : a.cfl * __longlong_as_double((long long)*P.cfl_min);
+      if (blockIdx.x == 0 && blockIdx.y == 0) *P.dt_used = dt;
+    } else {
+      dt = *P.dt_used;
+    }
+    sh = Ar<R>::from_d(a.stage == 0 ? 0.5 * dt : dt);
+  }
+  __syncthreads();
+  const R h = sh;
+  int i, j, k, nfl = 0;
+  R lim = R(INFINITY);
+  if (range_point(rg, i, j, k))
+    lim = update_fused_point<R>(P, Ub, Us, Uo, (const R*)P.E, h, a.src, i, j, k, a.stage == 1, &nfl);
+  if (a.stage == 1) {
+    if (P.floors) {
+      const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nfl);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.floored, (unsigned long long)tot);
+    }
+    block_min_atomic(lim, P.cfl_min);
+  }
+}
+
+// W of the ghost shell from the interior W and U of the current state (see ghost_point).
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_ghost(PatchDev P, const double* __restrict__ U) {
+  const long long n = ghost_count(P);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    if (ghost_index(P, t, i, j, k)) ghost_point<R>(P, U, i, j, k);
+  }
 }
 
 template <class R>
@@ -107,6 +141,10 @@ __global__ void k_hlld(int n, const double* __restrict__ wl, const double* __res
 }
 
 // ------------------------------------------------------------- host side ----
+static inline long long ghost_count_host(const PatchDev& P) {
+  return 2LL * P.g2[2] * P.QX * P.QY + 2LL * P.g2[1] * P.QX * P.n[2] + 2LL * P.g2[0] * (long long)P.n[1] * P.n[2];
+}
+
 static inline dim3 grid_of(const Range& rg) {
   const long long plane = (long long)rg.ext[0] * rg.ext[1];
   return dim3((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)rg.ext[2], 1);
@@ -156,17 +194,16 @@ static inline Range edge_range(const PatchDev& P) {
   return r;
 }
 
+// One stage of the step for one patch: fluxes from the stored W, corner EMFs, and the
+// fused update + recovery.  The predictor writes U^{n+1/2} into Uh; the corrector, whose base
+// is U^n and whose source term is evaluated at U^{n+1/2}, writes U^{n+1} into Uh as well (each
+// cell's U^{n+1/2} is read by the thread that overwrites it, and no kernel of the stage reads
+// the faces of Uh after the fluxes), so the caller swaps Un and Uh after the corrector.
 template <class R>
 static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, long long* launches,
                        ProfRec* prof) {
-  const double* Usrc = a.stage == 0 ? P.Un : P.Uh;   // state the fluxes are built from
-  double* Uout = a.stage == 0 ? P.Uh : P.Un;         // corrector updates U^n in place
-  const Range pr = prim_range(P);
-  {
-    ProfScope ps(prof, KC_PRIM, s);
-    k_prim<R><<<grid_of(pr), kBlock, 0, s>>>(P, Usrc, pr, 1, a.stage == 0 ? 1 : 0);
-  }
-  int nl = 1;
+  const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
+  int nl = 0;
   for (int d = 0; d < 3; ++d) {
     if (!P.act[d]) continue;
     const Range fr = flux_range(P, d);
@@ -189,10 +226,32 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
   }
   {
     ProfScope ps(prof, KC_UPDATE, s);
-    k_update<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, Uout, er, a);
+    k_update_fused<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, P.Uh, er, a);
+  }
+  {
+    ProfScope ps(prof, KC_GHOST, s);
+    const long long ng = ghost_count_host(P);
+    if (ng > 0) {
+      long long blocks = (ng + kBlock - 1) / kBlock;
+      if (blocks > 65535) blocks = 65535;
+      k_ghost<R><<<(unsigned)blocks, kBlock, 0, s>>>(P, P.Uh);
+      ++nl;
+    }
   }
   nl += 2;
   *launches += nl;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// W of the current state over the padded box, and its CFL limit into the patch's slot
+// (which the caller resets): the recovery that starts a step when W is not already that of
+// the current state.
+template <class R>
+static int issue_prim(const PatchDev& P, cudaStream_t s, long long* launches, ProfRec* prof) {
+  const Range pr = prim_range(P);
+  ProfScope ps(prof, KC_PRIM, s);
+  k_prim<R><<<grid_of(pr), kBlock, 0, s>>>(P, P.Un, pr, 1, 1);
+  *launches += 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -216,6 +275,7 @@ template <class R> Backend make_backend() {
   Backend b;
   b.scratch_elem = sizeof(R);
   b.stage = &issue_stage<R>;
+  b.prim = &issue_prim<R>;
   b.cfl = &issue_cfl<R>;
   b.hlld = &issue_hlld<R>;
   b.persistent = &issue_persistent<R>;

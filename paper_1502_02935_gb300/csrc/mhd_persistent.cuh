@@ -151,7 +151,7 @@ __device__ __forceinline__ void persistent_phase(const PersistentArgs& A, int st
       if (in) {
         const bool interior = stage == 0 && i >= 0 && i < sP.n[0] && j >= 0 && j < sP.n[1] && k >= 0 &&
                               k < sP.n[2];
-        lim = prim_point<R>(sP, Usrc, (R*)sP.W, i, j, k, true, interior);
+        lim = Ar<R>::to_d(prim_point<R>(sP, Usrc, (R*)sP.W, i, j, k, true, interior));
       }
       if (stage == 0) tile_min_atomic(lim, sP.cfl_min);
     } else if (PH == PH_FLUX) {
