@@ -371,11 +371,11 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
 // --------------------------------------------------------- reconstruction ----
 // kappa = 1/3 compressive minmod scheme (Eq. 12-14 read in the standard form that is
 // third-order upwind biased): K1 = 1/6, K2 = 1/3, b = 4.
-// minmod(a, b) = sign(a) max(0, min(|a|, sign(a) b)): the smaller magnitude with a's sign
-// when a and b have the same sign, else 0 (written branch-free)
+// minmod(a, b): the smaller magnitude with the common sign when a and b have the same
+// sign, else 0; as max(min(a, b), min(max(a, b), 0)), which is exact (min and max do not
+// round) and needs no product a b (which can underflow)
 template <class R> __device__ __forceinline__ R minmod(R a, R b) {
-  const R m = Ar<R>::abs_(a) < Ar<R>::abs_(b) ? Ar<R>::abs_(a) : Ar<R>::abs_(b);
-  return a * b > R(0) ? copysign(m, a) : R(0);
+  return fmax(fmin(a, b), fmin(fmax(a, b), R(0)));
 }
 
 template <class R>
@@ -523,47 +523,57 @@ __device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict
 }
 
 // ------------------------------------------------------------- phase: flux ----
-// HLLD flux through the D-face at (i, j, k) (face index i-1/2 along D), with
-// donor-cell (ORDER 1) or kappa-scheme (ORDER 2) interface states; the normal field
-// is the face value; a face whose reconstructed rho or p is not positive falls back
-// to the donor-cell states.
+// HLLD flux through a D-face with donor-cell (ORDER 1) or kappa-scheme (ORDER 2)
+// interface states; the normal field is the face value; a face whose reconstructed rho
+// or p is not positive falls back to the donor-cell states.  get(m, o) returns primitive
+// component m (W index) of the cell at offset o in {-2, -1, 0, 1} along D from the face
+// (o = -1 left, o = 0 right).  f[0..7]: rho, m_D, m_T1, m_T2, E, B_T1, B_T2 fluxes and the
+// wave-speed scale sigma.
+template <class R, int D, int ORDER, class Get>
+__device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, R* f) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  const int comp[7] = {WR, WVX + D, WVX + T1, WVX + T2, WP, WBX + T1, WBX + T2};
+  R wl[7], wr[7];
+  if (ORDER == 1) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      wl[m] = get(comp[m], -1);
+      wr[m] = get(comp[m], 0);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) kappa_face<R>(get(comp[m], -2), get(comp[m], -1), get(comp[m], 0), get(comp[m], 1), wl[m], wr[m]);
+    if (!(wl[0] > R(0)) || !(wr[0] > R(0)) || !(wl[4] > R(0)) || !(wr[4] > R(0))) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        wl[m] = get(comp[m], -1);
+        wr[m] = get(comp[m], 0);
+      }
+    }
+  }
+  hlld<R>(wl, wr, bn, gam, f);
+}
+
+// normal field at D-face (i, j, k) from the state's face values
+template <class R, int D>
+__device__ __forceinline__ R face_bn(const PatchDev& P, const double* __restrict__ Ub, int i, int j, int k) {
+  const int c3[3] = {i, j, k};
+  int s3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s3[a] = (a == D) ? fmap(P, a, c3[a]) : cmap(P, a, c3[a]);
+  return Ar<R>::from_d(Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])]);
+}
+
+// the flux through the D-face at (i, j, k) (face index i-1/2 along D) from the stored W
 template <class R, int D, int ORDER>
 __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restrict__ W,
                                            const double* __restrict__ Ub, R* __restrict__ F,
                                            int i, int j, int k) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long q = qidx(P, i, j, k), QS = P.QS, st = qstride(P, D);
-  const int comp[7] = {WR, WVX + D, WVX + T1, WVX + T2, WP, WBX + T1, WBX + T2};
-  R wl[7], wr[7];
-  if (ORDER == 1) {
-#pragma unroll
-    for (int m = 0; m < 7; ++m) {
-      const R* w = W + comp[m] * QS + q;
-      wl[m] = w[-st];
-      wr[m] = w[0];
-    }
-  } else {
-#pragma unroll
-    for (int m = 0; m < 7; ++m) {
-      const R* w = W + comp[m] * QS + q;
-      kappa_face<R>(w[-2 * st], w[-st], w[0], w[st], wl[m], wr[m]);
-    }
-    if (!(wl[0] > R(0)) || !(wr[0] > R(0)) || !(wl[4] > R(0)) || !(wr[4] > R(0))) {
-#pragma unroll
-      for (int m = 0; m < 7; ++m) {
-        const R* w = W + comp[m] * QS + q;
-        wl[m] = w[-st];
-        wr[m] = w[0];
-      }
-    }
-  }
-  int c3[3] = {i, j, k};
-  int s3[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) s3[a] = (a == D) ? fmap(P, a, c3[a]) : cmap(P, a, c3[a]);
-  const R bn = Ar<R>::from_d(Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])]);
   R f[8];
-  hlld<R>(wl, wr, bn, Gam<R>::get(P), f);
+  flux_core<R, D, ORDER>([&](int m, int o) { return W[m * QS + q + o * st]; }, face_bn<R, D>(P, Ub, i, j, k),
+                         Gam<R>::get(P), f);
   F[q] = f[0];
   F[(1 + D) * QS + q] = f[1];
   F[(1 + T1) * QS + q] = f[2];
@@ -585,6 +595,22 @@ template <class R> __device__ __forceinline__ R upwind(R fr, R sigma, R left, R 
   return fr > t ? left : (fr < -t ? right : R(0.5) * (left + right));
 }
 
+// Face EMFs around the edge: Ea_b, Ea_bm = -F_A(B_B) on the A-faces at b and b-1;
+// Eb_a, Eb_am = F_B(B_A) on the B-faces at a and a-1.  Cell EMFs ec0..ec3 at (a, b),
+// (a-1, b), (a, b-1), (a-1, b-1).  Mass fluxes and sigmas of the same four faces.
+template <class R>
+__device__ __forceinline__ R corner_core(R Ea_b, R Ea_bm, R Eb_a, R Eb_am, R ec0, R ec1, R ec2, R ec3, R frA_b,
+                                         R sA_b, R frA_bm, R sA_bm, R frB_a, R sB_a, R frB_am, R sB_am) {
+  const R d_bq = upwind<R>(frA_b, sA_b, ec1 - Eb_am, ec0 - Eb_a);
+  const R d_b3q = upwind<R>(frA_bm, sA_bm, Eb_am - ec3, Eb_a - ec2);
+  const R d_aq = upwind<R>(frB_a, sB_a, ec2 - Ea_bm, ec0 - Ea_b);
+  const R d_a3q = upwind<R>(frB_am, sB_am, Ea_bm - ec3, Ea_b - ec1);
+  return R(0.25) * (Ea_b + Ea_bm + Eb_a + Eb_am) + R(0.25) * (d_b3q - d_bq) + R(0.25) * (d_a3q - d_aq);
+}
+
+// cell EMF -(v x B)_C from the velocity and field components A, B
+template <class R> __device__ __forceinline__ R cell_emf(R vA, R vB, R bA, R bB) { return -(vA * bB - vB * bA); }
+
 template <class R, int C>
 __device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restrict__ W,
                                              R* __restrict__ E, int i, int j, int k) {
@@ -602,24 +628,15 @@ __device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restr
   } else {
     const long long sa = qstride(P, A), sb = qstride(P, B);
     const long long oa = q - sa, ob = q - sb, oab = q - sa - sb;
-    const R Ea_b = -FA[5 * QS + q], Ea_bm = -FA[5 * QS + ob];
-    const R Eb_a = FB[6 * QS + q], Eb_am = FB[6 * QS + oa];
     const R* vA = W + (WVX + A) * QS;
     const R* vB = W + (WVX + B) * QS;
     const R* bA = W + (WBX + A) * QS;
     const R* bB = W + (WBX + B) * QS;
-    const R ec0 = -(vA[q] * bB[q] - vB[q] * bA[q]);
-    const R ec1 = -(vA[oa] * bB[oa] - vB[oa] * bA[oa]);
-    const R ec2 = -(vA[ob] * bB[ob] - vB[ob] * bA[ob]);
-    const R ec3 = -(vA[oab] * bB[oab] - vB[oab] * bA[oab]);
-    const R* SA = FA + 7 * QS;
-    const R* SB = FB + 7 * QS;
-    const R d_bq = upwind<R>(FA[q], SA[q], ec1 - Eb_am, ec0 - Eb_a);
-    const R d_b3q = upwind<R>(FA[ob], SA[ob], Eb_am - ec3, Eb_a - ec2);
-    const R d_aq = upwind<R>(FB[q], SB[q], ec2 - Ea_bm, ec0 - Ea_b);
-    const R d_a3q = upwind<R>(FB[oa], SB[oa], Ea_bm - ec3, Ea_b - ec1);
-    e = R(0.25) * (Ea_b + Ea_bm + Eb_a + Eb_am) + R(0.25) * (d_b3q - d_bq) +
-        R(0.25) * (d_a3q - d_aq);
+    e = corner_core<R>(-FA[5 * QS + q], -FA[5 * QS + ob], FB[6 * QS + q], FB[6 * QS + oa],
+                       cell_emf<R>(vA[q], vB[q], bA[q], bB[q]), cell_emf<R>(vA[oa], vB[oa], bA[oa], bB[oa]),
+                       cell_emf<R>(vA[ob], vB[ob], bA[ob], bB[ob]), cell_emf<R>(vA[oab], vB[oab], bA[oab], bB[oab]),
+                       FA[q], FA[7 * QS + q], FA[ob], FA[7 * QS + ob], FB[q], FB[7 * QS + q], FB[oa],
+                       FB[7 * QS + oa]);
   }
   E[C * QS + q] = e;
 }

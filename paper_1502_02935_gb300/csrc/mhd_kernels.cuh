@@ -194,15 +194,9 @@ static inline Range edge_range(const PatchDev& P) {
   return r;
 }
 
-// One stage of the step for one patch: fluxes from the stored W, corner EMFs, and the
-// fused update + recovery.  The predictor writes U^{n+1/2} into Uh; the corrector, whose base
-// is U^n and whose source term is evaluated at U^{n+1/2}, writes U^{n+1} into Uh as well (each
-// cell's U^{n+1/2} is read by the thread that overwrites it, and no kernel of the stage reads
-// the faces of Uh after the fluxes), so the caller swaps Un and Uh after the corrector.
+// per-direction flux kernels and the corner-EMF kernel of one stage
 template <class R>
-static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, long long* launches,
-                       ProfRec* prof) {
-  const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
+static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s, ProfRec* prof) {
   int nl = 0;
   for (int d = 0; d < 3; ++d) {
     if (!P.act[d]) continue;
@@ -220,13 +214,26 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     ++nl;
   }
   const Range er = edge_range(P);
-  {
-    ProfScope ps(prof, KC_EMF, s);
-    k_emf<R><<<grid_of(er), kBlock, 0, s>>>(P, er);
-  }
+  ProfScope ps(prof, KC_EMF, s);
+  k_emf<R><<<grid_of(er), kBlock, 0, s>>>(P, er);
+  return nl + 1;
+}
+
+// One stage of the step for one patch: per-direction fluxes and the corner EMFs from the
+// stored W, then the fused update + recovery and the ghost shell of W.  The predictor writes U^{n+1/2} into Uh; the corrector, whose base is U^n and whose
+// source term is evaluated at U^{n+1/2}, writes U^{n+1} into Uh as well (each cell's
+// U^{n+1/2} is read by the thread that overwrites it, and no kernel of the stage reads the
+// faces of Uh after the fluxes), so the caller swaps Un and Uh after the corrector.
+template <class R>
+static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, long long* launches,
+                       ProfRec* prof) {
+  const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
+  int nl = issue_fluxes<R>(P, a, Usrc, s, prof);
+  const Range er = edge_range(P);
   {
     ProfScope ps(prof, KC_UPDATE, s);
     k_update_fused<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, P.Uh, er, a);
+    ++nl;
   }
   {
     ProfScope ps(prof, KC_GHOST, s);
@@ -238,7 +245,6 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
       ++nl;
     }
   }
-  nl += 2;
   *launches += nl;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
