@@ -71,18 +71,21 @@ __global__ void __launch_bounds__(kBlock) k_flux(PatchDev P, const double* __res
   flux_point<R, D, ORDER>(P, (const R*)P.W, Ub, (R*)P.F[D], i, j, k);
 }
 
+// corner EMFs: memory-latency bound; eight resident blocks per SM (measured)
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_emf(PatchDev P, Range rg) {
+__global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
   int i, j, k;
   if (!range_point(rg, i, j, k)) return;
   emf_point<R>(P, (const R*)P.W, (R*)P.E, i, j, k);
 }
 
-// Stage update fused with the recovery of the new state (see update_fused_point).  The
+// Stage update fused with the recovery of the new state (see update_fused_point).  Its FP64
+// arithmetic is the bound; six resident blocks per SM (40 registers, a few spills to L1)
+// hide the memory latency better than fewer blocks without spills (measured).  The
 // predictor takes dt from the host or the CFL slot and records it; the corrector reuses the
 // recorded dt and accumulates the CFL limit of the new state into the (reset) slot.
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_update_fused(PatchDev P, const double* __restrict__ Ub,
+__global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const double* __restrict__ Ub,
                                                          const double* __restrict__ Us,
                                                          double* __restrict__ Uo, Range rg, StageArgs a) {
   // dt and h once per block
