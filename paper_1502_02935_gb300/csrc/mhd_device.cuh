@@ -836,7 +836,7 @@ __device__ __forceinline__ bool ghost_index(const PatchDev& P, long long t, int&
   return false;
 }
 
-__device__ __forceinline__ long long ghost_count(const PatchDev& P) {
+__host__ __device__ __forceinline__ long long ghost_count(const PatchDev& P) {
   return 2LL * P.g2[2] * P.QX * P.QY + 2LL * P.g2[1] * P.QX * P.n[2] + 2LL * P.g2[0] * (long long)P.n[1] * P.n[2];
 }
 

@@ -144,9 +144,6 @@ __global__ void k_hlld(int n, const double* __restrict__ wl, const double* __res
 }
 
 // ------------------------------------------------------------- host side ----
-static inline long long ghost_count_host(const PatchDev& P) {
-  return 2LL * P.g2[2] * P.QX * P.QY + 2LL * P.g2[1] * P.QX * P.n[2] + 2LL * P.g2[0] * (long long)P.n[1] * P.n[2];
-}
 
 static inline dim3 grid_of(const Range& rg) {
   const long long plane = (long long)rg.ext[0] * rg.ext[1];
@@ -240,7 +237,7 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
   }
   {
     ProfScope ps(prof, KC_GHOST, s);
-    const long long ng = ghost_count_host(P);
+    const long long ng = ghost_count(P);
     if (ng > 0) {
       long long blocks = (ng + kBlock - 1) / kBlock;
       if (blocks > 65535) blocks = 65535;

@@ -4,9 +4,11 @@
 // The launch is cooperative (all CTAs co-resident).  It runs the eight phases of a step
 // (recovery+CFL, fluxes, corner EMFs, update; twice) over the work list of every patch,
 // with a grid-wide barrier between phases.  Work items are tiles of TX x TY points of one
-// z-plane of a phase's index box; one CTA of TX*TY threads takes a tile at a time,
-// strided over the grid.  Patches are listed largest first.  Each patch keeps its own
-// CFL time step.
+// z-plane of a phase's index box; each CTA takes a contiguous range of the phase's tiles,
+// so that it rarely changes patch (a strided assignment reloaded the patch descriptor at
+// almost every tile of the small patches).  Patches are listed largest first.  Each patch
+// keeps its own CFL time step.  (The update fused with the recovery, which the per-phase
+// launches use, is slower here: it needs more resident warps than this single kernel has.)
 //
 // The barrier's wait is bounded by the GPU global timer: a CTA that waits longer than the
 // limit sets ERR_TIMEOUT in the device error word and every CTA returns at its next
@@ -111,14 +113,21 @@ __device__ __forceinline__ void persistent_phase(const PersistentArgs& A, int st
                                                  int& cur) {
   const long long* pre = PH == PH_PRIM ? A.pre_prim : (PH == PH_FLUX ? A.pre_flux : A.pre_edge);
   const long long total = pre[A.np];
-  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    int lo = 0, hi = A.np - 1;  // last patch p with pre[p] <= t
+  // this CTA's contiguous share of the phase's tiles
+  const long long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+  if (t0 >= t1) return;
+  int p = 0;  // last patch with pre[p] <= t0
+  {
+    int lo = 0, hi = A.np - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (pre[mid] <= t) lo = mid;
+      if (pre[mid] <= t0) lo = mid;
       else hi = mid - 1;
     }
-    const int p = lo;
+    p = lo;
+  }
+  for (long long t = t0; t < t1; ++t) {
+    while (t >= pre[p + 1]) ++p;
     if (p != cur) {
       __syncthreads();
       const int* src = (const int*)(A.P + p);
@@ -171,7 +180,7 @@ __device__ __forceinline__ void persistent_phase(const PersistentArgs& A, int st
       if (in) emf_point<R>(sP, (const R*)sP.W, (R*)sP.E, i, j, k);
     } else {
       const double dt = A.dt_host > 0.0 ? A.dt_host : A.cfl * __longlong_as_double((long long)*sP.cfl_min);
-      const R h = (R)(stage == 0 ? 0.5 * dt : dt);
+      const R h = Ar<R>::from_d(stage == 0 ? 0.5 * dt : dt);
       if (stage == 1 && lt == 0 && threadIdx.x == 0) *sP.dt_used = dt;
       if (in) update_point<R>(sP, sP.Un, Usrc, stage == 0 ? sP.Uh : sP.Un, (const R*)sP.E, h, A.src, i, j, k);
     }
