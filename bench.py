@@ -54,7 +54,11 @@ KCLASS = {
     "flux2_y": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "flux2_z": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "emf": dict(fp64=0, fp32=75, bytes=(12 + 6 + 3) * 4, unit="edge point"),
-    "update": dict(fp64=8, fp32=40, bytes=15 * 4 + 3 * 4 + 64 + 64, unit="point"),
+    # update fused with the recovery of the new state: FP64 = 14 DADD (cell, six faces, three
+    # face sums) + |m|^2 and |B|^2 (5 + 5) + Newton step of 1/rho (4) + p (6); bytes = F (60) +
+    # E (12) + base U (64) + new U (64) + new W (32)
+    "update": dict(fp64=34, fp32=130, bytes=15 * 4 + 3 * 4 + 64 + 64 + 8 * 4, unit="point"),
+    "ghost": dict(fp64=0, fp32=0, bytes=8 * 4 * 2, unit="ghost point"),
 }
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); a DFMA probe measured 1.0
 
@@ -62,6 +66,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); a DFMA probe m
 def units_per_launch(cls: str, n: int) -> int:
     if cls == "recovery":
         return (n + 4) ** 3
+    if cls == "ghost":
+        return (n + 4) ** 3 - n ** 3
     if cls.startswith("flux"):
         return (n + 1) * (n + 2) * (n + 2)
     return (n + 1) ** 3
