@@ -42,9 +42,9 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 # Algorithmic work per item of each kernel class of the mixed path, counted from the
-# formulas: FP64 flops of the precision split, FP32 flops of the
-# bulk arithmetic (FMA = 2), and unique HBM bytes.  A kernel's roofline is the resource it
-# uses the largest fraction of.
+# formulas the kernels evaluate: FP64 flops of the precision split, FP32 flops of the bulk
+# arithmetic (FMA = 2), and unique HBM bytes.  A kernel's roofline is the resource it uses
+# the largest fraction of.
 KCLASS = {
     "recovery": dict(fp64=23, fp32=30, bytes=64 + 8 * 4, unit="padded cell"),
     "flux1_x": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
@@ -61,6 +61,10 @@ KCLASS = {
     "ghost": dict(fp64=0, fp32=0, bytes=8 * 4 * 2, unit="ghost point"),
 }
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); a DFMA probe measured 1.0
+# DRAM bytes (read + write) per point of the fused update, from one ncu capture of this
+# kernel on turbulence 128^3 (520.6 MB per launch over 129^3 points); scaled by the points of
+# a launch.  Retake it when the kernel changes.
+MEASURED_DRAM_BYTES_PER_POINT = {"update": 520.6e6 / 129 ** 3}
 
 
 def units_per_launch(cls: str, n: int) -> int:
@@ -377,7 +381,9 @@ def run_ours(args, world, rank, local, pg):
         roofs[k] = dict(cand[best], others={r: round(cand[r]["frac"], 4) for r in cand if r != best})
     dom = max(roofs, key=lambda k: prof[k][0])
     roof = dict(roofs[dom])
-    roof.update({"traffic": None, "kernel": dom})
+    per_point = MEASURED_DRAM_BYTES_PER_POINT.get(dom)
+    roof.update({"traffic": per_point * units_per_launch(dom, n) if per_point else None, "kernel": dom,
+                 "traffic_note": "ncu DRAM bytes per point at 128^3, scaled to this launch" if per_point else None})
     shares = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
 
     # plain FP64 path on the same box
