@@ -448,6 +448,130 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
+# ------------------------------------------------------------------ --table ----
+def run_table(args):
+    """Every workload configuration, GPU and oracle side by side (opt-in, minutes): GPU
+    zone-updates/s of the plain FP64 path and the mixed path; the oracle on one host core and
+    on all of them, each on a bounded sample stated in the output; and, for the 1D shock
+    tube and the 2D vortex, the per-field L1 difference from the oracle at the end time."""
+    import torch
+    import oracle
+    from paper_1502_02935_gb300 import inputs, mhd
+    hbm_peak, _, _ = load_peaks()
+    ncores = os.cpu_count() or 1
+    stream = torch.cuda.Stream()
+
+    def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None):
+        sts = states if isinstance(states, list) else [states]
+        g = mhd.Grid(sts if len(sts) > 1 else sts[0], precision=precision, cfl=CFL, flags=flags,
+                     stream=stream.cuda_stream)
+        if src:
+            g.set_sources(**src)
+        if thermal:
+            g.set_thermal(mhd.THERMAL_PLAIN, **thermal)
+        if flags & mhd.FLAG_PERSISTENT:
+            g.autotune(None)
+        for _ in range(3):
+            g.step(-1.0)
+        torch.cuda.synchronize()
+        ms = timed_steps(g, steps, stream)
+        g.close()
+        return sum(st.geom.ncell for st in sts) * steps / (ms / 1e3)
+
+    def oracle_rate(states, threads, steps, src=None, thermal=None, cfl=CFL):
+        oracle.set_threads(threads)
+        sts = states if isinstance(states, list) else [states]
+        t0 = time.perf_counter()
+        for st in sts:
+            for _ in range(steps):
+                dt = oracle.cfl_dt(st, cfl, source=src)
+                st = oracle.step(st, dt, source=src)
+                if thermal:
+                    st, _ = oracle.thermal_apply(st, dt, thermal)
+        el = time.perf_counter() - t0
+        return sum(st.geom.ncell for st in sts) * steps / el, el
+
+    def gpu_to_time(st, precision, cfl, t_end):
+        g = mhd.Grid(st, precision=precision, cfl=cfl, stream=stream.cuda_stream)
+        t, n = 0.0, 0
+        while t < t_end * (1 - 1e-14):
+            dt = min(g.cfl_dt(), t_end - t)
+            g.step(dt)
+            t += dt
+            n += 1
+        out = g.get_state(0)
+        g.close()
+        return out, n
+
+    def l1(a, b):
+        names = ["rho", "mx", "my", "mz", "E"]
+        res = {nm: float(np.sum(np.abs(a.U[q] - b.U[q])) / max(np.sum(np.abs(b.U[q])), 1e-300))
+               for q, nm in enumerate(names)}
+        for nm in ("Bx", "By", "Bz"):
+            x, y = getattr(a, nm), getattr(b, nm)
+            res[nm] = float(np.sum(np.abs(x - y)) / max(np.sum(np.abs(y)), 1e-300))
+        return {k: v for k, v in res.items() if np.isfinite(v)}
+
+    table = {}
+    # C1: 1D shock tube, plain FP64 only
+    st = inputs.brio_wu(800)
+    oracle.set_threads(ncores)
+    ref, nref = oracle.run(st, 0.8, 0.1)
+    t0 = time.perf_counter()
+    got, n = gpu_to_time(st, "fp64", 0.8, 0.1)
+    el = time.perf_counter() - t0
+    r1, _ = oracle_rate(st, 1, 50, cfl=0.8)
+    rn, _ = oracle_rate(st, ncores, 50, cfl=0.8)
+    table["C1 Brio-Wu 800, FP64, t=0.1"] = {
+        "gpu_fp64": 800 * n / el, "gpu_note": f"{n} steps with a host CFL query each (latency-bound)",
+        "oracle_1core": r1, "oracle_all": rn, "steps": n, "oracle_steps": nref, "l1_fp64_vs_oracle": l1(got, ref)}
+    # C2: 2D vortex 512^2, FP64 and mixed, to t = 0.5
+    st = inputs.orszag_tang(512, 512)
+    oracle.set_threads(ncores)
+    t0 = time.perf_counter()
+    ref, nref = oracle.run(st, CFL, 0.5)
+    el_ref = time.perf_counter() - t0
+    g64, _ = gpu_to_time(st, "fp64", CFL, 0.5)
+    gmx, _ = gpu_to_time(st, "mixed", CFL, 0.5)
+    r1, _ = oracle_rate(st, 1, 10)
+    table["C2 Orszag-Tang 512^2, t=0.5"] = {
+        "gpu_fp64": gpu_rate(st, "fp64", 200), "gpu_mixed": gpu_rate(st, "mixed", 200),
+        "oracle_1core": r1, "oracle_all": 512 * 512 * nref / el_ref, "oracle_steps": nref,
+        "l1_fp64_vs_oracle": l1(g64, ref), "l1_mixed_vs_oracle": l1(gmx, ref)}
+    # C3: turbulence 256^3
+    st = inputs.turbulence(256, seed=SEED)
+    mixed = gpu_rate(st, "mixed", 20)
+    r1, _ = oracle_rate(inputs.turbulence(64, seed=SEED), 1, 5)
+    rn, _ = oracle_rate(st, ncores, 2)
+    table["C3 turbulence 256^3"] = {
+        "gpu_fp64": gpu_rate(st, "fp64", 5), "gpu_mixed": mixed, "hbm_alg_frac_mixed": mixed * 128 / (hbm_peak * 1e9),
+        "oracle_1core": r1, "oracle_1core_sample": "64^3 box, 5 steps", "oracle_all": rn,
+        "oracle_all_sample": "256^3 box, 2 steps"}
+    # C4: 64 blast patches
+    sts = inputs.blast_batch(64, seed=SEED)
+    r1, _ = oracle_rate(sts[:4], 1, 1)
+    rn, _ = oracle_rate(sts, ncores, 1)
+    table["C4 64 blast patches"] = {
+        "gpu_fp64_per_phase": gpu_rate(sts, "fp64", 3),
+        "gpu_mixed_per_phase": gpu_rate(sts, "mixed", 10),
+        "gpu_mixed_persistent": gpu_rate(sts, "mixed", 10, flags=mhd.FLAG_GRAPH | mhd.FLAG_PERSISTENT),
+        "oracle_1core": r1, "oracle_1core_sample": "first 4 patches, 1 step", "oracle_all": rn,
+        "oracle_all_sample": "all 64 patches, 1 step"}
+    # C5: disc with the plain thermal integrator (surrogate figures: the default bench run)
+    th = inputs.DISC_THERMAL
+    src = dict(inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+    st = inputs.disc(512, 512, 128)
+    r1, _ = oracle_rate(inputs.disc(128, 128, 32), 1, 2, src=src, thermal=th)
+    rn, _ = oracle_rate(st, ncores, 1, src=src, thermal=th)
+    table["C5 disc 512x512x128, plain thermal"] = {
+        "gpu_fp64": gpu_rate(st, "fp64", 3, src=src, thermal=th),
+        "gpu_mixed": gpu_rate(st, "mixed", 10, src=src, thermal=th),
+        "oracle_1core": r1, "oracle_1core_sample": "128x128x32 disc, 2 steps", "oracle_all": rn,
+        "oracle_all_sample": "512x512x128 disc, 1 step"}
+    print(json.dumps({"table": table, "host_cores": ncores, "unit": "zone-updates/s"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,8 +585,12 @@ def main():
                     help="disc workload cells (nx ny nz); 0 0 0 skips it")
     ap.add_argument("--disc-steps", dest="disc_steps", type=int, nargs=2, default=[50, 150],
                     help="disc workload: plain (harvest) steps, then surrogate steps")
+    ap.add_argument("--table", action="store_true",
+                    help="every workload configuration, GPU and oracle side by side (minutes; no bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.table:
+        return run_table(args)
     if args.disc == [0, 0, 0]:
         args.disc = None
     world, rank, local, pg = dist_setup()
