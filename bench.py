@@ -282,7 +282,7 @@ def run_disc(args, stream):
     plain_ms = prof["thermal"][0] / max(prof["thermal"][1], 1)
     step_ms_plain = sum(v[0] for v in prof.values()) / harvest_steps
     t0 = time.perf_counter()
-    loss, rows = g.surrogate_train(epochs=40, batch=8192, lr=3e-3, seed=SEED)
+    loss, rows = g.surrogate_train(epochs=100, batch=8192, lr=3e-3, seed=SEED)
     train_s = time.perf_counter() - t0
     mid = g.get_state(0)
     g.set_thermal(mhd.THERMAL_SURROGATE, **th)

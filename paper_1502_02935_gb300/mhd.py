@@ -235,7 +235,7 @@ class Grid:
     def surrogate_harvest(self, capacity: int, stride: int = 1):
         self._check(self.L.mhd_surrogate_harvest(self.h, int(capacity), int(stride)), "mhd_surrogate_harvest")
 
-    def surrogate_train(self, epochs=20, batch=4096, lr=3e-3, seed=1502, qmax=0.0):
+    def surrogate_train(self, epochs=100, batch=8192, lr=3e-3, seed=1502, qmax=0.0):
         loss = C.c_double()
         rows = C.c_longlong()
         self._check(self.L.mhd_surrogate_train(self.h, int(epochs), int(batch), float(lr), int(seed), float(qmax),
