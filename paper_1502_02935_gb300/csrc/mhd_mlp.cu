@@ -238,13 +238,14 @@ __global__ void __launch_bounds__(256) k_thermal_fallback(PatchDev P, ThermalDev
                                                           const unsigned long long* __restrict__ fb_count) {
   const long long n = (long long)*fb_count;
   const double dt = *P.dt_used;
+  const double cef = th_cef(P, th);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long c = fb_list[q];
     const int i = (int)(c % P.n[0]);
     const long long r = c / P.n[0];
     const int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
     double T, nh, ce;
-    th_cell(P, th, P.Un, i, j, k, T, nh, ce);
+    th_cell(P, th, P.Un, i, j, k, cef, T, nh, ce);
     int st, nsub;
     const double T1 = th_integrate(T, nh, ce, dt, th, &st, &nsub);
     P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);

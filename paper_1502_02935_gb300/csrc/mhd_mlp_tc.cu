@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
   const double dt = *P.dt_used;
   const float ldt = log10f((float)dt);
   const DlinConst dc = th_dlin_const(th, P.gm1);
+  const double cef = th_cef(P, th);
+  const float zf = (float)th.z;
   for (long long base = (long long)blockIdx.x * kTcRows; base < nc; base += (long long)gridDim.x * kTcRows) {
     const long long c = base + threadIdx.x;
     int i = 0, j = 0, k = 0;
@@ -223,8 +225,10 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
       const long long r = c / P.n[0];
       j = (int)(r % P.n[1]);
       k = (int)(r / P.n[1]);
-      th_cell(P, th, P.Un, i, j, k, T, nh, ce);
-      const float raw[4] = {log10f((float)nh), log10f((float)th_clamp(T)), ldt, (float)th.z};
+      th_cell(P, th, P.Un, i, j, k, cef, T, nh, ce);
+      // features in FP32 (integer-pipe conversions; the clamp lets a NaN through to fall back)
+      const float tf = d2f_alu(T);
+      const float raw[4] = {log10f(d2f_alu(nh)), log10f(tf < 10.0f ? 10.0f : (tf > 1e8f ? 1e8f : tf)), ldt, zf};
       dl = th_scale(th_dlin(dc, raw[0], raw[1], raw[2]));
       inrange = true;
 #pragma unroll
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
       const float d = y * dl;  // predicted change of log10 T
       if (inrange && fabsf(y) <= M.qmax && fabsf(d) <= M.dmax) {
         const double T0 = th_clamp(T);
-        const double T1 = th_clamp(T0 * (double)exp10f(d));
+        const double T1 = th_clamp(T0 * f2d_alu(exp10f(d)));
         P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);
       } else {
         fb_list[atomicAdd(fb_count, 1ull)] = (int)c;

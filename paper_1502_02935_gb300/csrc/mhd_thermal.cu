@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(256) k_thermal_plain(PatchDev P, ThermalDev th
   const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const double dt = *P.dt_used;
+  const double cef = th_cef(P, th);
   int nsub = 0, capped = 0, live = 0;
   if (c < nc) {
     const int i = (int)(c % P.n[0]);
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(256) k_thermal_plain(PatchDev P, ThermalDev th
     const int j = (int)(r % P.n[1]);
     const int k = (int)(r / P.n[1]);
     double T, nh, ce;
-    th_cell(P, th, P.Un, i, j, k, T, nh, ce);
+    th_cell(P, th, P.Un, i, j, k, cef, T, nh, ce);
     int st;
     const double T1 = th_integrate(T, nh, ce, dt, th, &st, &nsub);
     P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);

@@ -152,20 +152,29 @@ __device__ __forceinline__ float th_scale(float D) { return D / (1.0f + fabsf(D)
 constexpr float kQClip = 8.0f;  // harvested targets are clipped to [-kQClip, kQClip]
 constexpr int kHvCols = 6;      // harvested row: log10 n_H, log10 T, log10 dt, Z, q, change
 
-// Temperature, n_H and c_e of interior cell (i, j, k) from the FP64 state.
+// Temperature, n_H and c_e of interior cell (i, j, k) from the FP64 state.  The same
+// arithmetic as the recovery of the step (no FP64 division, which costs the FP64 pipe about
+// ten instructions here): 1/rho from the FP32 reciprocal and one FP64 Newton step (relative
+// error ~1e-14), face sums with the factors (gamma-1)/2 and (gamma-1)/8 folded in;
+// cef = 1 / (t_per_pr (gamma - 1)), computed once per launch by th_cef.
+__device__ __forceinline__ double th_cef(const PatchDev& P, const ThermalDev& th) {
+  return 1.0 / (th.t_per_pr * P.gm1);
+}
+
 __device__ __forceinline__ void th_cell(const PatchDev& P, const ThermalDev& th, const double* __restrict__ U,
-                                        int i, int j, int k, double& T, double& nh, double& ce) {
+                                        int i, int j, int k, double cef, double& T, double& nh, double& ce) {
   const long long FS = P.FS, c = sidx(P, i, j, k);
   const double rho = U[c];
-  const double vx = U[MX * FS + c] / rho, vy = U[MY * FS + c] / rho, vz = U[MZ * FS + c] / rho;
-  const double bx = 0.5 * (U[BXF * FS + c] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)]);
-  const double by = 0.5 * (U[BYF * FS + c] + U[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)]);
-  const double bz = 0.5 * (U[BZF * FS + c] + U[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))]);
-  const double p = P.gm1 * (U[EN * FS + c] - 0.5 * rho * (vx * vx + vy * vy + vz * vz) -
-                            0.5 * (bx * bx + by * by + bz * bz));
-  T = th.t_per_pr * p / rho;
+  const double irho = inv_density<float>(rho);
+  const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c];
+  const double sbx = U[BXF * FS + c] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)];
+  const double sby = U[BYF * FS + c] + U[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)];
+  const double sbz = U[BZF * FS + c] + U[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))];
+  const double p = P.gm1 * U[EN * FS + c] - P.hgm1 * ((mx * mx + my * my + mz * mz) * irho) -
+                   P.egm1 * (sbx * sbx + sby * sby + sbz * sbz);
+  T = th.t_per_pr * p * irho;
   nh = th.nh_per_rho * rho;
-  ce = rho / (th.t_per_pr * P.gm1);
+  ce = rho * cef;
 }
 
 }  // namespace mhd
