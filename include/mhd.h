@@ -141,11 +141,15 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* src);
 
 /* Advance every patch by one van Leer step (Eq. 7, Eq. 8).  dt > 0: that dt for
  * every patch.  dt <= 0: each patch uses cfl * its own CFL limit of its current
- * state, computed on the device (no host synchronisation).  Asynchronous. */
+ * state, computed on the device (no host synchronisation).  Asynchronous.
+ * Runs are bitwise reproducible: a state read out with mhd_get_state and set back
+ * with mhd_set_state continues exactly as the uninterrupted run. */
 int mhd_step(mhd_ctx* ctx, double dt);
 
 /* cfl * min over all patches, cells and active axes of d/(|v_d| + c_fast,d) for the
- * current state.  Synchronises the stream. */
+ * current state: bit for bit the dt that mhd_step(ctx, -1) takes next (for one patch;
+ * with several, each patch takes its own, mhd_cfl_dt_patches).  Synchronises the
+ * stream. */
 int mhd_cfl_dt(mhd_ctx* ctx, double* dt_out);
 
 /* Per-patch CFL time steps, n_patches values.  Synchronises. */

@@ -373,3 +373,30 @@ def test_orszag_tang_to_t05_against_oracle():
                            ("E", got.U[4], ref.U[4]), ("Bx", got.Bx, ref.Bx), ("By", got.By, ref.By)):
             l1 = float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
             assert l1 <= bound, (precision, name, l1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_restart_is_bitwise(precision):
+    """Six device-CFL steps in one run equal three steps, a read-out of the state, a new
+    context from it and three more steps, bit for bit (the recovery that the new context
+    starts with gives the same W and CFL step as the update fused with it), with and
+    without graph replay."""
+    st = inputs.turbulence((24, 20, 16), seed=11)
+    for flags in (0, mhd.FLAG_GRAPH):
+        a = mhd.Grid(st, precision=precision, cfl=0.4, flags=flags)
+        for _ in range(6):
+            a.step(-1.0)
+        sa = a.get_state(0)
+        a.close()
+        b = mhd.Grid(st, precision=precision, cfl=0.4, flags=flags)
+        for _ in range(3):
+            b.step(-1.0)
+        mid = b.get_state(0)
+        b.close()
+        c = mhd.Grid(mid, precision=precision, cfl=0.4, flags=flags)
+        for _ in range(3):
+            c.step(-1.0)
+        sc = c.get_state(0)
+        c.close()
+        for f in ("U", "Bx", "By", "Bz"):
+            assert np.array_equal(getattr(sa, f), getattr(sc, f)), (flags, f)
