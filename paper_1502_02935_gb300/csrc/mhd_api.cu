@@ -77,6 +77,12 @@ struct mhd_ctx {
   double cfl = 0.4;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // several patches: each patch's step is an independent chain of launches, spread over
+  // these streams (forked from and joined back into `stream`)
+  std::vector<cudaStream_t> aux;
+  std::vector<int> aux_of;  // stream of each patch (cells balanced, largest patches first)
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   std::vector<PatchHost> P;
   Backend be{};
   SourceDev src{};
@@ -166,6 +172,9 @@ static void free_ctx(mhd_ctx* ctx) {
   if (ctx->dt_used) cudaFree(ctx->dt_used);
   if (ctx->err) cudaFree(ctx->err);
   if (ctx->staging) cudaFree(ctx->staging);
+  for (auto a : ctx->aux) cudaStreamDestroy(a);
+  for (auto e : ctx->ev_join) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -382,16 +391,40 @@ static int issue_step(mhd_ctx* ctx, double dt) {
     if (rc == MHD_OK && ctx->profiling) return flush_profile(ctx);
     return rc;
   }
+  StageArgs a{};
+  a.dt_host = dt;
+  a.cfl = ctx->cfl;
+  a.src = ctx->src;
+  if (!ctx->aux.empty() && !ctx->profiling) {
+    // one chain per patch: [recovery], predictor, reset of its CFL slot, corrector
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    for (auto q : ctx->aux) CK(cudaStreamWaitEvent(q, ctx->ev_fork, 0));
+    for (int p = 0; p < ctx->np; ++p) {
+      cudaStream_t q = ctx->aux[ctx->aux_of[p]];
+      const PatchDev& D = ctx->P[p].dev;
+      if (!ctx->w_valid) {
+        CK(cudaMemsetAsync(ctx->cfl_min + p, 0xFF, sizeof(unsigned long long), q));
+        if (ctx->be.prim(D, q, &ctx->launches, nullptr)) return cuda_fail(ctx, cudaGetLastError(), "recovery launch");
+      }
+      for (int stage = 0; stage < 2; ++stage) {
+        a.stage = stage;
+        if (stage == 1) CK(cudaMemsetAsync(ctx->cfl_min + p, 0xFF, sizeof(unsigned long long), q));
+        if (ctx->be.stage(D, a, q, &ctx->launches, nullptr)) return cuda_fail(ctx, cudaGetLastError(), "stage launch");
+      }
+    }
+    for (size_t q = 0; q < ctx->aux.size(); ++q) {
+      CK(cudaEventRecord(ctx->ev_join[q], ctx->aux[q]));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[q], 0));
+    }
+    step_transition(ctx);
+    return issue_thermal_all(ctx);  // the thermal term shares its fallback list: after the join
+  }
   if (!ctx->w_valid) {
     CK(cudaMemsetAsync(ctx->cfl_min, 0xFF, sizeof(unsigned long long) * ctx->np, ctx->stream));
     for (auto& p : ctx->P)
       if (ctx->be.prim(p.dev, ctx->stream, &ctx->launches, prof))
         return cuda_fail(ctx, cudaGetLastError(), "recovery launch");
   }
-  StageArgs a{};
-  a.dt_host = dt;
-  a.cfl = ctx->cfl;
-  a.src = ctx->src;
   for (int stage = 0; stage < 2; ++stage) {
     a.stage = stage;
     // the corrector accumulates the CFL limit of the new state into a reset slot (the
@@ -531,6 +564,26 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
   if (g->flags & MHD_FLAG_PERSISTENT) {
     ctx->persistent = true;
     if (build_tables(ctx, 32, 8, 1.0)) return bail(MHD_ERR_CUDA);
+  } else if (ctx->np > 1) {
+    const int ns = ctx->np < 8 ? ctx->np : 8;
+    ctx->aux.assign(ns, nullptr);
+    ctx->ev_join.assign(ns, nullptr);
+    for (int q = 0; q < ns; ++q)
+      if (cudaStreamCreateWithFlags(&ctx->aux[q], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_join[q], cudaEventDisableTiming) != cudaSuccess)
+        return bail(MHD_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MHD_ERR_CUDA);
+    // balance cells over the streams, largest patches first
+    std::vector<int> order(ctx->np);
+    for (int p = 0; p < ctx->np; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ctx->P[x].ncell > ctx->P[y].ncell; });
+    std::vector<long long> load(ns, 0);
+    ctx->aux_of.assign(ctx->np, 0);
+    for (int p : order) {
+      const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      ctx->aux_of[p] = q;
+      load[q] += ctx->P[p].ncell;
+    }
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(MHD_ERR_CUDA);
   *out = ctx;
