@@ -530,7 +530,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
               (long long)n[0] * n[1] * (n[2] + 1);
     if (H.dense > max_dense) max_dense = H.dense;
     const size_t sbytes = sizeof(double) * 16 * (size_t)D.FS;
-    const size_t qbytes = ctx->be.scratch_elem * (size_t)(8 + 3 * NFLUX + 3) * (size_t)D.QS;
+    const size_t qbytes = ctx->be.scratch_elem * (size_t)(NWQ + 3 * NFLUX + 3) * (size_t)D.QS;
     if (cudaMalloc(&H.state, sbytes) != cudaSuccess) return bail(MHD_ERR_NOMEM);
     if (cudaMalloc(&H.scratch, qbytes) != cudaSuccess) return bail(MHD_ERR_NOMEM);
     cudaMemset(H.state, 0, sbytes);
@@ -540,7 +540,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     char* q = (char*)H.scratch;
     const size_t fs = ctx->be.scratch_elem * (size_t)D.QS;
     D.W = q;
-    q += 8 * fs;
+    q += NWQ * fs;
     for (int a = 0; a < 3; ++a) {
       D.F[a] = q;
       q += NFLUX * fs;

@@ -23,6 +23,8 @@ namespace mhd {
 
 enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BXF = 5, BYF = 6, BZF = 7 };
 enum { WR = 0, WVX = 1, WVY = 2, WVZ = 3, WP = 4, WBX = 5, WBY = 6, WBZ = 7 };
+// stored with W: the cell EMF -(v x B), components x, y, z (read by the corner EMFs)
+enum { WEX = 8, WEY = 9, WEZ = 10, NWQ = 11 };
 enum { NFLUX = 8 };  // rho, mx, my, mz, E, B_t1, B_t2, mass-flux scale
 enum : int { ERR_NONFINITE = 1, ERR_NEGATIVE = 2, ERR_TIMEOUT = 4 };
 enum { POT_NONE = 0, POT_GAUSS_X = 1, POT_LOG_DISC = 2 };
@@ -409,6 +411,9 @@ template <class R> __device__ __forceinline__ R centre(const PatchDev& P, int a,
 }
 
 // ---------------------------------------------------------- phase: recovery --
+// cell EMF -(v x B)_C (Eq. 9) from the velocity and field components A = C+1, B = C+2
+template <class R> __device__ __forceinline__ R cell_emf(R vA, R vB, R bA, R bB) { return -(vA * bB - vB * bA); }
+
 // exponent test of a double on the integer pipe (not inf, not NaN)
 __device__ __forceinline__ bool finite_d(double x) {
   return ((unsigned)__double2hiint(x) & 0x7FF00000u) != 0x7FF00000u;
@@ -446,6 +451,9 @@ __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx,
     W[WBX * QS + q] = bx;
     W[WBY * QS + q] = by;
     W[WBZ * QS + q] = bz;
+    W[WEX * QS + q] = cell_emf<R>(vy, vz, by, bz);
+    W[WEY * QS + q] = cell_emf<R>(vz, vx, bz, bx);
+    W[WEZ * QS + q] = cell_emf<R>(vx, vy, bx, by);
   }
   R lim = R(INFINITY);
   if (interior) {
@@ -608,8 +616,6 @@ __device__ __forceinline__ R corner_core(R Ea_b, R Ea_bm, R Eb_a, R Eb_am, R ec0
   return R(0.25) * (Ea_b + Ea_bm + Eb_a + Eb_am) + R(0.25) * (d_b3q - d_bq) + R(0.25) * (d_a3q - d_aq);
 }
 
-// cell EMF -(v x B)_C from the velocity and field components A, B
-template <class R> __device__ __forceinline__ R cell_emf(R vA, R vB, R bA, R bB) { return -(vA * bB - vB * bA); }
 
 template <class R, int C>
 __device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restrict__ W,
@@ -628,14 +634,9 @@ __device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restr
   } else {
     const long long sa = qstride(P, A), sb = qstride(P, B);
     const long long oa = q - sa, ob = q - sb, oab = q - sa - sb;
-    const R* vA = W + (WVX + A) * QS;
-    const R* vB = W + (WVX + B) * QS;
-    const R* bA = W + (WBX + A) * QS;
-    const R* bB = W + (WBX + B) * QS;
-    e = corner_core<R>(-FA[5 * QS + q], -FA[5 * QS + ob], FB[6 * QS + q], FB[6 * QS + oa],
-                       cell_emf<R>(vA[q], vB[q], bA[q], bB[q]), cell_emf<R>(vA[oa], vB[oa], bA[oa], bB[oa]),
-                       cell_emf<R>(vA[ob], vB[ob], bA[ob], bB[ob]), cell_emf<R>(vA[oab], vB[oab], bA[oab], bB[oab]),
-                       FA[q], FA[7 * QS + q], FA[ob], FA[7 * QS + ob], FB[q], FB[7 * QS + q], FB[oa],
+    const R* ec = W + (WEX + C) * QS;  // cell EMFs stored by the recovery
+    e = corner_core<R>(-FA[5 * QS + q], -FA[5 * QS + ob], FB[6 * QS + q], FB[6 * QS + oa], ec[q], ec[oa], ec[ob],
+                       ec[oab], FA[q], FA[7 * QS + q], FA[ob], FA[7 * QS + ob], FB[q], FB[7 * QS + q], FB[oa],
                        FB[7 * QS + oa]);
   }
   E[C * QS + q] = e;
@@ -854,7 +855,7 @@ __device__ __forceinline__ void ghost_point(const PatchDev& P, const double* __r
   if (copy) {
     const long long QS = P.QS, t = qidx(P, i, j, k), q = qidx(P, cmap(P, 0, i), cmap(P, 1, j), cmap(P, 2, k));
 #pragma unroll
-    for (int m = 0; m < 8; ++m) W[m * QS + t] = W[m * QS + q];
+    for (int m = 0; m < NWQ; ++m) W[m * QS + t] = W[m * QS + q];
   } else {
     prim_point<R>(P, U, W, i, j, k, true, false);
   }
