@@ -53,18 +53,18 @@ KCLASS = {
     "flux2_x": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "flux2_y": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "flux2_z": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "emf": dict(fp64=0, fp32=75, bytes=(12 + 6 + 3) * 4, unit="edge point"),
+    "emf": dict(fp64=0, fp32=60, bytes=(12 + 3 + 3) * 4, unit="edge point"),
     # update fused with the recovery of the new state: FP64 = 14 DADD (cell, six faces, three
     # face sums) + |m|^2 and |B|^2 (5 + 5) + Newton step of 1/rho (4) + p (6); bytes = F (60) +
-    # E (12) + base U (64) + new U (64) + new W (32)
-    "update": dict(fp64=34, fp32=130, bytes=15 * 4 + 3 * 4 + 64 + 64 + 8 * 4, unit="point"),
-    "ghost": dict(fp64=0, fp32=0, bytes=8 * 4 * 2, unit="ghost point"),
+    # E (12) + base U (64) + new U (64) + new W and cell EMF (44)
+    "update": dict(fp64=34, fp32=140, bytes=15 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="point"),
+    "ghost": dict(fp64=0, fp32=0, bytes=11 * 4 * 2, unit="ghost point"),
 }
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); a DFMA probe measured 1.0
 # DRAM bytes (read + write) per point of the fused update, from one ncu capture of this
-# kernel on turbulence 128^3 (520.6 MB per launch over 129^3 points); scaled by the points of
+# kernel on turbulence 128^3 (554.1 MB per launch over 129^3 points); scaled by the points of
 # a launch.  Retake it when the kernel changes.
-MEASURED_DRAM_BYTES_PER_POINT = {"update": 520.6e6 / 129 ** 3}
+MEASURED_DRAM_BYTES_PER_POINT = {"update": 554.1e6 / 129 ** 3}
 
 
 def units_per_launch(cls: str, n: int) -> int:
