@@ -42,11 +42,13 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 # Algorithmic work per item of each kernel class of the mixed path, counted from the
-# formulas the kernels evaluate: FP64 flops of the precision split, FP32 flops of the bulk
-# arithmetic (FMA = 2), and unique HBM bytes.  A kernel's roofline is the resource it uses
-# the largest fraction of.
+# formulas the kernels evaluate: FP64 pipe operations of the precision split (an add, a
+# multiply or an FMA is one operation: each holds the FP64 pipe for the same time), FP32
+# flops of the bulk arithmetic (FMA = 2), and unique HBM bytes.  A kernel's roofline is the
+# resource it uses the largest fraction of.
 KCLASS = {
-    "recovery": dict(fp64=23, fp32=30, bytes=64 + 8 * 4, unit="padded cell"),
+    # recovery: three face sums, |m|^2 and |B|^2 (3 + 3), Newton step of 1/rho (2), p (4)
+    "recovery": dict(fp64=15, fp32=30, bytes=64 + 8 * 4, unit="padded cell"),
     "flux1_x": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "flux1_y": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "flux1_z": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
@@ -54,13 +56,15 @@ KCLASS = {
     "flux2_y": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "flux2_z": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
     "emf": dict(fp64=0, fp32=60, bytes=(12 + 3 + 3) * 4, unit="edge point"),
-    # update fused with the recovery of the new state: FP64 = 14 DADD (cell, six faces, three
-    # face sums) + |m|^2 and |B|^2 (5 + 5) + Newton step of 1/rho (4) + p (6); bytes = F (60) +
+    # update fused with the recovery of the new state: FP64 = 14 adds (cell, six faces, three
+    # face sums) + |m|^2 and |B|^2 (3 + 3) + Newton step of 1/rho (2) + p (4); bytes = F (60) +
     # E (12) + base U (64) + new U (64) + new W and cell EMF (44)
-    "update": dict(fp64=34, fp32=140, bytes=15 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="point"),
+    "update": dict(fp64=26, fp32=140, bytes=15 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="point"),
     "ghost": dict(fp64=0, fp32=0, bytes=11 * 4 * 2, unit="ghost point"),
 }
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (profiling recipe); a DFMA probe measured 1.0
+# FP64 pipe operations per clock per SM: the nominal 1.25 TFLOP/s of the part is
+# 152 SMs x 2 FMAs x 2 flops x ~2.06 GHz.  (A DFMA probe measured 1.0 TFLOP/s.)
+FP64_OPS_PER_SM_CLK = 2
 # DRAM bytes (read + write) per point of the fused update, from one ncu capture of this
 # kernel on turbulence 128^3 (554.1 MB per launch over 129^3 points); scaled by the points of
 # a launch.  Retake it when the kernel changes.
@@ -362,6 +366,7 @@ def run_ours(args, world, rank, local, pg):
     grid.set_profiling(False)
     tot = sum(v[0] for v in prof.values()) or 1.0
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    fp64_peak = SM_COUNT * FP64_OPS_PER_SM_CLK * sm_max_mhz * 1e6 / 1e9
     roofs = {}
     for k, kc in KCLASS.items():
         if not prof.get(k) or not prof[k][1]:
@@ -373,9 +378,9 @@ def run_ours(args, world, rank, local, pg):
                     "peak_note": f"{peak_kind} hbm_gbs"},
             "fp32": {"bound": "alu", "pipe": "fp32", "achieved": kc["fp32"] * units / t / 1e12, "peak": fp32_peak,
                      "unit": "TFLOP/s", "peak_note": f"FP32: 152 SMs x 128 lanes x 2 x {sm_max_mhz:.0f} MHz (derived)"},
-            "fp64": {"bound": "alu", "pipe": "fp64", "achieved": kc["fp64"] * units / t / 1e12,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "peak_note": "FP64: nominal 1.25 TFLOP/s (recipe); a DFMA probe measured 1.0"},
+            "fp64": {"bound": "alu", "pipe": "fp64", "achieved": kc["fp64"] * units / t / 1e9,
+                     "peak": fp64_peak, "unit": "Gop/s",
+                     "peak_note": f"FP64 pipe: 152 SMs x 2 ops/clk x {sm_max_mhz:.0f} MHz (derived)"},
         }
         for c in cand.values():
             c["frac"] = c["achieved"] / c["peak"]
