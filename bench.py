@@ -61,6 +61,10 @@ KCLASS = {
     # E (12) + base U (64) + new U (64) + new W and cell EMF (44)
     "update": dict(fp64=26, fp32=140, bytes=15 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="point"),
     "ghost": dict(fp64=0, fp32=0, bytes=11 * 4 * 2, unit="ghost point"),
+    # corner EMFs fused with the update (three active axes): FP64 = 5 cell adds + 3 face
+    # updates + 3 face sums + 12 recovery; bytes = F of three directions (96) + cell EMFs of
+    # the input state (12) + base U (64) + new U (64) + new W and cell EMF (44)
+    "emf_update": dict(fp64=23, fp32=200, bytes=24 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="cell"),
 }
 # FP64 pipe operations per clock per SM: the nominal 1.25 TFLOP/s of the part is
 # 152 SMs x 2 FMAs x 2 flops x ~2.06 GHz.  (A DFMA probe measured 1.0 TFLOP/s.)
@@ -78,6 +82,8 @@ def units_per_launch(cls: str, n: int) -> int:
         return (n + 4) ** 3 - n ** 3
     if cls.startswith("flux"):
         return (n + 1) * (n + 2) * (n + 2)
+    if cls == "emf_update":
+        return n ** 3
     return (n + 1) ** 3
 
 

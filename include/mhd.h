@@ -224,12 +224,13 @@ int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long l
  * context's stream (steps are not replayed from a graph) and the elapsed times are summed
  * per kernel class: 0 recovery+CFL, 1-3 donor-cell HLLD fluxes x/y/z, 4-6 kappa-scheme
  * HLLD fluxes x/y/z, 7 corner EMFs, 8 update, 9 standalone CFL, 10 persistent step,
- * 11 thermal source, 12 end-of-step floors, 13 ghost W fill.  Switching on or off clears
- * the totals. */
+ * 11 thermal source, 12 end-of-step floors, 13 ghost W fill, 14 corner EMFs fused with the
+ * update (patches with three active axes; they launch no class 7 or 8 kernel).  Switching on
+ * or off clears the totals. */
 int mhd_set_profiling(mhd_ctx* ctx, int on);
 
 /* Totals since profiling was switched on: ms[c] milliseconds and launches[c] launches of
- * class c, for c < n (n >= 12).  Synchronises. */
+ * class c, for c < n (n >= 15).  Synchronises. */
 int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
 
 /* Autotuner of the persistent batched step (context made with MHD_FLAG_PERSISTENT): times

@@ -530,7 +530,9 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
               (long long)n[0] * n[1] * (n[2] + 1);
     if (H.dense > max_dense) max_dense = H.dense;
     const size_t sbytes = sizeof(double) * 16 * (size_t)D.FS;
-    const size_t qbytes = ctx->be.scratch_elem * (size_t)(NWQ + 3 * NFLUX + 3) * (size_t)D.QS;
+    // W, F (3 directions), E, and for a patch with three active axes a second W buffer
+    const bool w2 = D.act[0] && D.act[1] && D.act[2];
+    const size_t qbytes = ctx->be.scratch_elem * (size_t)(NWQ + 3 * NFLUX + 3 + (w2 ? NWQ : 0)) * (size_t)D.QS;
     if (cudaMalloc(&H.state, sbytes) != cudaSuccess) return bail(MHD_ERR_NOMEM);
     if (cudaMalloc(&H.scratch, qbytes) != cudaSuccess) return bail(MHD_ERR_NOMEM);
     cudaMemset(H.state, 0, sbytes);
@@ -546,6 +548,8 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
       q += NFLUX * fs;
     }
     D.E = q;
+    q += 3 * fs;
+    D.W2 = w2 ? (void*)q : nullptr;
     D.cfl_min = ctx->cfl_min + p;
     D.dt_used = ctx->dt_used + p;
     D.err = ctx->err;

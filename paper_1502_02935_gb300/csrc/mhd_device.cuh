@@ -48,6 +48,7 @@ struct PatchDev {
   void* W;
   void* F[3];
   void* E;
+  void* W2;  // second W buffer of the fused EMF + update kernel (3D patches)
   unsigned long long* cfl_min;  // per-patch ordered-bits minimum of the CFL limit
   double* dt_used;
   int* err;
@@ -617,27 +618,37 @@ __device__ __forceinline__ R corner_core(R Ea_b, R Ea_bm, R Eb_a, R Eb_am, R ec0
 }
 
 
+// Corner EMF E_C at scratch index q when both transverse axes A, B are active.  Every
+// product in corner_core is by 1/4 or 1/2 (exact), so no FMA contraction can change its
+// bits: each evaluation of the same edge gives the same value.
+template <class R, int C>
+__device__ __forceinline__ R corner_value(const PatchDev& P, const R* __restrict__ W, long long q) {
+  constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+  const long long QS = P.QS;
+  const R* FA = (const R*)P.F[A];
+  const R* FB = (const R*)P.F[B];
+  const long long sa = qstride(P, A), sb = qstride(P, B);
+  const long long oa = q - sa, ob = q - sb, oab = q - sa - sb;
+  const R* ec = W + (WEX + C) * QS;  // cell EMFs stored by the recovery
+  return corner_core<R>(-FA[5 * QS + q], -FA[5 * QS + ob], FB[6 * QS + q], FB[6 * QS + oa], ec[q], ec[oa], ec[ob],
+                        ec[oab], FA[q], FA[7 * QS + q], FA[ob], FA[7 * QS + ob], FB[q], FB[7 * QS + q], FB[oa],
+                        FB[7 * QS + oa]);
+}
+
 template <class R, int C>
 __device__ __forceinline__ void corner_point(const PatchDev& P, const R* __restrict__ W,
                                              R* __restrict__ E, int i, int j, int k) {
   constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
   const long long q = qidx(P, i, j, k), QS = P.QS;
-  const R* FA = (const R*)P.F[A];
-  const R* FB = (const R*)P.F[B];
   R e;
   if (P.act[A] && !P.act[B]) {
-    e = -FA[5 * QS + q];
+    e = -((const R*)P.F[A])[5 * QS + q];
   } else if (!P.act[A] && P.act[B]) {
-    e = FB[6 * QS + q];
+    e = ((const R*)P.F[B])[6 * QS + q];
   } else if (!P.act[A] && !P.act[B]) {
     return;
   } else {
-    const long long sa = qstride(P, A), sb = qstride(P, B);
-    const long long oa = q - sa, ob = q - sb, oab = q - sa - sb;
-    const R* ec = W + (WEX + C) * QS;  // cell EMFs stored by the recovery
-    e = corner_core<R>(-FA[5 * QS + q], -FA[5 * QS + ob], FB[6 * QS + q], FB[6 * QS + oa], ec[q], ec[oa], ec[ob],
-                       ec[oab], FA[q], FA[7 * QS + q], FA[ob], FA[7 * QS + ob], FB[q], FB[7 * QS + q], FB[oa],
-                       FB[7 * QS + oa]);
+    e = corner_value<R, C>(P, W, q);
   }
   E[C * QS + q] = e;
 }
@@ -655,6 +666,15 @@ __device__ __forceinline__ void emf_point(const PatchDev& P, const R* __restrict
 // New value of the a-face stored at state index sf whose lower-left edge has scratch
 // index q: B_a - h [dE_c/db - dE_b/dc] (Eq. 8), with explicitly rounded operations so that
 // every evaluation of the same face gives the same bits.
+// The same for a face whose four edge EMFs are given (all three axes active): E_c at the
+// face's lower and upper b-edges, E_b at its lower and upper c-edges.
+template <class R>
+__device__ __forceinline__ double face_from(double b_old, R ec0, R ec1, R eb0, R eb1, R inv_b, R inv_c, R h) {
+  const R curl = Ar<R>::sub_rn(Ar<R>::mul_rn(Ar<R>::sub_rn(ec1, ec0), inv_b),
+                               Ar<R>::mul_rn(Ar<R>::sub_rn(eb1, eb0), inv_c));
+  return __dsub_rn(b_old, Ar<R>::to_d(Ar<R>::mul_rn(h, curl)));
+}
+
 template <class R>
 __device__ __forceinline__ double face_new(const PatchDev& P, const double* __restrict__ Ub,
                                            const R* __restrict__ E, R h, int a, long long sf, long long q) {
@@ -717,34 +737,13 @@ __device__ __forceinline__ void update_point(const PatchDev& P, const double* __
   }
 }
 
-// ------------------------------------------------- fused update and recovery --
-// The fused update of a cell also needs the new values of its upper faces, which the
-// neighbouring cells own and write; it computes them again with face_new, whose explicitly
-// rounded operations make the copy bitwise equal to the owner's value.
-
-// Stage update, then (interior cells) the recovery of the new state: U at cell (i, j, k)
-// and its owned faces as update_point, the end-of-step floors when `last` and the floors
-// are on, and W of the new cell stored at the cell (its ghost images are filled afterwards
-// by ghost_point).  Returns the CFL limit of the new cell (+inf for face-only points);
-// floored cells are added to *nfl.
+// Cell fields of the stage update (Eq. 7 with h S of Eq. 2 evaluated at Us): u = base - h
+// (div F) + h S at interior cell (i, j, k), state index s, scratch index q.
 template <class R>
-__device__ __forceinline__ R update_fused_point(const PatchDev& P, const double* __restrict__ Ub,
-                                                     const double* __restrict__ Us, double* __restrict__ Uo,
-                                                     const R* __restrict__ E, R h, const SourceDev& src,
-                                                     int i, int j, int k, bool last, int* nfl) {
-  const long long s = sidx(P, i, j, k), FS = P.FS;
-  const long long q = qidx(P, i, j, k), QS = P.QS;
-  const int c3[3] = {i, j, k};
-  if (!(i < P.n[0] && j < P.n[1] && k < P.n[2])) {
-    // owned faces on the extra layer of an outflow axis
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int b = (a + 1) % 3, c = (a + 2) % 3;
-      if (c3[a] < P.nface[a] && c3[b] < P.n[b] && c3[c] < P.n[c])
-        Uo[(BXF + a) * FS + s] = face_new<R>(P, Ub, E, h, a, s, q);
-    }
-    return R(INFINITY);
-  }
+__device__ __forceinline__ void cell_update(const PatchDev& P, const double* __restrict__ Ub,
+                                            const double* __restrict__ Us, R h, const SourceDev& src, int i,
+                                            int j, int k, long long s, long long q, double* u) {
+  const long long FS = P.FS, QS = P.QS;
   R div[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -755,7 +754,6 @@ __device__ __forceinline__ R update_fused_point(const PatchDev& P, const double*
 #pragma unroll
     for (int f = 0; f < 5; ++f) div[f] += (Fd[f * QS + q + st] - Fd[f * QS + q]) * idd;
   }
-  double u[5];
   u[0] = Ub[s] - Ar<R>::to_d(h * div[0]);
   if (src.potential == POT_NONE) {
 #pragma unroll
@@ -773,6 +771,38 @@ __device__ __forceinline__ R update_fused_point(const PatchDev& P, const double*
       u[1 + a] = Ub[(MX + a) * FS + s] - Ar<R>::to_d(h * div[1 + a]) + Ar<R>::to_d(h * sm[a]);
     u[4] = Ub[EN * FS + s] - Ar<R>::to_d(h * div[4]) + Ar<R>::to_d(h * se);
   }
+}
+
+// ------------------------------------------------- fused update and recovery --
+// The fused update of a cell also needs the new values of its upper faces, which the
+// neighbouring cells own and write; it computes them again with face_new, whose explicitly
+// rounded operations make the copy bitwise equal to the owner's value.
+
+// Stage update, then (interior cells) the recovery of the new state: U at cell (i, j, k)
+// and its owned faces as update_point, the end-of-step floors when `last` and the floors
+// are on, and W of the new cell stored at the cell (its ghost images are filled afterwards
+// by ghost_point).  Returns the CFL limit of the new cell (+inf for face-only points);
+// floored cells are added to *nfl.
+template <class R>
+__device__ __forceinline__ R update_fused_point(const PatchDev& P, const double* __restrict__ Ub,
+                                                     const double* __restrict__ Us, double* __restrict__ Uo,
+                                                     const R* __restrict__ E, R h, const SourceDev& src,
+                                                     int i, int j, int k, bool last, int* nfl) {
+  const long long s = sidx(P, i, j, k), FS = P.FS;
+  const long long q = qidx(P, i, j, k);
+  const int c3[3] = {i, j, k};
+  if (!(i < P.n[0] && j < P.n[1] && k < P.n[2])) {
+    // owned faces on the extra layer of an outflow axis
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      if (c3[a] < P.nface[a] && c3[b] < P.n[b] && c3[c] < P.n[c])
+        Uo[(BXF + a) * FS + s] = face_new<R>(P, Ub, E, h, a, s, q);
+    }
+    return R(INFINITY);
+  }
+  double u[5];
+  cell_update<R>(P, Ub, Us, h, src, i, j, k, s, q, u);
   // new lower (owned) and upper faces
   double blo[3], bhi[3];
 #pragma unroll

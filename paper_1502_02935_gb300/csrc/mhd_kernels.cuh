@@ -115,6 +115,174 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
   }
 }
 
+// Corner EMFs and the stage update in one kernel, for patches with three active axes.
+// Five resident CTAs per SM (48 registers): four, five and six time the same on 256^3,
+// five is best on 128^3 (measured).  A
+// CTA owns a kTX x kTY column of cells over lz consecutive z-planes and marches up in z.
+// For plane k:
+//  (A) the edge EMFs the plane's faces need -- E_z at plane k, E_x and E_y at plane k + 1
+//      (at the first plane also at k) -- over the tile and its upper halo row and column,
+//      into shared memory;
+//  (B) from them, the new face values -- x and y faces at plane k, z faces at k + 1 (at the
+//      first plane also at k) -- over the tile and its upper halo, into shared memory;
+//      faces of the extra layer of an outflow axis, which no cell owns, are stored here;
+//  (C) each cell: flux divergence and source, its owned (lower) faces stored, the floors
+//      when asked, the recovery of the new state (W, cell EMFs) and its CFL limit.
+// E_x, E_y and the z faces roll between two plane buffers.  Each face is
+// computed about once (about 3.3 FP64 face updates per cell against 6 when every cell
+// recomputes its upper faces), and the edge EMFs do not go through HBM.  Edges and faces
+// of the halo are computed by both CTAs that need them; both get the same bits
+// (corner_value and face_from are insensitive to FMA contraction).  The cell EMFs are
+// read from Win, the W of the stage's input, while CTAs of neighbouring tiles write the W
+// of the new state: that goes to the other buffer, Wout.
+constexpr int kTX = 32, kTY = 8;
+static_assert(kTX * kTY == kBlock, "one thread per cell of a tile plane");
+
+template <class R>
+__device__ __forceinline__ R emf_at(const PatchDev& P, const R* __restrict__ W, int c, int i, int j, int k) {
+  const long long q = qidx(P, i, j, k);
+  return c == 0 ? corner_value<R, 0>(P, W, q) : (c == 1 ? corner_value<R, 1>(P, W, q) : corner_value<R, 2>(P, W, q));
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* __restrict__ Win,
+                                                       R* __restrict__ Wout, const double* __restrict__ Ub,
+                                                       const double* __restrict__ Us, double* __restrict__ Uo,
+                                                       StageArgs a, int lz) {
+  constexpr int SX = kTX + 1;  // row pitch of the arrays with an x halo
+  __shared__ R sEz[(kTY + 1) * SX];
+  __shared__ R sEx[2][(kTY + 1) * kTX];
+  __shared__ R sEy[2][kTY * SX];
+  __shared__ double sBx[kTY * SX];
+  __shared__ double sBy[(kTY + 1) * kTX];
+  __shared__ double sBz[2][kTY * kTX];
+  __shared__ R sh;
+  if (threadIdx.x == 0) {
+    double dt;
+    if (a.stage == 0) {
+      dt = a.dt_host > 0.0 ? a.dt_host : a.cfl * __longlong_as_double((long long)*P.cfl_min);
+      if (blockIdx.x == 0 && blockIdx.y == 0) *P.dt_used = dt;
+    } else {
+      dt = *P.dt_used;
+    }
+    sh = Ar<R>::from_d(a.stage == 0 ? 0.5 * dt : dt);
+  }
+  __syncthreads();
+  const R h = sh;
+  const int ntx = (P.n[0] + kTX - 1) / kTX;
+  const int i0 = (int)(blockIdx.x % ntx) * kTX, j0 = (int)(blockIdx.x / ntx) * kTY;
+  const int kz0 = (int)blockIdx.y * lz;
+  const int kz1 = min(kz0 + lz, P.n[2]);
+  const int ni = min(kTX, P.n[0] - i0), nj = min(kTY, P.n[1] - j0);
+  const int ti = (int)threadIdx.x % kTX, tj = (int)threadIdx.x / kTX;  // warp tj holds row tj
+  const bool own = ti < ni && tj < nj;
+  const R ix = Gam<R>::inv(P, 0), iy = Gam<R>::inv(P, 1), iz = Gam<R>::inv(P, 2);
+  const long long FS = P.FS, QX = P.QX, PX = P.PX;
+  const bool last = a.stage == 1;
+  R lim = R(INFINITY);
+  int nfl = 0;
+  // edge EMF c at tile offset (ii, jj) of plane kk into its shared array
+  auto put_e = [&](int c, int ii, int jj, int kk, int buf) {
+    const R e = emf_at<R>(P, Win, c, i0 + ii, j0 + jj, kk);
+    if (c == 2) sEz[jj * SX + ii] = e;
+    else if (c == 0) sEx[buf][jj * kTX + ii] = e;
+    else sEy[buf][jj * SX + ii] = e;
+  };
+  for (int k = kz0; k < kz1; ++k) {
+    const int cur = (k - kz0) & 1, nxt = cur ^ 1;
+    const bool first = k == kz0;
+    // (A) edge EMFs.  Each thread: E_z(k), E_x(k+1), E_y(k+1) at its own (ti, tj) (and
+    // E_x(k), E_y(k) at the first plane); warps 0-2 (3-4 at the first plane) add the
+    // upper halo row (jj = nj) and column (ii = ni).
+    if (own) {
+      put_e(2, ti, tj, k, 0);
+      put_e(0, ti, tj, k + 1, nxt);
+      put_e(1, ti, tj, k + 1, nxt);
+      if (first) {
+        put_e(0, ti, tj, k, cur);
+        put_e(1, ti, tj, k, cur);
+      }
+    }
+    {
+      const int w = tj, l = ti;
+      if (w == 0 && l < ni) put_e(2, l, nj, k, 0);
+      if (w == 1 && l < ni) put_e(0, l, nj, k + 1, nxt);
+      if (w == 2) {
+        if (l <= nj) put_e(2, ni, l, k, 0);
+        else if (l >= 16 && l - 16 < nj) put_e(1, ni, l - 16, k + 1, nxt);
+      }
+      if (first) {
+        if (w == 3 && l < ni) put_e(0, l, nj, k, cur);
+        if (w == 4 && l < nj) put_e(1, ni, l, k, cur);
+      }
+    }
+    __syncthreads();
+    // (B) new faces.  Each thread: the x and y faces of its cell at plane k and the z face
+    // above it (and the z face below it at the first plane); warps 0-1 add the halo x-face
+    // column (ii = ni) and y-face row (jj = nj).
+    const long long sk = sidx(P, i0, j0, k);
+    if (own) {
+      const long long so = sk + ti + (long long)tj * PX;
+      sBx[tj * SX + ti] = face_from<R>(Ub[BXF * FS + so], sEz[tj * SX + ti], sEz[(tj + 1) * SX + ti],
+                                       sEy[cur][tj * SX + ti], sEy[nxt][tj * SX + ti], iy, iz, h);
+      sBy[tj * kTX + ti] = face_from<R>(Ub[BYF * FS + so], sEx[cur][tj * kTX + ti], sEx[nxt][tj * kTX + ti],
+                                        sEz[tj * SX + ti], sEz[tj * SX + ti + 1], iz, ix, h);
+      const int ku = k + 1;
+      const long long su = sidx(P, i0 + ti, j0 + tj, fmap(P, 2, ku));
+      const double bz = face_from<R>(Ub[BZF * FS + su], sEy[nxt][tj * SX + ti], sEy[nxt][tj * SX + ti + 1],
+                                     sEx[nxt][tj * kTX + ti], sEx[nxt][(tj + 1) * kTX + ti], ix, iy, h);
+      sBz[nxt][tj * kTX + ti] = bz;
+      if (ku == P.n[2] && P.nface[2] > P.n[2]) Uo[BZF * FS + sidx(P, i0 + ti, j0 + tj, ku)] = bz;
+      if (first)
+        sBz[cur][tj * kTX + ti] = face_from<R>(Ub[BZF * FS + so], sEy[cur][tj * SX + ti], sEy[cur][tj * SX + ti + 1],
+                                               sEx[cur][tj * kTX + ti], sEx[cur][(tj + 1) * kTX + ti], ix, iy, h);
+    }
+    if (tj == 0 && ti < nj) {  // x face at the halo column
+      const int jj = ti, i = i0 + ni, j = j0 + jj;
+      const double b = face_from<R>(Ub[BXF * FS + sidx(P, fmap(P, 0, i), j, k)], sEz[jj * SX + ni],
+                                    sEz[(jj + 1) * SX + ni], sEy[cur][jj * SX + ni], sEy[nxt][jj * SX + ni], iy, iz, h);
+      sBx[jj * SX + ni] = b;
+      if (i == P.n[0] && P.nface[0] > P.n[0]) Uo[BXF * FS + sidx(P, i, j, k)] = b;
+    }
+    if (tj == 1 && ti < ni) {  // y face at the halo row
+      const int ii = ti, i = i0 + ii, j = j0 + nj;
+      const double b = face_from<R>(Ub[BYF * FS + sidx(P, i, fmap(P, 1, j), k)], sEx[cur][nj * kTX + ii],
+                                    sEx[nxt][nj * kTX + ii], sEz[nj * SX + ii], sEz[nj * SX + ii + 1], iz, ix, h);
+      sBy[nj * kTX + ii] = b;
+      if (j == P.n[1] && P.nface[1] > P.n[1]) Uo[BYF * FS + sidx(P, i, j, k)] = b;
+    }
+    __syncthreads();
+    // (C) the cell
+    if (own) {
+      const long long s = sk + ti + (long long)tj * PX;
+      const long long q = qidx(P, i0, j0, k) + ti + (long long)tj * QX;
+      double u[5];
+      cell_update<R>(P, Ub, Us, h, a.src, i0 + ti, j0 + tj, k, s, q, u);
+      const double blo[3] = {sBx[tj * SX + ti], sBy[tj * kTX + ti], sBz[cur][tj * kTX + ti]};
+      const double bhi[3] = {sBx[tj * SX + ti + 1], sBy[(tj + 1) * kTX + ti], sBz[nxt][tj * kTX + ti]};
+      if (last && P.floors)
+        nfl += floor_core(P, u[0], u[1], u[2], u[3], u[4], blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2]);
+      Uo[s] = u[0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Uo[(MX + c) * FS + s] = u[1 + c];
+      Uo[EN * FS + s] = u[4];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Uo[(BXF + c) * FS + s] = blo[c];
+      const R l = prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2],
+                               Wout, q, true, true);
+      lim = l < lim ? l : lim;
+    }
+    // C(k) and A(k + 1) touch different shared arrays and share one barrier interval
+  }
+  if (a.stage == 1) {
+    if (P.floors) {
+      const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nfl);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.floored, (unsigned long long)tot);
+    }
+    block_min_atomic(lim, P.cfl_min);
+  }
+}
+
 // W of the ghost shell from the interior W and U of the current state (see ghost_point).
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_ghost(PatchDev P, const double* __restrict__ U) {
@@ -144,6 +312,18 @@ __global__ void k_hlld(int n, const double* __restrict__ wl, const double* __res
 }
 
 // ------------------------------------------------------------- host side ----
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      n = 1;
+  }
+  return n;
+}
 
 static inline dim3 grid_of(const Range& rg) {
   const long long plane = (long long)rg.ext[0] * rg.ext[1];
@@ -194,9 +374,10 @@ static inline Range edge_range(const PatchDev& P) {
   return r;
 }
 
-// per-direction flux kernels and the corner-EMF kernel of one stage
+// per-direction flux kernels of one stage, and the corner-EMF kernel when asked
 template <class R>
-static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s, ProfRec* prof) {
+static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s, ProfRec* prof,
+                        bool emf) {
   int nl = 0;
   for (int d = 0; d < 3; ++d) {
     if (!P.act[d]) continue;
@@ -213,6 +394,7 @@ static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usr
     }
     ++nl;
   }
+  if (!emf) return nl;
   const Range er = edge_range(P);
   ProfScope ps(prof, KC_EMF, s);
   k_emf<R><<<grid_of(er), kBlock, 0, s>>>(P, er);
@@ -224,13 +406,35 @@ static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usr
 // source term is evaluated at U^{n+1/2}, writes U^{n+1} into Uh as well (each cell's
 // U^{n+1/2} is read by the thread that overwrites it, and no kernel of the stage reads the
 // faces of Uh after the fluxes), so the caller swaps Un and Uh after the corrector.
+//
+// Patches with three active axes use the fused EMF + update kernel, which reads the
+// stage's W and writes the new W to the other buffer: the predictor reads W and writes
+// W2, the corrector reads W2 and writes W, so W holds the new state's primitives after
+// every step.  Other patches use the corner-EMF kernel and the fused update, in place.
 template <class R>
 static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, long long* launches,
                        ProfRec* prof) {
   const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
-  int nl = issue_fluxes<R>(P, a, Usrc, s, prof);
-  const Range er = edge_range(P);
-  {
+  const bool fused = P.act[0] && P.act[1] && P.act[2] && P.W2;
+  PatchDev Q = P;  // Q.W: the W the stage reads
+  PatchDev G = P;  // G.W: the W the stage writes
+  if (fused) {
+    Q.W = a.stage == 0 ? P.W : P.W2;
+    G.W = a.stage == 0 ? P.W2 : P.W;
+  }
+  int nl = issue_fluxes<R>(Q, a, Usrc, s, prof, !fused);
+  if (fused) {
+    ProfScope ps(prof, KC_EMF_UPDATE, s);
+    // planes per CTA: 8, halved (down to 2) while the grid would be under two waves of
+    // five resident CTAs per SM
+    const int ntx = (P.n[0] + kTX - 1) / kTX, nty = (P.n[1] + kTY - 1) / kTY;
+    int lz = 8;
+    while (lz > 2 && (long long)ntx * nty * ((P.n[2] + lz - 1) / lz) < 2LL * 5 * sm_count()) lz >>= 1;
+    const dim3 grid((unsigned)(ntx * nty), (unsigned)((P.n[2] + lz - 1) / lz), 1);
+    k_emf_update<R><<<grid, kBlock, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz);
+    ++nl;
+  } else {
+    const Range er = edge_range(P);
     ProfScope ps(prof, KC_UPDATE, s);
     k_update_fused<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, P.Uh, er, a);
     ++nl;
@@ -241,7 +445,7 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     if (ng > 0) {
       long long blocks = (ng + kBlock - 1) / kBlock;
       if (blocks > 65535) blocks = 65535;
-      k_ghost<R><<<(unsigned)blocks, kBlock, 0, s>>>(P, P.Uh);
+      k_ghost<R><<<(unsigned)blocks, kBlock, 0, s>>>(G, P.Uh);
       ++nl;
     }
   }
