@@ -69,10 +69,10 @@ KCLASS = {
 # FP64 pipe operations per clock per SM: the nominal 1.25 TFLOP/s of the part is
 # 152 SMs x 2 FMAs x 2 flops x ~2.06 GHz.  (A DFMA probe measured 1.0 TFLOP/s.)
 FP64_OPS_PER_SM_CLK = 2
-# DRAM bytes (read + write) per point of the fused update, from one ncu capture of this
-# kernel on turbulence 128^3 (554.1 MB per launch over 129^3 points); scaled by the points of
-# a launch.  Retake it when the kernel changes.
-MEASURED_DRAM_BYTES_PER_POINT = {"update": 554.1e6 / 129 ** 3}
+# DRAM bytes (read + write) per item of the dominant kernel, from one ncu capture of the
+# EMF + update kernel on turbulence 192^3 (2.290 GB per launch over 192^3 cells, planes
+# marched as on 256^3); scaled by the items of a launch.  Retake it when the kernel changes.
+MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 2.290e9 / 192 ** 3}
 
 
 def units_per_launch(cls: str, n: int) -> int:
@@ -396,7 +396,7 @@ def run_ours(args, world, rank, local, pg):
     roof = dict(roofs[dom])
     per_point = MEASURED_DRAM_BYTES_PER_POINT.get(dom)
     roof.update({"traffic": per_point * units_per_launch(dom, n) if per_point else None, "kernel": dom,
-                 "traffic_note": "ncu DRAM bytes per point at 128^3, scaled to this launch" if per_point else None})
+                 "traffic_note": "ncu DRAM bytes per cell at 192^3, scaled to this launch" if per_point else None})
     shares = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
 
     # plain FP64 path on the same box
