@@ -155,11 +155,18 @@ int mhd_cfl_dt(mhd_ctx* ctx, double* dt_out);
 /* Per-patch CFL time steps, n_patches values.  Synchronises. */
 int mhd_cfl_dt_patches(mhd_ctx* ctx, double* dt_out);
 
-/* Copy the state of one patch out (host format above; on_device as in init). */
+/* Copy the state of one patch out (host format above; on_device as in init).  A kernel
+ * writes the caller's arrays directly when the device can address them: device memory,
+ * or page-locked host memory mapped into the device's address space (cudaHostAlloc;
+ * pinned PyTorch tensors are), in which case the data cross the host link from the
+ * kernel's stores.  Other host memory is filled from a device staging buffer by one copy
+ * per array.  Synchronises; the arrays are complete on return. */
 int mhd_get_state(mhd_ctx* ctx, int patch, double* U_out, double* Bface_out, int on_device);
 
-/* Replace the state of one patch (same format).  Used for resume and for
- * end-to-end runs that stream each step's input from the host. */
+/* Replace the state of one patch (same format; same direct or staged access as
+ * mhd_get_state).  Used for resume and for end-to-end runs that stream each step's input
+ * from the host.  Asynchronous: the caller keeps the arrays unchanged until the stream
+ * has passed this call (mhd_sync, or any synchronising call). */
 int mhd_set_state(mhd_ctx* ctx, int patch, const double* U, const double* Bface, int on_device);
 
 /* Wait for all issued work and return the device error status. */

@@ -39,16 +39,99 @@ struct PatchHost {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-__global__ void k_pack(PatchDev P, const double* __restrict__ U, double* __restrict__ out, long long total) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x)
-    pack_point(P, U, out, t);
+// The caller's dense layout of a patch: U as 5 fields [nz][ny][nx], then the faces Bx
+// [nz][ny][nx+1], By [nz][ny+1][nx], Bz [nz+1][ny][nx].  Row r of it (a run along x) is
+// field f at (j, k), len values long, starting at off in u (cell fields) or b (faces).
+__device__ __forceinline__ void dense_row(const PatchDev& P, long long r, int& f, int& j, int& k, int& len,
+                                          long long& off) {
+  const long long n0 = P.n[0], n1 = P.n[1], n2 = P.n[2];
+  const long long ru = 5 * n1 * n2;
+  if (r < ru) {
+    f = (int)(r / (n1 * n2));
+    const long long rr = r - f * n1 * n2;
+    k = (int)(rr / n1);
+    j = (int)(rr - k * n1);
+    len = (int)n0;
+    off = r * n0;
+    return;
+  }
+  r -= ru;
+  if (r < n1 * n2) {
+    f = BXF;
+    k = (int)(r / n1);
+    j = (int)(r - k * n1);
+    len = (int)n0 + 1;
+    off = r * (n0 + 1);
+    return;
+  }
+  long long base = n1 * n2 * (n0 + 1);
+  r -= n1 * n2;
+  if (r < (n1 + 1) * n2) {
+    f = BYF;
+    k = (int)(r / (n1 + 1));
+    j = (int)(r - k * (n1 + 1));
+    len = (int)n0;
+    off = base + r * n0;
+    return;
+  }
+  base += (n1 + 1) * n2 * n0;
+  r -= (n1 + 1) * n2;
+  f = BZF;
+  k = (int)(r / n1);
+  j = (int)(r - k * n1);
+  len = (int)n0;
+  off = base + r * n0;
 }
 
-__global__ void k_unpack(PatchDev P, const double* __restrict__ in, double* __restrict__ U, long long total) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x)
-    unpack_point(P, in, U, t);
+long long dense_rows(const PatchDev& P) {
+  const long long n1 = P.n[1], n2 = P.n[2];
+  return 6 * n1 * n2 + (n1 + 1) * n2 + n1 * (n2 + 1);
+}
+
+unsigned grid_rows(long long rows) { return (unsigned)(rows < (1LL << 20) ? (rows < 1 ? 1 : rows) : (1LL << 20)); }
+
+// state -> dense (u, b): one CTA per row; a face's stored index maps the high boundary
+// face of a periodic axis to face 0.  u and b may be device memory or page-locked host
+// memory mapped into the device's address space (the rows then cross the host link
+// straight from the kernel's stores).
+__global__ void k_pack(PatchDev P, const double* __restrict__ U, double* __restrict__ u, double* __restrict__ b,
+                       long long rows) {
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    int f, j, k, len;
+    long long off;
+    dense_row(P, r, f, j, k, len, off);
+    double* dst = (f < 5 ? u : b) + off;
+    const int jj = f == BYF ? fmap(P, 1, j) : j, kk = f == BZF ? fmap(P, 2, k) : k;
+    const double* src = U + f * P.FS + sidx(P, 0, jj, kk);
+    if (f == BXF)
+      for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[fmap(P, 0, i)];
+    else
+      for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
+  }
+}
+
+// dense (u, b) -> state, faces at their raw index
+__global__ void k_unpack(PatchDev P, const double* __restrict__ u, const double* __restrict__ b,
+                         double* __restrict__ U, long long rows) {
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    int f, j, k, len;
+    long long off;
+    dense_row(P, r, f, j, k, len, off);
+    const double* src = (f < 5 ? u : b) + off;
+    double* dst = U + f * P.FS + sidx(P, 0, j, k);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
+  }
+}
+
+// Device address of a page-locked host buffer mapped into the device's address space, or
+// null (pageable or unknown memory).
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // End-of-step floors over the interior cells of one patch; changed cells are counted.
@@ -63,11 +146,6 @@ __global__ void __launch_bounds__(256) k_floor(PatchDev P) {
   }
   const unsigned tot = __reduce_add_sync(0xffffffffu, changed);
   if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.floored, (unsigned long long)tot);
-}
-
-unsigned grid_for(long long n) {
-  long long b = (n + 255) / 256;
-  return (unsigned)(b < 1 ? 1 : (b > 65535LL * 32 ? 65535LL * 32 : b));
 }
 
 }  // namespace
@@ -687,27 +765,53 @@ int mhd_cfl_dt(mhd_ctx* ctx, double* out) {
   return MHD_OK;
 }
 
+// The pack and unpack kernels read and write the caller's arrays directly when the device
+// can address them (device memory, or page-locked mapped host memory); other host memory
+// goes through the staging buffer and one copy per array.
 int mhd_get_state(mhd_ctx* ctx, int patch, double* U_out, double* B_out, int on_device) {
   if (!ctx || patch < 0 || patch >= ctx->np || !U_out || !B_out) return MHD_ERR_ARG;
   PatchHost& H = ctx->P[patch];
-  k_pack<<<grid_for(H.dense), 256, 0, ctx->stream>>>(H.dev, H.dev.Un, ctx->staging, H.dense);
+  double* u = U_out;
+  double* b = B_out;
+  bool staged = false;
+  if (!on_device) {
+    u = (double*)mapped_host(U_out);
+    b = (double*)mapped_host(B_out);
+    if (!u || !b) {
+      u = ctx->staging;
+      b = ctx->staging + 5 * H.ncell;
+      staged = true;
+    }
+  }
+  const long long rows = dense_rows(H.dev);
+  k_pack<<<grid_rows(rows), 256, 0, ctx->stream>>>(H.dev, H.dev.Un, u, b, rows);
   ctx->launches += 1;
   CK(cudaGetLastError());
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  CK(cudaMemcpyAsync(U_out, ctx->staging, sizeof(double) * 5 * H.ncell, kind, ctx->stream));
-  CK(cudaMemcpyAsync(B_out, ctx->staging + 5 * H.ncell, sizeof(double) * (H.dense - 5 * H.ncell), kind,
-                     ctx->stream));
+  if (staged) {
+    CK(cudaMemcpyAsync(U_out, u, sizeof(double) * 5 * H.ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(B_out, b, sizeof(double) * (H.dense - 5 * H.ncell), cudaMemcpyDeviceToHost, ctx->stream));
+  }
   return read_error_word(ctx);
 }
 
 int mhd_set_state(mhd_ctx* ctx, int patch, const double* U, const double* B, int on_device) {
   if (!ctx || patch < 0 || patch >= ctx->np || !U || !B) return MHD_ERR_ARG;
   PatchHost& H = ctx->P[patch];
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(ctx->staging, U, sizeof(double) * 5 * H.ncell, kind, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->staging + 5 * H.ncell, B, sizeof(double) * (H.dense - 5 * H.ncell), kind,
-                     ctx->stream));
-  k_unpack<<<grid_for(H.dense), 256, 0, ctx->stream>>>(H.dev, ctx->staging, H.dev.Un, H.dense);
+  const double* u = U;
+  const double* b = B;
+  if (!on_device) {
+    u = (const double*)mapped_host(U);
+    b = (const double*)mapped_host(B);
+    if (!u || !b) {
+      CK(cudaMemcpyAsync(ctx->staging, U, sizeof(double) * 5 * H.ncell, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->staging + 5 * H.ncell, B, sizeof(double) * (H.dense - 5 * H.ncell),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      u = ctx->staging;
+      b = ctx->staging + 5 * H.ncell;
+    }
+  }
+  const long long rows = dense_rows(H.dev);
+  k_unpack<<<grid_rows(rows), 256, 0, ctx->stream>>>(H.dev, u, b, H.dev.Un, rows);
   ctx->launches += 1;
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
@@ -731,7 +835,9 @@ int mhd_get_metrics(mhd_ctx* ctx, mhd_metrics* m) {
   for (int p = 0; p < ctx->np; ++p) {
     PatchHost& H = ctx->P[p];
     std::vector<double> buf(H.dense);
-    k_pack<<<grid_for(H.dense), 256, 0, ctx->stream>>>(H.dev, H.dev.Un, ctx->staging, H.dense);
+    const long long rows = dense_rows(H.dev);
+    k_pack<<<grid_rows(rows), 256, 0, ctx->stream>>>(H.dev, H.dev.Un, ctx->staging, ctx->staging + 5 * H.ncell,
+                                                     rows);
     ctx->launches += 1;
     CK(cudaMemcpyAsync(buf.data(), ctx->staging, sizeof(double) * H.dense, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));

@@ -891,73 +891,6 @@ __device__ __forceinline__ void ghost_point(const PatchDev& P, const double* __r
   }
 }
 
-// ------------------------------------------------------------ host format ----
-// Pack/unpack between the dense host format (see mhd.h) and the device layout.
-__device__ __forceinline__ void pack_point(const PatchDev& P, const double* __restrict__ U,
-                                           double* __restrict__ out, long long t) {
-  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
-  if (t < 5 * nc) {
-    const int f = (int)(t / nc);
-    long long r = t - f * nc;
-    const int i = (int)(r % P.n[0]);
-    r /= P.n[0];
-    const int j = (int)(r % P.n[1]);
-    const int k = (int)(r / P.n[1]);
-    out[t] = U[f * P.FS + sidx(P, i, j, k)];
-    return;
-  }
-  long long r = t - 5 * nc;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int e[3] = {P.n[0], P.n[1], P.n[2]};
-    e[a] += 1;
-    const long long cnt = (long long)e[0] * e[1] * e[2];
-    if (r < cnt) {
-      int c[3];
-      c[0] = (int)(r % e[0]);
-      long long rr = r / e[0];
-      c[1] = (int)(rr % e[1]);
-      c[2] = (int)(rr / e[1]);
-      c[a] = fmap(P, a, c[a]);
-      out[t] = U[(BXF + a) * P.FS + sidx(P, c[0], c[1], c[2])];
-      return;
-    }
-    r -= cnt;
-  }
-}
-
-__device__ __forceinline__ void unpack_point(const PatchDev& P, const double* __restrict__ in,
-                                             double* __restrict__ U, long long t) {
-  const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
-  if (t < 5 * nc) {
-    const int f = (int)(t / nc);
-    long long r = t - f * nc;
-    const int i = (int)(r % P.n[0]);
-    r /= P.n[0];
-    const int j = (int)(r % P.n[1]);
-    const int k = (int)(r / P.n[1]);
-    U[f * P.FS + sidx(P, i, j, k)] = in[t];
-    return;
-  }
-  long long r = t - 5 * nc;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int e[3] = {P.n[0], P.n[1], P.n[2]};
-    e[a] += 1;
-    const long long cnt = (long long)e[0] * e[1] * e[2];
-    if (r < cnt) {
-      int c[3];
-      c[0] = (int)(r % e[0]);
-      long long rr = r / e[0];
-      c[1] = (int)(rr % e[1]);
-      c[2] = (int)(rr / e[1]);
-      U[(BXF + a) * P.FS + sidx(P, c[0], c[1], c[2])] = in[t];
-      return;
-    }
-    r -= cnt;
-  }
-}
-
 // ordered bits of a non-negative double (monotone as unsigned integers)
 __device__ __forceinline__ unsigned long long dbits(double x) {
   return (unsigned long long)__double_as_longlong(x);
