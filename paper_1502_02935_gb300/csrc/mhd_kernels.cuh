@@ -138,6 +138,39 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
 constexpr int kTX = 32, kTY = 8;
 static_assert(kTX * kTY == kBlock, "one thread per cell of a tile plane");
 
+// Periodic images of the W of interior cell (i, j, k) (scratch index q) in the ghost shell
+// of width 2: every combination of shifts by 0 or +-n per axis that lands in [-2, n + 1],
+// other than no shift.  Used when all three axes are periodic; it replaces the ghost-fill
+// kernel, whose copies it makes.
+template <class R>
+__device__ __forceinline__ void periodic_images(const PatchDev& P, R* __restrict__ W, int i, int j, int k,
+                                                long long q) {
+  const int c[3] = {i, j, k};
+  bool near = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) near |= c[a] < 2 || c[a] >= P.n[a] - 2;
+  if (!near) return;
+  const long long QS = P.QS;
+  R v[NWQ];
+#pragma unroll
+  for (int m = 0; m < NWQ; ++m) v[m] = W[m * QS + q];
+  for (int sz = -1; sz <= 1; ++sz) {
+    const int kk = k + sz * P.n[2];
+    if (kk < -2 || kk > P.n[2] + 1) continue;
+    for (int sy = -1; sy <= 1; ++sy) {
+      const int jj = j + sy * P.n[1];
+      if (jj < -2 || jj > P.n[1] + 1) continue;
+      for (int sx = -1; sx <= 1; ++sx) {
+        const int ii = i + sx * P.n[0];
+        if (ii < -2 || ii > P.n[0] + 1 || (sx == 0 && sy == 0 && sz == 0)) continue;
+        const long long t = qidx(P, ii, jj, kk);
+#pragma unroll
+        for (int m = 0; m < NWQ; ++m) W[m * QS + t] = v[m];
+      }
+    }
+  }
+}
+
 template <class R>
 __device__ __forceinline__ R emf_at(const PatchDev& P, const R* __restrict__ W, int c, int i, int j, int k) {
   const long long q = qidx(P, i, j, k);
@@ -148,7 +181,7 @@ template <class R>
 __global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* __restrict__ Win,
                                                        R* __restrict__ Wout, const double* __restrict__ Ub,
                                                        const double* __restrict__ Us, double* __restrict__ Uo,
-                                                       StageArgs a, int lz) {
+                                                       StageArgs a, int lz, int images) {
   constexpr int SX = kTX + 1;  // row pitch of the arrays with an x halo
   __shared__ R sEz[(kTY + 1) * SX];
   __shared__ R sEx[2][(kTY + 1) * kTX];
@@ -271,6 +304,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* _
       const R l = prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2],
                                Wout, q, true, true);
       lim = l < lim ? l : lim;
+      if (images) periodic_images<R>(P, Wout, i0 + ti, j0 + tj, k, q);
     }
     // C(k) and A(k + 1) touch different shared arrays and share one barrier interval
   }
@@ -416,6 +450,8 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
                        ProfRec* prof) {
   const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
   const bool fused = P.act[0] && P.act[1] && P.act[2] && P.W2;
+  // all axes periodic: the fused kernel writes W's ghost images itself
+  const int images = fused && P.per[0] && P.per[1] && P.per[2];
   PatchDev Q = P;  // Q.W: the W the stage reads
   PatchDev G = P;  // G.W: the W the stage writes
   if (fused) {
@@ -431,7 +467,7 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     int lz = 8;
     while (lz > 2 && (long long)ntx * nty * ((P.n[2] + lz - 1) / lz) < 2LL * 5 * sm_count()) lz >>= 1;
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((P.n[2] + lz - 1) / lz), 1);
-    k_emf_update<R><<<grid, kBlock, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz);
+    k_emf_update<R><<<grid, kBlock, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz, images);
     ++nl;
   } else {
     const Range er = edge_range(P);
@@ -439,7 +475,7 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     k_update_fused<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, P.Uh, er, a);
     ++nl;
   }
-  {
+  if (!images) {
     ProfScope ps(prof, KC_GHOST, s);
     const long long ng = ghost_count(P);
     if (ng > 0) {
