@@ -16,12 +16,25 @@ struct Range {
   int ext[3];
 };
 
+// (32-bit unsigned division when the plane of the box has fewer than 2^31 points, which
+// is every practical size; 64-bit division is a long software sequence)
 __device__ __forceinline__ bool range_point(const Range& rg, int& i, int& j, int& k) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long plane = (long long)rg.ext[0] * rg.ext[1];
-  if (r >= plane) return false;
-  const int jj = (int)(r / rg.ext[0]);
-  i = rg.lo[0] + (int)(r - (long long)jj * rg.ext[0]);
+  int ii, jj;
+  if (plane < (1LL << 31)) {
+    const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (unsigned)plane) return false;
+    const unsigned e0 = (unsigned)rg.ext[0];
+    const unsigned q = r / e0;
+    jj = (int)q;
+    ii = (int)(r - q * e0);
+  } else {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= plane) return false;
+    jj = (int)(r / rg.ext[0]);
+    ii = (int)(r - (long long)jj * rg.ext[0]);
+  }
+  i = rg.lo[0] + ii;
   j = rg.lo[1] + jj;
   k = rg.lo[2] + (int)blockIdx.y;
   return true;
