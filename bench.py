@@ -70,9 +70,9 @@ KCLASS = {
 # 152 SMs x 2 FMAs x 2 flops x ~2.06 GHz.  (A DFMA probe measured 1.0 TFLOP/s.)
 FP64_OPS_PER_SM_CLK = 2
 # DRAM bytes (read + write) per item of the dominant kernel, from one ncu capture of the
-# EMF + update kernel on turbulence 192^3 (2.290 GB per launch over 192^3 cells, planes
+# EMF + update kernel on turbulence 192^3 (2.195 GB per launch over 192^3 cells, planes
 # marched as on 256^3); scaled by the items of a launch.  Retake it when the kernel changes.
-MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 2.290e9 / 192 ** 3}
+MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 2.195e9 / 192 ** 3}
 
 
 def units_per_launch(cls: str, n: int) -> int:
