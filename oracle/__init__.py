@@ -29,7 +29,12 @@ class OrcPatch(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
-                ("bc", C.c_int * 6), ("gamma", C.c_double)]
+                ("bc", C.c_int * 6), ("gamma", C.c_double), ("riemann", C.c_int)]
+
+
+# Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics.  HLLC
+# takes HLLD at faces that carry a field.
+RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
 
 
 class OrcSource(C.Structure):
@@ -67,6 +72,7 @@ def lib():
                                   C.c_double, C.c_double, C.c_int]
             L.orc_run.restype = C.c_int
             L.orc_hlld_batch.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp]
+            L.orc_riemann_batch.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_reconstruct_1d.argtypes = [C.c_int, dp, dp, dp]
             L.orc_diagnostics.argtypes = [C.POINTER(OrcPatch), dp, dp, dp, dp, dp, dp]
             L.orc_set_threads.argtypes = [C.c_int]
@@ -102,8 +108,9 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def patch_struct(g) -> OrcPatch:
+def patch_struct(g, riemann: str = "hlld") -> OrcPatch:
     p = OrcPatch()
+    p.riemann = RIEMANN[riemann]
     p.nx, p.ny, p.nz = g.nx, g.ny, g.nz
     p.x0, p.y0, p.z0 = g.x0, g.y0, g.z0
     p.dx, p.dy, p.dz = g.dx, g.dy, g.dz
@@ -130,13 +137,13 @@ def _copy_state(st):
             np.ascontiguousarray(st.Bz, dtype=np.float64).copy())
 
 
-def step(st, dt: float, source=None, nsteps: int = 1, floored=None):
+def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str = "hlld"):
     """``nsteps`` van Leer steps of fixed size dt; returns a new State.  If ``floored``
     is a list, the per-step counts of cells changed by the end-of-step floors are
-    appended to it."""
+    appended to it.  ``riemann``: "hlld", "hllc" or "hll"."""
     L = lib()
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom), source_struct(source)
+    p, s = patch_struct(st.geom, riemann), source_struct(source)
     for _ in range(nsteps):
         n = L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
         if n < 0:
@@ -152,10 +159,10 @@ def cfl_dt(st, cfl: float, source=None) -> float:
                                   _p(U), _p(Bx), _p(By), _p(Bz), cfl))
 
 
-def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None):
+def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None, riemann: str = "hlld"):
     """Advance to t_end with CFL time steps; returns (State, steps)."""
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom), source_struct(source)
+    p, s = patch_struct(st.geom, riemann), source_struct(source)
     n = lib().orc_run(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(cfl),
                       float(t_end), int(max_steps))
     if n < 0:
@@ -170,6 +177,18 @@ def hlld(wl, wr, bn, gamma: float) -> np.ndarray:
     n = wl.shape[0]
     out = np.zeros((n, 8))
     lib().orc_hlld_batch(n, _p(wl), _p(wr), _p(bn), float(gamma), _p(out))
+    return out
+
+
+def riemann_flux(solver: str, wl, wr, bn, gamma: float) -> np.ndarray:
+    """Fluxes of the solver "hlld", "hllc" or "hll" at a batch of interfaces (same layout
+    as hlld)."""
+    wl = np.ascontiguousarray(np.atleast_2d(wl), dtype=np.float64)
+    wr = np.ascontiguousarray(np.atleast_2d(wr), dtype=np.float64)
+    bn = np.ascontiguousarray(np.atleast_1d(bn), dtype=np.float64)
+    n = wl.shape[0]
+    out = np.zeros((n, 8))
+    lib().orc_riemann_batch(RIEMANN[solver], n, _p(wl), _p(wr), _p(bn), float(gamma), _p(out))
     return out
 
 

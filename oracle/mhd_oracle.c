@@ -44,6 +44,7 @@ typedef struct {
   int act[3];   /* axis active (n > 1) */
   int per[3];   /* periodic (trivial axes count as periodic with n = 1) */
   double d[3], lo[3], gamma;
+  int riemann; /* ORC_RIEMANN_* */
   long tot;
   int floors;                         /* floors on (rho_floor > 0) */
   double rho_floor, pr_floor, pr_ceil; /* pr_ceil = +inf when no ceiling is set */
@@ -81,6 +82,8 @@ static int make_grid(const orc_patch* p, grid* G) {
   }
   if (!(p->gamma > 1.0)) return -1;
   G->gamma = p->gamma;
+  if (p->riemann < ORC_RIEMANN_HLLD || p->riemann > ORC_RIEMANN_HLL) return -1;
+  G->riemann = p->riemann;
   G->floors = 0;
   G->rho_floor = G->pr_floor = 0.0;
   G->pr_ceil = INFINITY;
@@ -345,10 +348,110 @@ static void hlld(const double* wl, const double* wr, double bn, double gam, doub
   flux[5] = sigma;
 }
 
+/* HLL (Harten, Lax & van Leer), one of the two gas-dynamics solvers of Section 2.1: the
+ * single averaged state between the outer waves S_L, S_R (the estimate above; with a field
+ * the fast speeds make it the two-wave MHD solver), from the integral form of the
+ * conservation law over the fan:
+ *   F = F_L (S_L > 0),  F_R (S_R < 0),  else
+ *   F = [S_R F_L - S_L F_R + S_L S_R (U_R - U_L)] / (S_R - S_L). */
+static void hll(const double* wl, const double* wr, double bn, double gam, double* flux) {
+  double UL[8], UR[8], FL[8], FR[8];
+  frame_cons(wl, bn, gam, UL);
+  frame_cons(wr, bn, gam, UR);
+  frame_flux(wl, bn, gam, FL);
+  frame_flux(wr, bn, gam, FR);
+  double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
+  double cfl = fast_speed(rl, wl[4], bn, wl[6], wl[7], gam);
+  double cfr = fast_speed(rr, wr[4], bn, wr[6], wr[7], gam);
+  double cmax = cfl > cfr ? cfl : cfr;
+  double sl = (ul < ur ? ul : ur) - cmax;
+  double sr = (ul > ur ? ul : ur) + cmax;
+  double sigma = (rl > rr ? rl : rr) * (fabs(sl) > fabs(sr) ? fabs(sl) : fabs(sr));
+  if (sl > 0.0) {
+    memcpy(flux, FL, sizeof FL);
+  } else if (sr < 0.0) {
+    memcpy(flux, FR, sizeof FR);
+  } else {
+    for (int m = 0; m < 8; ++m) flux[m] = (sr * FL[m] - sl * FR[m] + sl * sr * (UR[m] - UL[m])) / (sr - sl);
+  }
+  flux[5] = sigma;
+}
+
+/* HLLC (Toro, Spruce & Speares), the other gas-dynamics solver of Section 2.1, for B = 0:
+ * the HLL fan split by the contact S_M into two star states.  In the notation of the HLLD
+ * solver above with every field component zero (M&K Eq. 38, 41, 43, 48):
+ *   S_M = [(S_R - u_R) rho_R u_R - (S_L - u_L) rho_L u_L - p_R + p_L]
+ *         / [(S_R - u_R) rho_R - (S_L - u_L) rho_L],
+ *   p*  = [(S_R - u_R) rho_R p_L - (S_L - u_L) rho_L p_R
+ *          + rho_L rho_R (S_R - u_R)(S_L - u_L)(u_R - u_L)] / (same denominator),
+ *   rho*_a = rho_a (S_a - u_a)/(S_a - S_M), transverse velocities kept,
+ *   E*_a = [(S_a - u_a) E_a - p_a u_a + p* S_M] / (S_a - S_M),
+ *   F = F_L (S_L > 0), F_L + S_L (U*_L - U_L) (S_M >= 0), F_R + S_R (U*_R - U_R)
+ *   (S_R >= 0 > S_M), F_R (S_R < 0). */
+static void hllc(const double* wl, const double* wr, double gam, double* flux) {
+  double UL[8], UR[8], FL[8], FR[8];
+  frame_cons(wl, 0.0, gam, UL);
+  frame_cons(wr, 0.0, gam, UR);
+  frame_flux(wl, 0.0, gam, FL);
+  frame_flux(wr, 0.0, gam, FR);
+  double rl = wl[0], ul = wl[1], pl = wl[4];
+  double rr = wr[0], ur = wr[1], pr = wr[4];
+  double cl = fast_speed(rl, pl, 0.0, 0.0, 0.0, gam);
+  double cr = fast_speed(rr, pr, 0.0, 0.0, 0.0, gam);
+  double cmax = cl > cr ? cl : cr;
+  double sl = (ul < ur ? ul : ur) - cmax;
+  double sr = (ul > ur ? ul : ur) + cmax;
+  double sigma = (rl > rr ? rl : rr) * (fabs(sl) > fabs(sr) ? fabs(sl) : fabs(sr));
+  if (sl > 0.0) {
+    memcpy(flux, FL, sizeof FL);
+    flux[5] = sigma;
+    return;
+  }
+  if (sr < 0.0) {
+    memcpy(flux, FR, sizeof FR);
+    flux[5] = sigma;
+    return;
+  }
+  double dl = sl - ul, dr = sr - ur;
+  double den = dr * rr - dl * rl;
+  double sm = (dr * rr * ur - dl * rl * ul - pr + pl) / den;
+  double pts = (dr * rr * pl - dl * rl * pr + rl * rr * dr * dl * (ur - ul)) / den;
+  const double* w = sm >= 0.0 ? wl : wr;
+  const double* Ua = sm >= 0.0 ? UL : UR;
+  const double* Fa = sm >= 0.0 ? FL : FR;
+  double S = sm >= 0.0 ? sl : sr;
+  double ds = S - w[1];
+  double rs = w[0] * ds / (S - sm);
+  double Us[8] = {rs, rs * sm, rs * w[2], rs * w[3], (ds * Ua[4] - w[4] * w[1] + pts * sm) / (S - sm),
+                  0.0, 0.0, 0.0};
+  for (int m = 0; m < 8; ++m) flux[m] = Fa[m] + S * (Us[m] - Ua[m]);
+  flux[5] = sigma;
+}
+
+/* the solver of the grid at one face; flux[5] is the face's mass-flux scale */
+static void riemann(int solver, const double* wl, const double* wr, double bn, double gam, double* flux) {
+  if (solver == ORC_RIEMANN_HLL) {
+    hll(wl, wr, bn, gam, flux);
+  } else if (solver == ORC_RIEMANN_HLLC && bn == 0.0 && wl[6] == 0.0 && wl[7] == 0.0 && wr[6] == 0.0 &&
+             wr[7] == 0.0) {
+    hllc(wl, wr, gam, flux);
+  } else {
+    hlld(wl, wr, bn, gam, flux);
+  }
+}
+
 void orc_hlld_batch(int n, const double* wl, const double* wr, const double* bn,
                     double gamma, double* flux) {
   for (int q = 0; q < n; ++q) {
     hlld(wl + 8 * q, wr + 8 * q, bn[q], gamma, flux + 8 * q);
+    flux[8 * q + 5] = 0.0;
+  }
+}
+
+void orc_riemann_batch(int solver, int n, const double* wl, const double* wr, const double* bn,
+                       double gamma, double* flux) {
+  for (int q = 0; q < n; ++q) {
+    riemann(solver, wl + 8 * q, wr + 8 * q, bn[q], gamma, flux + 8 * q);
     flux[8 * q + 5] = 0.0;
   }
 }
@@ -444,7 +547,7 @@ static void compute_fluxes(const grid* G, int d, int order, double* const W[NF],
         }
         double bn = U[BXF + d][ixv(G, c)];
         double f[8];
-        hlld(wl, wr, bn, G->gamma, f);
+        riemann(G->riemann, wl, wr, bn, G->gamma, f);
         long o = ixv(G, c);
         Fl[RHO][o] = f[0];
         Fl[MX + d][o] = f[1];

@@ -23,6 +23,10 @@ extern "C" {
 #endif
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1 };
+/* Riemann solver (Section 2.1: HLL or HLLC for pure gas dynamics, HLLD for MHD).
+ * HLLC is the gas-dynamics solver: a face that carries a field (B_n or a transverse
+ * component non-zero on either side) takes HLLD, which is HLLC when B = 0. */
+enum { ORC_RIEMANN_HLLD = 0, ORC_RIEMANN_HLLC = 1, ORC_RIEMANN_HLL = 2 };
 enum { ORC_POT_NONE = 0, ORC_POT_GAUSS_X = 1, ORC_POT_LOG_DISC = 2 };
 
 typedef struct {
@@ -31,6 +35,7 @@ typedef struct {
   double dx, dy, dz;
   int bc[6];           /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
   double gamma;
+  int riemann;         /* ORC_RIEMANN_* (0: HLLD) */
 } orc_patch;
 
 typedef struct {
@@ -66,6 +71,10 @@ int orc_run(const orc_patch* p, const orc_source* s, double* U, double* Bx,
  * field.  flux = [rho, mn, mt1, mt2, E, 0, Bt1, Bt2] fluxes, 8 per interface. */
 void orc_hlld_batch(int n, const double* wl, const double* wr, const double* bn,
                     double gamma, double* flux);
+
+/* The same for the solver ORC_RIEMANN_* (HLLC: HLLD at faces with a field). */
+void orc_riemann_batch(int solver, int n, const double* wl, const double* wr, const double* bn,
+                       double gamma, double* flux);
 
 /* kappa = 1/3 compressive minmod reconstruction on a 1D array of n values:
  * for interfaces m = 2..n-2 (between w[m-1] and w[m]) writes wl[m], wr[m]. */

@@ -235,6 +235,25 @@ def sod(n: int = 200) -> State:
                            0.0, 0.0, 0.0)
 
 
+def sedov(nx: int = 512, ny: int = 768, r0: float = 0.01, e0: float = 1.0, p0: float = 1e-5,
+          gamma: float = 1.4) -> State:
+    """2D Sedov-Taylor blast (Section 3.7) with B = 0 on [-0.5, 0.5] x [-0.75, 0.75] (cells
+    of side 1/512 at the paper's 512 x 768), outflow boundaries: rho = 1, p = p0, and the
+    energy e0 (per unit length) deposited as pressure in the cells whose centres lie within
+    r0 of the centre: p = (gamma - 1) e0 / (their area), so that exactly e0 is added.
+    (The printed in-sphere pressure is garbled; this is the standard point explosion.)"""
+    d = 1.0 / 512.0 * (512.0 / nx)
+    g = Geom(nx, ny, 1, -0.5 * nx * d, -0.5 * ny * d, 0.0, d, d, 1.0, (1, 1, 1, 1, 0, 0), gamma)
+    x, y, _ = g.centres()
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    inside = (X * X + Y * Y < r0 * r0)
+    n_in = int(inside.sum())
+    if n_in == 0:
+        raise ValueError("r0 is smaller than a cell")
+    p = np.where(inside, (gamma - 1.0) * e0 / (n_in * d * d), p0)[None]
+    return state_from_prim(g, 1.0, 0.0, 0.0, 0.0, p, 0.0, 0.0, 0.0)
+
+
 def orszag_tang(nx: int = 512, ny: int | None = None) -> State:
     """2D periodic MHD vortex on [0, 1]^2, gamma = 5/3, rho = 25/(36 pi), p = 5/(12 pi),
     v = (-sin 2 pi y, sin 2 pi x, 0), B = (-sin 2 pi y, sin 4 pi x, 0)/sqrt(4 pi)

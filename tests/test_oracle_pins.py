@@ -142,6 +142,121 @@ def test_hlld_degenerate_states_finite():
     assert np.all(np.isfinite(f2))
 
 
+# ------------------------------------------ HLL and HLLC (Section 2.1) ----
+
+def test_hll_matches_textbook():
+    """HLL, one of the two gas-dynamics solvers of Section 2.1 (two-wave, so also defined
+    with a field), against the HLL flux written independently in tests/textbook.py."""
+    for bmag, gam in ((0.0, 1.4), (1.0, 5.0 / 3.0)):
+        wl, wr = random_w(300, bmag), random_w(300, bmag)
+        bn = RNG.normal(0.0, bmag, 300)
+        f = oracle.riemann_flux("hll", wl, wr, bn, gam)
+        for q in range(300):
+            ref = textbook.hll(wl[q], wr[q], bn[q], gam)
+            ref[5] = 0.0
+            assert np.max(np.abs(f[q] - ref)) <= 1e-12 * (1 + np.max(np.abs(ref))), (bmag, q)
+
+
+def test_hllc_matches_textbook():
+    """HLLC (the oracle writes it in Miyoshi & Kusano's B = 0 notation) against Toro's
+    HLLC in tests/textbook.py: the two arrangements of the star state agree."""
+    gam = 1.4
+    wl, wr = random_w(300, 0.0), random_w(300, 0.0)
+    wl[:, 6:] = 0.0
+    wr[:, 6:] = 0.0
+    f = oracle.riemann_flux("hllc", wl, wr, np.zeros(300), gam)
+    for q in range(300):
+        ref = textbook.hllc(wl[q], wr[q], gam)
+        assert np.max(np.abs(f[q] - ref)) <= 1e-12 * (1 + np.max(np.abs(ref))), q
+
+
+def test_hllc_takes_hlld_at_faces_with_field():
+    """HLLC is the gas-dynamics solver: a face where any field component is non-zero on
+    either side is handed to HLLD, bit for bit."""
+    wl, wr = random_w(200), random_w(200)
+    bn = RNG.normal(0.0, 1.0, 200)
+    # faces with only one component non-zero
+    wl[:50, 6:] = 0.0
+    wr[:50, 6:] = 0.0
+    wl[50:100, 7] = 0.0
+    wr[50:100, 6:] = 0.0
+    bn[50:100] = 0.0
+    assert np.array_equal(oracle.riemann_flux("hllc", wl, wr, bn, 5.0 / 3.0), oracle.hlld(wl, wr, bn, 5.0 / 3.0))
+
+
+@pytest.mark.parametrize("solver", ["hll", "hllc"])
+def test_gas_dynamics_solvers_consistent(solver):
+    """F(U, U) = F(U) for HLL and HLLC (consistency of any Riemann flux)."""
+    w = random_w(200, 0.0 if solver == "hllc" else 1.0)
+    bn = np.zeros(200) if solver == "hllc" else RNG.normal(0.0, 1.0, 200)
+    if solver == "hllc":
+        w[:, 6:] = 0.0
+    got = oracle.riemann_flux(solver, w, w, bn, 1.4)
+    for q in range(200):
+        ref = textbook.physical_flux(w[q], bn[q], 1.4)
+        assert np.max(np.abs(got[q] - ref)) <= 1e-13 * (np.max(np.abs(ref)) + 1.0)
+
+
+def test_sod_with_hll_and_hllc():
+    """Sod tube (Section 3.1) with the two gas-dynamics solvers: the L1 error in rho
+    against the exact solution at t = 0.5 falls with resolution for both.  HLLC, which
+    resolves the contact, stays below HLL at every resolution.  The HLLC run equals the
+    HLLD run to rounding (HLLD is HLLC when B = 0)."""
+    errs = {"hll": [], "hllc": []}
+    for n in (100, 200, 400):
+        st = inputs.sod(n)
+        x = st.geom.centres()[0]
+        ex = textbook.exact_riemann_euler((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, x / 0.5)
+        for solver in errs:
+            out, _ = oracle.run(st, 0.8, 0.5, riemann=solver)
+            errs[solver].append(np.mean(np.abs(out.U[0, 0, 0, :] - ex[0])) * 2.0)
+            if solver == "hllc" and n == 200:
+                ref, _ = oracle.run(st, 0.8, 0.5, riemann="hlld")
+                assert np.max(np.abs(out.U - ref.U)) <= 1e-12 * np.max(np.abs(ref.U))
+    for solver, e in errs.items():
+        assert e[0] > e[1] > e[2], (solver, e)
+    assert all(a < b for a, b in zip(errs["hllc"], errs["hll"])), errs
+
+
+def _shock_radius(st):
+    """Outer half-maximum radius of the angle-averaged density of a centred blast."""
+    g = st.geom
+    x, y, _ = g.centres()
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    r = np.sqrt(X * X + Y * Y).ravel()
+    rho = st.U[0, 0].ravel()
+    nb = int(0.5 / g.dx)
+    idx = np.minimum((r / g.dx).astype(int), nb - 1)
+    prof = np.bincount(idx, weights=rho, minlength=nb) / np.maximum(np.bincount(idx, minlength=nb), 1)
+    rb = (np.arange(nb) + 0.5) * g.dx
+    k = int(np.argmax(prof))
+    half = 0.5 * (prof[k] + 1.0)
+    for m in range(k, nb - 1):
+        if prof[m] >= half > prof[m + 1]:
+            return rb[m] + (prof[m] - half) / (prof[m] - prof[m + 1]) * g.dx
+    raise AssertionError("no shock found")
+
+
+def test_sedov_radius_follows_the_self_similar_law():
+    """2D Sedov-Taylor blast (Section 3.7, B = 0, HLLC): the self-similar solution of a
+    line explosion has R = xi0 (E t^2 / rho)^(1/4), so R grows as t^(1/2).  The exponent
+    fitted over t = 0.02 ... 0.08 is 1/2 within 0.04, and the density stays symmetric
+    under x -> -x and y -> -y to rounding."""
+    st = inputs.sedov(128, 128, r0=0.04)
+    ts, rs = [], []
+    t = 0.0
+    for _ in range(4):
+        st, _ = oracle.run(st, 0.4, 0.02, riemann="hllc")
+        t += 0.02
+        ts.append(t)
+        rs.append(_shock_radius(st))
+    slope = np.polyfit(np.log(ts), np.log(rs), 1)[0]
+    assert abs(slope - 0.5) <= 0.04, (slope, rs)
+    rho = st.U[0, 0]
+    assert np.max(np.abs(rho - rho[:, ::-1])) <= 1e-10 * np.max(rho)
+    assert np.max(np.abs(rho - rho[::-1, :])) <= 1e-10 * np.max(rho)
+
+
 # -------------------------------------------------------- reconstruction ----
 
 def test_reconstruct_linear_exact():

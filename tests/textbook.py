@@ -3,6 +3,8 @@
 * ``physical_flux``: the ideal-MHD flux of Eq. 3 in the frame of an interface.
 * ``hllc``: Toro's HLLC flux for the Euler equations (B = 0) with the same outer
   speed estimates; Miyoshi & Kusano's HLLD reduces to it when B vanishes.
+* ``hll``: the HLL flux (Toro, Sec. 10.3) for the ideal-MHD flux of Eq. 3 with the
+  same outer speed estimates from the fast magnetosonic speed.
 * ``exact_riemann_euler``: Toro's exact Riemann solver for an ideal gas (two-shock /
   two-rarefaction pressure function, Newton iteration on p*), sampled at x/t.
 
@@ -58,6 +60,32 @@ def hllc(wl, wr, gamma):
     if ss >= 0:
         return FL + sl * (ustar(rl, ul, vl, wl_, pl, sl) - conserved(wl, 0.0, gamma))
     return FR + sr * (ustar(rr, ur, vr, wr_, pr, sr) - conserved(wr, 0.0, gamma))
+
+
+def fast_magnetosonic(rho, p, bn, bt1, bt2, gamma):
+    """c_f^2 = (a^2 + b^2)/2 + sqrt((a^2 + b^2)^2 - 4 a^2 b_n^2)/2, a^2 = gamma p/rho,
+    b^2 = |B|^2/rho, b_n^2 = B_n^2/rho."""
+    a2 = gamma * p / rho
+    b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho
+    bn2 = bn * bn / rho
+    return math.sqrt(0.5 * (a2 + b2 + math.sqrt(max((a2 + b2) ** 2 - 4.0 * a2 * bn2, 0.0))))
+
+
+def hll(wl, wr, bn, gamma):
+    """HLL: F_L if S_L >= 0, F_R if S_R <= 0, else the flux of the single intermediate
+    state, (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L), with
+    S_L = min(uL, uR) - max(cfL, cfR), S_R = max(uL, uR) + max(cfL, cfR)."""
+    cl = fast_magnetosonic(wl[0], wl[4], bn, wl[6], wl[7], gamma)
+    cr = fast_magnetosonic(wr[0], wr[4], bn, wr[6], wr[7], gamma)
+    sl = min(wl[1], wr[1]) - max(cl, cr)
+    sr = max(wl[1], wr[1]) + max(cl, cr)
+    FL, FR = physical_flux(wl, bn, gamma), physical_flux(wr, bn, gamma)
+    if sl >= 0:
+        return FL
+    if sr <= 0:
+        return FR
+    UL, UR = conserved(wl, bn, gamma), conserved(wr, bn, gamma)
+    return (sr * FL - sl * FR + sl * sr * (UR - UL)) / (sr - sl)
 
 
 def exact_riemann_euler(left, right, gamma, xi):
