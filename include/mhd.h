@@ -63,6 +63,9 @@ enum {
 };
 
 enum { MHD_POT_NONE = 0, MHD_POT_GAUSS_X = 1, MHD_POT_LOG_DISC = 2 };
+/* Riemann solvers (Section 2.1): HLLD for magneto-gas dynamics (the default); HLLC and
+ * HLL for pure gas dynamics (B = 0). */
+enum { MHD_RIEMANN_HLLD = 0, MHD_RIEMANN_HLLC = 1, MHD_RIEMANN_HLL = 2 };
 
 enum { MHD_THERMAL_OFF = 0, MHD_THERMAL_PLAIN = 1, MHD_THERMAL_SURROGATE = 2 };
 
@@ -138,6 +141,17 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* grid, const double* const*
 
 /* Set the external potential (Eq. 2 source vector) and the floors.  Default: none. */
 int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* src);
+
+/* Interface flux solver of every patch for the following steps (Section 2.1 names HLL and
+ * HLLC for pure gas dynamics and HLLD for magneto-gas dynamics):
+ *   MHD_RIEMANN_HLLD: Miyoshi & Kusano's five-wave solver (default);
+ *   MHD_RIEMANN_HLLC: the three-wave gas-dynamics solver at faces where every field
+ *                     component is zero on both sides, HLLD at the others (HLLD is HLLC
+ *                     when B = 0, so a field-free run only gets cheaper);
+ *   MHD_RIEMANN_HLL:  the two-wave solver with the same outer speeds, at every face.
+ * The outer speed estimate and the mass-flux scale of the corner EMFs are the same for
+ * all three.  MHD_ERR_ARG for another value. */
+int mhd_set_riemann(mhd_ctx* ctx, int solver);
 
 /* Advance every patch by one van Leer step (Eq. 7, Eq. 8).  dt > 0: that dt for
  * every patch.  dt <= 0: each patch uses cfl * its own CFL limit of its current
@@ -266,6 +280,10 @@ void mhd_destroy(mhd_ctx* ctx);
  * 0, Bt1, Bt2].  All four are device pointers; precision MHD_PREC_FP64 computes in
  * FP64, MHD_PREC_MIXED in FP32 (inputs/outputs stay FP64).  stream may be NULL. */
 int mhd_riemann_hlld(int n, const double* wl, const double* wr, const double* bn, double gamma,
+                     int precision, double* flux, void* stream);
+
+/* The same for the solver MHD_RIEMANN_* (MHD_RIEMANN_HLLC: HLLD at faces with a field). */
+int mhd_riemann_flux(int solver, int n, const double* wl, const double* wr, const double* bn, double gamma,
                      int precision, double* flux, void* stream);
 
 /* Unit-level entry for parity tests: the plain FP64 thermal integrator of

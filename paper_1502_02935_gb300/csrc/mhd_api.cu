@@ -632,6 +632,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     D.dt_used = ctx->dt_used + p;
     D.err = ctx->err;
     D.index = p;
+    D.riemann = RIEMANN_HLLD;
     D.floors = 0;
     D.rho_floor = D.pr_floor = 0.0;
     D.pr_ceil = INFINITY;
@@ -702,6 +703,15 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   drop_graph(ctx);  // sources are baked into captured launches
   ctx->w_valid = false;
+  return MHD_OK;
+}
+
+int mhd_set_riemann(mhd_ctx* ctx, int solver) {
+  if (!ctx) return MHD_ERR_ARG;
+  if (solver < MHD_RIEMANN_HLLD || solver > MHD_RIEMANN_HLL) return fail(ctx, MHD_ERR_ARG, "unknown Riemann solver");
+  for (auto& p : ctx->P) p.dev.riemann = solver;
+  if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
+  drop_graph(ctx);  // the solver is part of the captured launches' arguments
   return MHD_OK;
 }
 
@@ -1316,7 +1326,19 @@ int mhd_riemann_hlld(int n, const double* wl, const double* wr, const double* bn
   if (precision != MHD_PREC_FP64 && precision != MHD_PREC_MIXED) return MHD_ERR_ARG;
   Backend be = precision == MHD_PREC_FP64 ? backend_fp64() : backend_mixed();
   cudaStream_t s = (cudaStream_t)stream;
-  if (be.hlld(n, wl, wr, bn, gamma, flux, s)) return MHD_ERR_CUDA;
+  if (be.riemann(MHD_RIEMANN_HLLD, n, wl, wr, bn, gamma, flux, s)) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  return MHD_OK;
+}
+
+int mhd_riemann_flux(int solver, int n, const double* wl, const double* wr, const double* bn, double gamma,
+                     int precision, double* flux, void* stream) {
+  if (solver < MHD_RIEMANN_HLLD || solver > MHD_RIEMANN_HLL) return MHD_ERR_ARG;
+  if (n < 0 || (n > 0 && (!wl || !wr || !bn || !flux)) || !(gamma > 1.0)) return MHD_ERR_ARG;
+  if (precision != MHD_PREC_FP64 && precision != MHD_PREC_MIXED) return MHD_ERR_ARG;
+  Backend be = precision == MHD_PREC_FP64 ? backend_fp64() : backend_mixed();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (be.riemann(solver, n, wl, wr, bn, gamma, flux, s)) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
   return MHD_OK;
 }

@@ -42,8 +42,9 @@ struct Backend {
   int (*prim)(const PatchDev&, cudaStream_t, long long* launches, ProfRec* prof);
   // CFL limit of the current state into the patch's cfl_min slot
   int (*cfl)(const PatchDev&, cudaStream_t, long long* launches);
-  int (*hlld)(int n, const double* wl, const double* wr, const double* bn, double gamma,
-              double* flux, cudaStream_t s);
+  // unit-level Riemann fluxes (solver: 0 HLLD, 1 HLLC, 2 HLL)
+  int (*riemann)(int solver, int n, const double* wl, const double* wr, const double* bn, double gamma,
+                 double* flux, cudaStream_t s);
   // one whole step of every patch in one cooperative launch of `blocks` CTAs
   int (*persistent)(const PersistentArgs&, int blocks, cudaStream_t, long long* launches);
   int (*occupancy)(int block, int* blocks_per_sm);

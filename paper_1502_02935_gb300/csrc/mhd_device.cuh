@@ -28,6 +28,8 @@ enum { WEX = 8, WEY = 9, WEZ = 10, NWQ = 11 };
 enum { NFLUX = 8 };  // rho, mx, my, mz, E, B_t1, B_t2, mass-flux scale
 enum : int { ERR_NONFINITE = 1, ERR_NEGATIVE = 2, ERR_TIMEOUT = 4 };
 enum { POT_NONE = 0, POT_GAUSS_X = 1, POT_LOG_DISC = 2 };
+// Riemann solvers of Section 2.1: HLLD (MHD), HLLC and HLL (pure gas dynamics)
+enum { RIEMANN_HLLD = 0, RIEMANN_HLLC = 1, RIEMANN_HLL = 2 };
 
 struct PatchDev {
   int n[3];      // interior cells per axis
@@ -57,6 +59,7 @@ struct PatchDev {
   int floors;
   double rho_floor, pr_floor, pr_ceil;
   unsigned long long* floored;  // count of cells changed by the end-of-step floors
+  int riemann;                  // RIEMANN_*
 };
 
 struct SourceDev {
@@ -371,6 +374,124 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   f[0] = F0; f[1] = F1; f[2] = F2; f[3] = F3; f[4] = F4; f[5] = F5; f[6] = F6;
 }
 
+// ------------------------------------------------------------ HLL, HLLC ----
+// The two gas-dynamics solvers of Section 2.1, same layout as hlld.
+// HLL (Harten, Lax & van Leer): one averaged state between the outer speeds of the HLLD
+// estimate (fast speeds, so it is also the two-wave MHD solver):
+//   F = [S_R F_L - S_L F_R + S_L S_R (U_R - U_L)] / (S_R - S_L) inside the fan.
+template <class R>
+__device__ __forceinline__ void hll(const R* wl, const R* wr, R bn, R gam, R* f) {
+  const R half = R(0.5);
+  const R igm1 = Ar<R>::rcp(gam - R(1));
+  const R bn2 = bn * bn;
+  const R w[2][7] = {{wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6]},
+                     {wr[0], wr[1], wr[2], wr[3], wr[4], wr[5], wr[6]}};
+  R U[2][7], F[2][7], cf[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const R rho = w[s][0], un = w[s][1], v1 = w[s][2], v2 = w[s][3], p = w[s][4], b1 = w[s][5], b2 = w[s][6];
+    const R bb = bn2 + b1 * b1 + b2 * b2;
+    const R pt = p + half * bb;
+    const R e = p * igm1 + half * rho * (un * un + v1 * v1 + v2 * v2) + half * bb;
+    const R vb = un * bn + v1 * b1 + v2 * b2;
+    U[s][0] = rho;
+    U[s][1] = rho * un;
+    U[s][2] = rho * v1;
+    U[s][3] = rho * v2;
+    U[s][4] = e;
+    U[s][5] = b1;
+    U[s][6] = b2;
+    F[s][0] = rho * un;
+    F[s][1] = rho * un * un + pt - bn2;
+    F[s][2] = rho * un * v1 - bn * b1;
+    F[s][3] = rho * un * v2 - bn * b2;
+    F[s][4] = (e + pt) * un - vb * bn;
+    F[s][5] = b1 * un - bn * v1;
+    F[s][6] = b2 * un - bn * v2;
+    cf[s] = fast_speed<R>(rho, p, bb, bn2, gam);
+  }
+  const R cmax = cf[0] > cf[1] ? cf[0] : cf[1];
+  const R ul = w[0][1], ur = w[1][1];
+  const R sl = (ul < ur ? ul : ur) - cmax;
+  const R sr = (ul > ur ? ul : ur) + cmax;
+  f[7] = (w[0][0] > w[1][0] ? w[0][0] : w[1][0]) *
+         (Ar<R>::abs_(sl) > Ar<R>::abs_(sr) ? Ar<R>::abs_(sl) : Ar<R>::abs_(sr));
+  if (sl > R(0)) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) f[m] = F[0][m];
+  } else if (sr < R(0)) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) f[m] = F[1][m];
+  } else {
+    const R idn = Ar<R>::rcp(sr - sl);
+#pragma unroll
+    for (int m = 0; m < 7; ++m) f[m] = (sr * F[0][m] - sl * F[1][m] + sl * sr * (U[1][m] - U[0][m])) * idn;
+  }
+}
+
+// HLLC (Toro, Spruce & Speares) for a face without field: the HLL fan split at the
+// contact S_M into two star states (HLLD's single-star states with B = 0: Miyoshi & Kusano
+// Eq. 38, 41, 43, 48); transverse velocities are kept across the contact.
+template <class R>
+__device__ __forceinline__ void hllc(const R* wl, const R* wr, R gam, R* f) {
+  const R half = R(0.5);
+  const R igm1 = Ar<R>::rcp(gam - R(1));
+  const R rl = wl[0], ul = wl[1], vl = wl[2], zl = wl[3], pl = wl[4];
+  const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4];
+  const R el = pl * igm1 + half * rl * (ul * ul + vl * vl + zl * zl);
+  const R er = pr * igm1 + half * rr * (ur * ur + vr * vr + zr * zr);
+  const R cl = Ar<R>::sqrt_(gam * pl * Ar<R>::rcp(rl)), cr = Ar<R>::sqrt_(gam * pr * Ar<R>::rcp(rr));
+  const R cmax = cl > cr ? cl : cr;
+  const R sl = (ul < ur ? ul : ur) - cmax;
+  const R sr = (ul > ur ? ul : ur) + cmax;
+  f[5] = R(0);
+  f[6] = R(0);
+  f[7] = (rl > rr ? rl : rr) * (Ar<R>::abs_(sl) > Ar<R>::abs_(sr) ? Ar<R>::abs_(sl) : Ar<R>::abs_(sr));
+  if (sl > R(0) || sr < R(0)) {
+    const bool left = sl > R(0);
+    const R rho = left ? rl : rr, un = left ? ul : ur, v1 = left ? vl : vr, v2 = left ? zl : zr;
+    const R p = left ? pl : pr, e = left ? el : er;
+    f[0] = rho * un;
+    f[1] = rho * un * un + p;
+    f[2] = rho * un * v1;
+    f[3] = rho * un * v2;
+    f[4] = (e + p) * un;
+    return;
+  }
+  const R dl = sl - ul, dr = sr - ur;
+  const R iden = Ar<R>::rcp(dr * rr - dl * rl);
+  const R sm = (dr * rr * ur - dl * rl * ul - pr + pl) * iden;
+  const R pts = (dr * rr * pl - dl * rl * pr + rl * rr * dr * dl * (ur - ul)) * iden;
+  const bool left = sm >= R(0);
+  const R S = left ? sl : sr;
+  const R rho = left ? rl : rr, un = left ? ul : ur, v1 = left ? vl : vr, v2 = left ? zl : zr;
+  const R p = left ? pl : pr, e = left ? el : er;
+  const R ds = S - un;
+  const R ism = Ar<R>::rcp(S - sm);
+  const R rs = rho * ds * ism;
+  const R es = (ds * e - p * un + pts * sm) * ism;
+  // F* = F_a + S_a (U*_a - U_a)
+  f[0] = rho * un + S * (rs - rho);
+  f[1] = rho * un * un + p + S * (rs * sm - rho * un);
+  f[2] = rho * un * v1 + S * (rs - rho) * v1;
+  f[3] = rho * un * v2 + S * (rs - rho) * v2;
+  f[4] = (e + p) * un + S * (es - e);
+}
+
+// the patch's solver at one face; HLLC hands a face that carries a field to HLLD (which
+// is HLLC when B = 0)
+template <class R>
+__device__ __forceinline__ void riemann(int solver, const R* wl, const R* wr, R bn, R gam, R* f) {
+  if (solver == RIEMANN_HLL) {
+    hll<R>(wl, wr, bn, gam, f);
+  } else if (solver == RIEMANN_HLLC && bn == R(0) && wl[5] == R(0) && wl[6] == R(0) && wr[5] == R(0) &&
+             wr[6] == R(0)) {
+    hllc<R>(wl, wr, gam, f);
+  } else {
+    hlld<R>(wl, wr, bn, gam, f);
+  }
+}
+
 // --------------------------------------------------------- reconstruction ----
 // kappa = 1/3 compressive minmod scheme (Eq. 12-14 read in the standard form that is
 // third-order upwind biased): K1 = 1/6, K2 = 1/3, b = 4.
@@ -539,7 +660,7 @@ __device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict
 // (o = -1 left, o = 0 right).  f[0..7]: rho, m_D, m_T1, m_T2, E, B_T1, B_T2 fluxes and the
 // wave-speed scale sigma.
 template <class R, int D, int ORDER, class Get>
-__device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, R* f) {
+__device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, int solver, R* f) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const int comp[7] = {WR, WVX + D, WVX + T1, WVX + T2, WP, WBX + T1, WBX + T2};
   R wl[7], wr[7];
@@ -560,7 +681,7 @@ __device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, R* f) {
       }
     }
   }
-  hlld<R>(wl, wr, bn, gam, f);
+  riemann<R>(solver, wl, wr, bn, gam, f);
 }
 
 // normal field at D-face (i, j, k) from the state's face values
@@ -577,12 +698,12 @@ __device__ __forceinline__ R face_bn(const PatchDev& P, const double* __restrict
 template <class R, int D, int ORDER>
 __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restrict__ W,
                                            const double* __restrict__ Ub, R* __restrict__ F,
-                                           int i, int j, int k) {
+                                           int i, int j, int k, int solver) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long q = qidx(P, i, j, k), QS = P.QS, st = qstride(P, D);
   R f[8];
   flux_core<R, D, ORDER>([&](int m, int o) { return W[m * QS + q + o * st]; }, face_bn<R, D>(P, Ub, i, j, k),
-                         Gam<R>::get(P), f);
+                         Gam<R>::get(P), solver, f);
   F[q] = f[0];
   F[(1 + D) * QS + q] = f[1];
   F[(1 + T1) * QS + q] = f[2];

@@ -77,12 +77,14 @@ __global__ void __launch_bounds__(kBlock) k_prim(PatchDev P, const double* __res
   if (want_cfl) block_min_atomic(lim, P.cfl_min);
 }
 
-template <class R, int D, int ORDER>
+// one direction's fluxes with the Riemann solver S (RIEMANN_*) fixed at compile time
+template <class R, int D, int ORDER, int S>
 __global__ void __launch_bounds__(kBlock) k_flux(PatchDev P, const double* __restrict__ Ub, Range rg) {
   int i, j, k;
   if (!range_point(rg, i, j, k)) return;
-  flux_point<R, D, ORDER>(P, (const R*)P.W, Ub, (R*)P.F[D], i, j, k);
+  flux_point<R, D, ORDER>(P, (const R*)P.W, Ub, (R*)P.F[D], i, j, k, S);
 }
+
 
 // corner EMFs: memory-latency bound; eight resident blocks per SM (measured)
 template <class R>
@@ -341,8 +343,8 @@ __global__ void __launch_bounds__(kBlock) k_ghost(PatchDev P, const double* __re
 }
 
 template <class R>
-__global__ void k_hlld(int n, const double* __restrict__ wl, const double* __restrict__ wr,
-                       const double* __restrict__ bn, double gam, double* __restrict__ flux) {
+__global__ void k_riemann(int solver, int n, const double* __restrict__ wl, const double* __restrict__ wr,
+                          const double* __restrict__ bn, double gam, double* __restrict__ flux) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   R a[7], b[7], f[8];
@@ -352,7 +354,7 @@ __global__ void k_hlld(int n, const double* __restrict__ wl, const double* __res
     a[m] = (R)wl[8 * q + src[m]];
     b[m] = (R)wr[8 * q + src[m]];
   }
-  hlld<R>(a, b, (R)bn[q], (R)gam, f);
+  riemann<R>(solver, a, b, (R)bn[q], (R)gam, f);
 #pragma unroll
   for (int m = 0; m < 7; ++m) flux[8 * q + src[m]] = (double)f[m];
   flux[8 * q + 5] = 0.0;
@@ -421,6 +423,15 @@ static inline Range edge_range(const PatchDev& P) {
   return r;
 }
 
+// one direction's flux kernel for the patch's Riemann solver
+template <class R, int D, int ORDER>
+static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cudaStream_t s) {
+  const dim3 g = grid_of(fr);
+  if (P.riemann == RIEMANN_HLLC) k_flux<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr);
+  else if (P.riemann == RIEMANN_HLL) k_flux<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr);
+  else k_flux<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr);
+}
+
 // per-direction flux kernels of one stage, and the corner-EMF kernel when asked
 template <class R>
 static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s, ProfRec* prof,
@@ -431,13 +442,13 @@ static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usr
     const Range fr = flux_range(P, d);
     ProfScope ps(prof, (a.stage == 0 ? KC_FLUX1 : KC_FLUX2) + d, s);
     if (a.stage == 0) {
-      if (d == 0) k_flux<R, 0, 1><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
-      if (d == 1) k_flux<R, 1, 1><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
-      if (d == 2) k_flux<R, 2, 1><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+      if (d == 0) launch_flux<R, 0, 1>(P, Usrc, fr, s);
+      if (d == 1) launch_flux<R, 1, 1>(P, Usrc, fr, s);
+      if (d == 2) launch_flux<R, 2, 1>(P, Usrc, fr, s);
     } else {
-      if (d == 0) k_flux<R, 0, 2><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
-      if (d == 1) k_flux<R, 1, 2><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
-      if (d == 2) k_flux<R, 2, 2><<<grid_of(fr), kBlock, 0, s>>>(P, Usrc, fr);
+      if (d == 0) launch_flux<R, 0, 2>(P, Usrc, fr, s);
+      if (d == 1) launch_flux<R, 1, 2>(P, Usrc, fr, s);
+      if (d == 2) launch_flux<R, 2, 2>(P, Usrc, fr, s);
     }
     ++nl;
   }
@@ -523,10 +534,10 @@ static int issue_cfl(const PatchDev& P, cudaStream_t s, long long* launches) {
 }
 
 template <class R>
-static int issue_hlld(int n, const double* wl, const double* wr, const double* bn, double gam,
-                      double* flux, cudaStream_t s) {
+static int issue_riemann(int solver, int n, const double* wl, const double* wr, const double* bn, double gam,
+                         double* flux, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_hlld<R><<<(n + 127) / 128, 128, 0, s>>>(n, wl, wr, bn, gam, flux);
+  k_riemann<R><<<(n + 127) / 128, 128, 0, s>>>(solver, n, wl, wr, bn, gam, flux);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -536,7 +547,7 @@ template <class R> Backend make_backend() {
   b.stage = &issue_stage<R>;
   b.prim = &issue_prim<R>;
   b.cfl = &issue_cfl<R>;
-  b.hlld = &issue_hlld<R>;
+  b.riemann = &issue_riemann<R>;
   b.persistent = &issue_persistent<R>;
   b.occupancy = &persistent_occupancy<R>;
   return b;

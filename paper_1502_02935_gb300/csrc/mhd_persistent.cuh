@@ -167,13 +167,13 @@ __device__ __forceinline__ void persistent_phase(const PersistentArgs& A, int st
       if (in) {
         const int d = bi - BOX_FLUX0;
         if (stage == 0) {
-          if (d == 0) flux_point<R, 0, 1>(sP, (const R*)sP.W, Usrc, (R*)sP.F[0], i, j, k);
-          else if (d == 1) flux_point<R, 1, 1>(sP, (const R*)sP.W, Usrc, (R*)sP.F[1], i, j, k);
-          else flux_point<R, 2, 1>(sP, (const R*)sP.W, Usrc, (R*)sP.F[2], i, j, k);
+          if (d == 0) flux_point<R, 0, 1>(sP, (const R*)sP.W, Usrc, (R*)sP.F[0], i, j, k, sP.riemann);
+          else if (d == 1) flux_point<R, 1, 1>(sP, (const R*)sP.W, Usrc, (R*)sP.F[1], i, j, k, sP.riemann);
+          else flux_point<R, 2, 1>(sP, (const R*)sP.W, Usrc, (R*)sP.F[2], i, j, k, sP.riemann);
         } else {
-          if (d == 0) flux_point<R, 0, 2>(sP, (const R*)sP.W, Usrc, (R*)sP.F[0], i, j, k);
-          else if (d == 1) flux_point<R, 1, 2>(sP, (const R*)sP.W, Usrc, (R*)sP.F[1], i, j, k);
-          else flux_point<R, 2, 2>(sP, (const R*)sP.W, Usrc, (R*)sP.F[2], i, j, k);
+          if (d == 0) flux_point<R, 0, 2>(sP, (const R*)sP.W, Usrc, (R*)sP.F[0], i, j, k, sP.riemann);
+          else if (d == 1) flux_point<R, 1, 2>(sP, (const R*)sP.W, Usrc, (R*)sP.F[1], i, j, k, sP.riemann);
+          else flux_point<R, 2, 2>(sP, (const R*)sP.W, Usrc, (R*)sP.F[2], i, j, k, sP.riemann);
         }
       }
     } else if (PH == PH_EMF) {

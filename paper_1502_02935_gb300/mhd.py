@@ -71,7 +71,10 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_cfl_dt_noalloc", "mhd_autotune", "mhd_set_wait_limit", "mhd_set_thermal",
            "mhd_thermal_stats", "mhd_thermal_cells", "mhd_surrogate_harvest", "mhd_surrogate_train",
            "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
-           "mhd_mlp_forward_tc"]
+           "mhd_mlp_forward_tc", "mhd_set_riemann", "mhd_riemann_flux"]
+
+# Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics
+RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
 
 
 def lib():
@@ -100,6 +103,8 @@ def lib():
     L.mhd_destroy.argtypes = [vp]
     L.mhd_destroy.restype = None
     L.mhd_riemann_hlld.argtypes = [ip, vp, vp, vp, C.c_double, ip, vp, vp]
+    L.mhd_riemann_flux.argtypes = [ip, ip, vp, vp, vp, C.c_double, ip, vp, vp]
+    L.mhd_set_riemann.argtypes = [vp, ip]
     L.mhd_set_profiling.argtypes = [vp, ip]
     L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
     L.mhd_cfl_dt_noalloc.argtypes = [C.POINTER(PatchDesc), C.c_double, vp, vp, vp, vp]
@@ -174,6 +179,10 @@ class Grid:
                     pr_floor=0.0, pr_ceil=0.0):
         s = SourceDesc(int(potential), psi0, xc, xw, v0, rc, rho_floor, pr_floor, pr_ceil)
         self._check(self.L.mhd_set_sources(self.h, C.byref(s)), "mhd_set_sources")
+
+    def set_riemann(self, solver: str):
+        """"hlld" (default), "hllc" or "hll" for the following steps."""
+        self._check(self.L.mhd_set_riemann(self.h, RIEMANN[solver]), "mhd_set_riemann")
 
     def step(self, dt: float = -1.0):
         self._check(self.L.mhd_step(self.h, float(dt)), "mhd_step")
@@ -309,6 +318,23 @@ def riemann_hlld(wl, wr, bn, gamma: float, precision="fp64") -> np.ndarray:
                                 _prec(precision), out.data_ptr(), stream)
     if rc != 0:
         raise MHDError(rc, "mhd_riemann_hlld")
+    return out.cpu().numpy()
+
+
+def riemann_flux(solver: str, wl, wr, bn, gamma: float, precision="fp64") -> np.ndarray:
+    """Fluxes of the solver "hlld", "hllc" or "hll" at n interfaces, on the GPU (see
+    mhd_riemann_flux)."""
+    import torch
+    wl = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(wl), dtype=np.float64)).cuda()
+    wr = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(wr), dtype=np.float64)).cuda()
+    bn = torch.as_tensor(np.ascontiguousarray(np.atleast_1d(bn), dtype=np.float64)).cuda()
+    n = wl.shape[0]
+    out = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib().mhd_riemann_flux(RIEMANN[solver], n, wl.data_ptr(), wr.data_ptr(), bn.data_ptr(), float(gamma),
+                                _prec(precision), out.data_ptr(), stream)
+    if rc != 0:
+        raise MHDError(rc, "mhd_riemann_flux")
     return out.cpu().numpy()
 
 
