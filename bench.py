@@ -474,10 +474,12 @@ def run_table(args):
     ncores = os.cpu_count() or 1
     stream = torch.cuda.Stream()
 
-    def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None):
+    def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None, riemann=None):
         sts = states if isinstance(states, list) else [states]
         g = mhd.Grid(sts if len(sts) > 1 else sts[0], precision=precision, cfl=CFL, flags=flags,
                      stream=stream.cuda_stream)
+        if riemann:
+            g.set_riemann(riemann)
         if src:
             g.set_sources(**src)
         if thermal:
@@ -526,61 +528,99 @@ def run_table(args):
         return {k: v for k, v in res.items() if np.isfinite(v)}
 
     table = {}
-    # C1: 1D shock tube, plain FP64 only
-    st = inputs.brio_wu(800)
-    oracle.set_threads(ncores)
-    ref, nref = oracle.run(st, 0.8, 0.1)
-    t0 = time.perf_counter()
-    got, n = gpu_to_time(st, "fp64", 0.8, 0.1)
-    el = time.perf_counter() - t0
-    r1, _ = oracle_rate(st, 1, 50, cfl=0.8)
-    rn, _ = oracle_rate(st, ncores, 50, cfl=0.8)
-    table["C1 Brio-Wu 800, FP64, t=0.1"] = {
-        "gpu_fp64": 800 * n / el, "gpu_note": f"{n} steps with a host CFL query each (latency-bound)",
-        "oracle_1core": r1, "oracle_all": rn, "steps": n, "oracle_steps": nref, "l1_fp64_vs_oracle": l1(got, ref)}
-    # C2: 2D vortex 512^2, FP64 and mixed, to t = 0.5
-    st = inputs.orszag_tang(512, 512)
-    oracle.set_threads(ncores)
-    t0 = time.perf_counter()
-    ref, nref = oracle.run(st, CFL, 0.5)
-    el_ref = time.perf_counter() - t0
-    g64, _ = gpu_to_time(st, "fp64", CFL, 0.5)
-    gmx, _ = gpu_to_time(st, "mixed", CFL, 0.5)
-    r1, _ = oracle_rate(st, 1, 10)
-    table["C2 Orszag-Tang 512^2, t=0.5"] = {
-        "gpu_fp64": gpu_rate(st, "fp64", 200), "gpu_mixed": gpu_rate(st, "mixed", 200),
-        "oracle_1core": r1, "oracle_all": 512 * 512 * nref / el_ref, "oracle_steps": nref,
-        "l1_fp64_vs_oracle": l1(g64, ref), "l1_mixed_vs_oracle": l1(gmx, ref)}
-    # C3: turbulence 256^3
-    st = inputs.turbulence(256, seed=SEED)
-    mixed = gpu_rate(st, "mixed", 20)
-    r1, _ = oracle_rate(inputs.turbulence(64, seed=SEED), 1, 5)
-    rn, _ = oracle_rate(st, ncores, 2)
-    table["C3 turbulence 256^3"] = {
-        "gpu_fp64": gpu_rate(st, "fp64", 5), "gpu_mixed": mixed, "hbm_alg_frac_mixed": mixed * 128 / (hbm_peak * 1e9),
-        "oracle_1core": r1, "oracle_1core_sample": "64^3 box, 5 steps", "oracle_all": rn,
-        "oracle_all_sample": "256^3 box, 2 steps"}
-    # C4: 64 blast patches
-    sts = inputs.blast_batch(64, seed=SEED)
-    r1, _ = oracle_rate(sts[:4], 1, 1)
-    rn, _ = oracle_rate(sts, ncores, 1)
-    table["C4 64 blast patches"] = {
-        "gpu_fp64_per_phase": gpu_rate(sts, "fp64", 3),
-        "gpu_mixed_per_phase": gpu_rate(sts, "mixed", 10),
-        "gpu_mixed_persistent": gpu_rate(sts, "mixed", 10, flags=mhd.FLAG_GRAPH | mhd.FLAG_PERSISTENT),
-        "oracle_1core": r1, "oracle_1core_sample": "first 4 patches, 1 step", "oracle_all": rn,
-        "oracle_all_sample": "all 64 patches, 1 step"}
-    # C5: disc with the plain thermal integrator (surrogate figures: the default bench run)
-    th = inputs.DISC_THERMAL
-    src = dict(inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
-    st = inputs.disc(512, 512, 128)
-    r1, _ = oracle_rate(inputs.disc(128, 128, 32), 1, 2, src=src, thermal=th)
-    rn, _ = oracle_rate(st, ncores, 1, src=src, thermal=th)
-    table["C5 disc 512x512x128, plain thermal"] = {
-        "gpu_fp64": gpu_rate(st, "fp64", 3, src=src, thermal=th),
-        "gpu_mixed": gpu_rate(st, "mixed", 10, src=src, thermal=th),
-        "oracle_1core": r1, "oracle_1core_sample": "128x128x32 disc, 2 steps", "oracle_all": rn,
-        "oracle_all_sample": "512x512x128 disc, 1 step"}
+    rows = [r for r in (args.rows or "").split(",") if r]
+
+    def want(key):
+        return not rows or key in rows
+
+    if want("C1"):
+        # C1: 1D shock tube, plain FP64 only
+        st = inputs.brio_wu(800)
+        oracle.set_threads(ncores)
+        ref, nref = oracle.run(st, 0.8, 0.1)
+        t0 = time.perf_counter()
+        got, n = gpu_to_time(st, "fp64", 0.8, 0.1)
+        el = time.perf_counter() - t0
+        r1, _ = oracle_rate(st, 1, 50, cfl=0.8)
+        rn, _ = oracle_rate(st, ncores, 50, cfl=0.8)
+        table["C1 Brio-Wu 800, FP64, t=0.1"] = {
+            "gpu_fp64": 800 * n / el, "gpu_note": f"{n} steps with a host CFL query each (latency-bound)",
+            "oracle_1core": r1, "oracle_all": rn, "steps": n, "oracle_steps": nref, "l1_fp64_vs_oracle": l1(got, ref)}
+    if want("C2"):
+        # C2: 2D vortex 512^2, FP64 and mixed, to t = 0.5
+        st = inputs.orszag_tang(512, 512)
+        oracle.set_threads(ncores)
+        t0 = time.perf_counter()
+        ref, nref = oracle.run(st, CFL, 0.5)
+        el_ref = time.perf_counter() - t0
+        g64, _ = gpu_to_time(st, "fp64", CFL, 0.5)
+        gmx, _ = gpu_to_time(st, "mixed", CFL, 0.5)
+        r1, _ = oracle_rate(st, 1, 10)
+        table["C2 Orszag-Tang 512^2, t=0.5"] = {
+            "gpu_fp64": gpu_rate(st, "fp64", 200), "gpu_mixed": gpu_rate(st, "mixed", 200),
+            "oracle_1core": r1, "oracle_all": 512 * 512 * nref / el_ref, "oracle_steps": nref,
+            "l1_fp64_vs_oracle": l1(g64, ref), "l1_mixed_vs_oracle": l1(gmx, ref)}
+    if want("C3"):
+        # C3: turbulence 256^3
+        st = inputs.turbulence(256, seed=SEED)
+        mixed = gpu_rate(st, "mixed", 20)
+        r1, _ = oracle_rate(inputs.turbulence(64, seed=SEED), 1, 5)
+        rn, _ = oracle_rate(st, ncores, 2)
+        table["C3 turbulence 256^3"] = {
+            "gpu_fp64": gpu_rate(st, "fp64", 5), "gpu_mixed": mixed, "hbm_alg_frac_mixed": mixed * 128 / (hbm_peak * 1e9),
+            "oracle_1core": r1, "oracle_1core_sample": "64^3 box, 5 steps", "oracle_all": rn,
+            "oracle_all_sample": "256^3 box, 2 steps"}
+    if want("C4"):
+        # C4: 64 blast patches
+        sts = inputs.blast_batch(64, seed=SEED)
+        r1, _ = oracle_rate(sts[:4], 1, 1)
+        rn, _ = oracle_rate(sts, ncores, 1)
+        table["C4 64 blast patches"] = {
+            "gpu_fp64_per_phase": gpu_rate(sts, "fp64", 3),
+            "gpu_mixed_per_phase": gpu_rate(sts, "mixed", 10),
+            "gpu_mixed_persistent": gpu_rate(sts, "mixed", 10, flags=mhd.FLAG_GRAPH | mhd.FLAG_PERSISTENT),
+            "oracle_1core": r1, "oracle_1core_sample": "first 4 patches, 1 step", "oracle_all": rn,
+            "oracle_all_sample": "all 64 patches, 1 step"}
+    if want("C5"):
+        # C5: disc with the plain thermal integrator (surrogate figures: the default bench run)
+        th = inputs.DISC_THERMAL
+        src = dict(inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+        st = inputs.disc(512, 512, 128)
+        r1, _ = oracle_rate(inputs.disc(128, 128, 32), 1, 2, src=src, thermal=th)
+        rn, _ = oracle_rate(st, ncores, 1, src=src, thermal=th)
+        table["C5 disc 512x512x128, plain thermal"] = {
+            "gpu_fp64": gpu_rate(st, "fp64", 3, src=src, thermal=th),
+            "gpu_mixed": gpu_rate(st, "mixed", 10, src=src, thermal=th),
+            "oracle_1core": r1, "oracle_1core_sample": "128x128x32 disc, 2 steps", "oracle_all": rn,
+            "oracle_all_sample": "512x512x128 disc, 1 step"}
+    if want("gas"):
+        # pure gas dynamics (B = 0) with the solvers of Section 2.1: the 2D Sedov blast at the
+        # paper's 512 x 768, and the 256^3 turbulent box without its field
+        st, fl = inputs.sedov(512, 768), inputs.SEDOV_FLOORS
+        oracle.set_threads(1)
+        ref, ndone, el = st, 0, 0.0
+        got_g = mhd.Grid(st, precision="mixed", cfl=CFL, stream=stream.cuda_stream)
+        got_g.set_riemann("hllc")
+        got_g.set_sources(**fl)
+        for _ in range(20):
+            dt = oracle.cfl_dt(ref, CFL, source=fl)
+            got_g.step(dt)
+            t0 = time.perf_counter()
+            ref = oracle.step(ref, dt, source=fl, riemann="hllc")
+            el += time.perf_counter() - t0
+            ndone += 1
+        got = got_g.get_state(0)
+        got_g.close()
+        sedov = {"gpu_mixed_" + s_: gpu_rate(st, "mixed", 50, src=fl, riemann=s_) for s_ in ("hllc", "hll", "hlld")}
+        sedov["gpu_fp64_hllc"] = gpu_rate(st, "fp64", 20, src=fl, riemann="hllc")
+        sedov.update({"oracle_1core_hllc": st.geom.ncell * ndone / el,
+                      "oracle_1core_sample": f"512x768, {ndone} steps (one plane: the oracle's loop over z has no parallel work)",
+                      "l1_mixed_hllc_vs_oracle": l1(got, ref), "l1_steps": ndone,
+                      "floors": "rho >= 1e-8, p/rho >= 1e-6 (without them the plain scheme reaches p < 0 at step 7)"})
+        table["Sedov 2D 512x768, B = 0 (HLLC / HLL / HLLD)"] = sedov
+        st = inputs.turbulence(256, seed=SEED, b0=0.0)
+        table["turbulence 256^3, B = 0 (HLLC / HLL / HLLD)"] = {
+            "gpu_mixed_" + s_: gpu_rate(st, "mixed", 10, riemann=s_) for s_ in ("hllc", "hll", "hlld")}
     print(json.dumps({"table": table, "host_cores": ncores, "unit": "zone-updates/s"}), flush=True)
     return 0
 
@@ -600,6 +640,8 @@ def main():
                     help="disc workload: plain (harvest) steps, then surrogate steps")
     ap.add_argument("--table", action="store_true",
                     help="every workload configuration, GPU and oracle side by side (minutes; no bench line)")
+    ap.add_argument("--rows", default="",
+                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas (default all)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.table:
