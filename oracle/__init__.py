@@ -29,12 +29,15 @@ class OrcPatch(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
-                ("bc", C.c_int * 6), ("gamma", C.c_double), ("riemann", C.c_int)]
+                ("bc", C.c_int * 6), ("gamma", C.c_double), ("riemann", C.c_int), ("recon", C.c_int)]
 
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics.  HLLC
 # takes HLLD at faces that carry a field.
 RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
+# Reconstructions of Eq. 12-14: kappa = 1/3 (default), 0, -1 in the standard arrangement, and
+# kappa = 1/3 in the printed arrangement (oracle only: a cross-check of that reading).
+RECON = {"kappa_third": 0, "kappa_zero": 1, "kappa_upwind": 2, "printed": 3}
 
 
 class OrcSource(C.Structure):
@@ -74,6 +77,7 @@ def lib():
             L.orc_hlld_batch.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_riemann_batch.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_reconstruct_1d.argtypes = [C.c_int, dp, dp, dp]
+            L.orc_reconstruct_1d_ex.argtypes = [C.c_int, C.c_int, dp, dp, dp]
             L.orc_diagnostics.argtypes = [C.POINTER(OrcPatch), dp, dp, dp, dp, dp, dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_set_threads.restype = C.c_int
@@ -108,9 +112,10 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def patch_struct(g, riemann: str = "hlld") -> OrcPatch:
+def patch_struct(g, riemann: str = "hlld", recon: str = "kappa_third") -> OrcPatch:
     p = OrcPatch()
     p.riemann = RIEMANN[riemann]
+    p.recon = RECON[recon]
     p.nx, p.ny, p.nz = g.nx, g.ny, g.nz
     p.x0, p.y0, p.z0 = g.x0, g.y0, g.z0
     p.dx, p.dy, p.dz = g.dx, g.dy, g.dz
@@ -137,13 +142,14 @@ def _copy_state(st):
             np.ascontiguousarray(st.Bz, dtype=np.float64).copy())
 
 
-def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str = "hlld"):
+def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str = "hlld",
+         recon: str = "kappa_third"):
     """``nsteps`` van Leer steps of fixed size dt; returns a new State.  If ``floored``
     is a list, the per-step counts of cells changed by the end-of-step floors are
-    appended to it.  ``riemann``: "hlld", "hllc" or "hll"."""
+    appended to it.  ``riemann``: "hlld", "hllc" or "hll"; ``recon``: a key of RECON."""
     L = lib()
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom, riemann), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon), source_struct(source)
     for _ in range(nsteps):
         n = L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
         if n < 0:
@@ -159,10 +165,11 @@ def cfl_dt(st, cfl: float, source=None) -> float:
                                   _p(U), _p(Bx), _p(By), _p(Bz), cfl))
 
 
-def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None, riemann: str = "hlld"):
+def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None, riemann: str = "hlld",
+        recon: str = "kappa_third"):
     """Advance to t_end with CFL time steps; returns (State, steps)."""
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom, riemann), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon), source_struct(source)
     n = lib().orc_run(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(cfl),
                       float(t_end), int(max_steps))
     if n < 0:
@@ -192,11 +199,11 @@ def riemann_flux(solver: str, wl, wr, bn, gamma: float) -> np.ndarray:
     return out
 
 
-def reconstruct_1d(w):
+def reconstruct_1d(w, recon: str = "kappa_third"):
     w = np.ascontiguousarray(w, dtype=np.float64)
     wl = np.full_like(w, np.nan)
     wr = np.full_like(w, np.nan)
-    lib().orc_reconstruct_1d(w.size, _p(w), _p(wl), _p(wr))
+    lib().orc_reconstruct_1d_ex(RECON[recon], w.size, _p(w), _p(wl), _p(wr))
     return wl, wr
 
 

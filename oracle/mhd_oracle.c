@@ -45,6 +45,7 @@ typedef struct {
   int per[3];   /* periodic (trivial axes count as periodic with n = 1) */
   double d[3], lo[3], gamma;
   int riemann; /* ORC_RIEMANN_* */
+  int recon;   /* ORC_RECON_* */
   long tot;
   int floors;                         /* floors on (rho_floor > 0) */
   double rho_floor, pr_floor, pr_ceil; /* pr_ceil = +inf when no ceiling is set */
@@ -84,6 +85,8 @@ static int make_grid(const orc_patch* p, grid* G) {
   G->gamma = p->gamma;
   if (p->riemann < ORC_RIEMANN_HLLD || p->riemann > ORC_RIEMANN_HLL) return -1;
   G->riemann = p->riemann;
+  if (p->recon < ORC_RECON_KAPPA_THIRD || p->recon > ORC_RECON_PRINTED) return -1;
+  G->recon = p->recon;
   G->floors = 0;
   G->rho_floor = G->pr_floor = 0.0;
   G->pr_ceil = INFINITY;
@@ -465,26 +468,41 @@ void orc_riemann_batch(int solver, int n, const double* wl, const double* wr, co
  *   w_L(i+1/2) = w_i     + K1 minmod(dw_{i-1}, b dw_i) + K2 minmod(dw_i, b dw_{i-1})
  *   w_R(i+1/2) = w_{i+1} - K1 minmod(dw_{i+1}, b dw_i) - K2 minmod(dw_i, b dw_{i+1})
  * with dw_i = w_{i+1} - w_i. */
-static const double KAPPA = 1.0 / 3.0;
-
 static double minmod(double a, double b) {
   double s = a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0);
   double m = fabs(a) < s * b ? fabs(a) : s * b;
   return s * (m > 0.0 ? m : 0.0);
 }
 
-/* values w_{i-1}, w_i, w_{i+1}, w_{i+2} -> states left and right of face i+1/2 */
-static void kappa_face(const double* w4, double* wl, double* wr) {
-  double K1 = (1.0 - KAPPA) / 4.0, K2 = (1.0 + KAPPA) / 4.0, b = (3.0 - KAPPA) / (1.0 - KAPPA);
+static double recon_kappa(int recon) {
+  return recon == ORC_RECON_KAPPA_ZERO ? 0.0 : (recon == ORC_RECON_KAPPA_UPWIND ? -1.0 : 1.0 / 3.0);
+}
+
+/* values w_{i-1}, w_i, w_{i+1}, w_{i+2} -> states left and right of face i+1/2.
+ * ORC_RECON_PRINTED: dW_i = K2 minmod(dw_{i-1}, dw_i) + K1 minmod(dw_i, b dw_{i-1}),
+ * dW_{i+1} = K2 minmod(dw_{i+1}, dw_i) + K1 minmod(dw_i, b dw_{i+1}), w_L = w_i + dW_i,
+ * w_R = w_{i+1} - dW_{i+1} (Eq. 13-14 as printed). */
+static void kappa_face(int recon, const double* w4, double* wl, double* wr) {
+  double kappa = recon_kappa(recon);
+  double K1 = (1.0 - kappa) / 4.0, K2 = (1.0 + kappa) / 4.0, b = (3.0 - kappa) / (1.0 - kappa);
   double dwm = w4[1] - w4[0]; /* dw_{i-1} */
   double dw0 = w4[2] - w4[1]; /* dw_i     */
   double dwp = w4[3] - w4[2]; /* dw_{i+1} */
+  if (recon == ORC_RECON_PRINTED) {
+    *wl = w4[1] + K2 * minmod(dwm, dw0) + K1 * minmod(dw0, b * dwm);
+    *wr = w4[2] - K2 * minmod(dwp, dw0) - K1 * minmod(dw0, b * dwp);
+    return;
+  }
   *wl = w4[1] + K1 * minmod(dwm, b * dw0) + K2 * minmod(dw0, b * dwm);
   *wr = w4[2] - K1 * minmod(dwp, b * dw0) - K2 * minmod(dw0, b * dwp);
 }
 
 void orc_reconstruct_1d(int n, const double* w, double* wl, double* wr) {
-  for (int m = 2; m <= n - 2; ++m) kappa_face(w + m - 2, wl + m, wr + m);
+  for (int m = 2; m <= n - 2; ++m) kappa_face(ORC_RECON_KAPPA_THIRD, w + m - 2, wl + m, wr + m);
+}
+
+void orc_reconstruct_1d_ex(int recon, int n, const double* w, double* wl, double* wr) {
+  for (int m = 2; m <= n - 2; ++m) kappa_face(recon, w + m - 2, wl + m, wr + m);
 }
 
 /* ------------------------------------------------------------ face fluxes ----
@@ -535,7 +553,7 @@ static void compute_fluxes(const grid* G, int d, int order, double* const W[NF],
             wr[m] = q[cell[2]];
           } else {
             double w4[4] = {q[cell[0]], q[cell[1]], q[cell[2]], q[cell[3]]};
-            kappa_face(w4, &wl[m], &wr[m]);
+            kappa_face(G->recon, w4, &wl[m], &wr[m]);
           }
         }
         if (order != 1 && (wl[0] <= 0.0 || wr[0] <= 0.0 || wl[4] <= 0.0 || wr[4] <= 0.0)) {

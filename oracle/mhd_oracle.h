@@ -27,6 +27,12 @@ enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1 };
  * HLLC is the gas-dynamics solver: a face that carries a field (B_n or a transverse
  * component non-zero on either side) takes HLLD, which is HLLC when B = 0. */
 enum { ORC_RIEMANN_HLLD = 0, ORC_RIEMANN_HLLC = 1, ORC_RIEMANN_HLL = 2 };
+/* Reconstruction of Eq. 12-14: kappa = 1/3 (third-order upwind biased, the paper's
+ * choice), 0 (second-order upwind biased), -1 (second-order fully upwind), in the
+ * standard compressive kappa-scheme arrangement; and kappa = 1/3 in the arrangement of
+ * K1, K2 and b exactly as printed (a cross-check of that reading; second order only). */
+enum { ORC_RECON_KAPPA_THIRD = 0, ORC_RECON_KAPPA_ZERO = 1, ORC_RECON_KAPPA_UPWIND = 2,
+       ORC_RECON_PRINTED = 3 };
 enum { ORC_POT_NONE = 0, ORC_POT_GAUSS_X = 1, ORC_POT_LOG_DISC = 2 };
 
 typedef struct {
@@ -36,6 +42,7 @@ typedef struct {
   int bc[6];           /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
   double gamma;
   int riemann;         /* ORC_RIEMANN_* (0: HLLD) */
+  int recon;           /* ORC_RECON_* (0: kappa = 1/3) */
 } orc_patch;
 
 typedef struct {
@@ -79,6 +86,9 @@ void orc_riemann_batch(int solver, int n, const double* wl, const double* wr, co
 /* kappa = 1/3 compressive minmod reconstruction on a 1D array of n values:
  * for interfaces m = 2..n-2 (between w[m-1] and w[m]) writes wl[m], wr[m]. */
 void orc_reconstruct_1d(int n, const double* w, double* wl, double* wr);
+
+/* The same for the reconstruction ORC_RECON_*. */
+void orc_reconstruct_1d_ex(int recon, int n, const double* w, double* wl, double* wr);
 
 /* Total over the interior of the 5 cell fields (fixed order) and the maximum of
  * |div B| * min(d) over interior cells. */

@@ -254,6 +254,23 @@ def sedov(nx: int = 512, ny: int = 768, r0: float = 0.01, e0: float = 1.0, p0: f
     return state_from_prim(g, 1.0, 0.0, 0.0, 0.0, p, 0.0, 0.0, 0.0)
 
 
+def rotor(n: int = 512, v0: float = 2.0, gamma: float = 1.4) -> State:
+    """Magnetic rotor (Section 3.6) on [-0.5, 0.5]^2, outflow: rho = 10 and rigid rotation
+    v = v0 (-y, x)/r0 for r < r0 = 0.1; rho = 1 + 9 f, v = v0 f (-y, x)/r0 with
+    f = (r1 - r)/(r1 - r0) for r0 < r < r1 = 0.2 (as printed); rho = 1 at rest beyond;
+    p = 1 and Bx = 5/sqrt(4 pi) everywhere.  v0, gamma, the domain and the end time are not
+    given (v0 = 2, gamma = 1.4, t = 0.15 taken)."""
+    g = Geom(n, n, 1, -0.5, -0.5, 0.0, 1.0 / n, 1.0 / n, 1.0, (1, 1, 1, 1, 0, 0), gamma)
+    x, y, _ = g.centres()
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    r = np.sqrt(X * X + Y * Y)
+    r0, r1 = 0.1, 0.2
+    f = np.where(r < r0, 1.0, np.where(r < r1, (r1 - r) / (r1 - r0), 0.0))
+    rho = np.where(r < r0, 10.0, 1.0 + 9.0 * f)
+    vx, vy = -v0 * f * Y / r0, v0 * f * X / r0
+    return state_from_prim(g, rho[None], vx[None], vy[None], 0.0, 1.0, 5.0 / math.sqrt(4.0 * math.pi), 0.0, 0.0)
+
+
 # Floors for the Sedov blast at the paper's resolution: with its 1e8 pressure jump from a
 # five-cell source the plain scheme drives ambient cells ahead of the shock to p < 0 within
 # ten steps (the FP64 oracle too); p/rho >= 1e-6 (ambient 1e-5) keeps it positive.

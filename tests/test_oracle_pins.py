@@ -297,6 +297,42 @@ def test_reconstruct_third_order_smooth():
     assert errs[0] / errs[1] > 6.5 and errs[1] / errs[2] > 6.5
 
 
+@pytest.mark.parametrize("recon,ratio", [("kappa_third", (7.5, 8.5)), ("kappa_zero", (3.5, 4.5)),
+                                         ("kappa_upwind", (3.5, 4.5)), ("printed", (3.5, 4.5))])
+def test_reconstruct_variants_order(recon, ratio):
+    """Eq. 12-14 with the kappa values the text names: 1/3 is third order (error / 8 per
+    halving of h), 0 and -1 second order (/ 4); kappa = 1/3 in the printed arrangement of
+    K1, K2 and b is second order only (why the standard arrangement is the reading)."""
+    errs = []
+    for n in (80, 160, 320):
+        x = np.linspace(-1.0, 1.0, n + 1)
+        h = x[1] - x[0]
+        avg = (np.cos(x[:-1]) - np.cos(x[1:])) / h
+        wl, wr = oracle.reconstruct_1d(avg, recon)
+        exact = np.sin(x[1:-1])
+        m = np.arange(4, n - 3)
+        errs.append(max(np.max(np.abs(wl[m] - exact[m - 1])), np.max(np.abs(wr[m] - exact[m - 1]))))
+    for a, b in zip(errs, errs[1:]):
+        assert ratio[0] < a / b < ratio[1], (recon, errs)
+
+
+@pytest.mark.parametrize("recon,kappa", [("kappa_third", 1.0 / 3.0), ("kappa_zero", 0.0),
+                                         ("kappa_upwind", -1.0), ("printed", 1.0 / 3.0)])
+def test_reconstruct_quadratic_closed_form(recon, kappa):
+    """Closed form: on cell averages of w = x^2 (a_i = x_i^2 + h^2/12), where minmod does not
+    act, the standard arrangement gives w_L(x_i + h/2) = x_i^2 + x_i h + h^2/12 + kappa h^2/2,
+    an error of h^2 (kappa/2 - 1/6) (zero for kappa = 1/3); the printed arrangement swaps
+    K1 and K2 on the two slopes, an error of -h^2 (1/6 + kappa/2)."""
+    h = 0.01
+    xc = 1.0 + h * np.arange(40)
+    avg = xc * xc + h * h / 12.0
+    wl, _ = oracle.reconstruct_1d(avg, recon)
+    m = np.arange(3, 37)  # interface m lies between cells m-1 and m, at xc[m-1] + h/2
+    err = wl[m] - (xc[m - 1] + 0.5 * h) ** 2
+    want = h * h * (kappa / 2.0 - 1.0 / 6.0) if recon != "printed" else -h * h * (1.0 / 6.0 + kappa / 2.0)
+    assert np.max(np.abs(err - want)) <= 1e-12, (recon, err[:3], want)
+
+
 # ---------------------------------------------------------- step invariants --
 
 def _rel_change(a, b, scale):
