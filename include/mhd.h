@@ -66,6 +66,10 @@ enum { MHD_POT_NONE = 0, MHD_POT_GAUSS_X = 1, MHD_POT_LOG_DISC = 2 };
 /* Riemann solvers (Section 2.1): HLLD for magneto-gas dynamics (the default); HLLC and
  * HLL for pure gas dynamics (B = 0). */
 enum { MHD_RIEMANN_HLLD = 0, MHD_RIEMANN_HLLC = 1, MHD_RIEMANN_HLL = 2 };
+/* Reconstruction of the corrector (Eq. 12-14): kappa = 1/3, third-order upwind biased (the
+ * paper's choice, default); kappa = 0, second-order upwind biased; kappa = -1, second-order
+ * fully upwind. */
+enum { MHD_RECON_KAPPA_THIRD = 0, MHD_RECON_KAPPA_ZERO = 1, MHD_RECON_KAPPA_UPWIND = 2 };
 
 enum { MHD_THERMAL_OFF = 0, MHD_THERMAL_PLAIN = 1, MHD_THERMAL_SURROGATE = 2 };
 
@@ -152,6 +156,11 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* src);
  * The outer speed estimate and the mass-flux scale of the corner EMFs are the same for
  * all three.  MHD_ERR_ARG for another value. */
 int mhd_set_riemann(mhd_ctx* ctx, int solver);
+
+/* Reconstruction of every patch for the following steps, MHD_RECON_* (the minmod
+ * kappa-scheme with K1 = (1 - kappa)/4, K2 = (1 + kappa)/4, b = (3 - kappa)/(1 - kappa)).
+ * MHD_ERR_ARG for another value. */
+int mhd_set_reconstruction(mhd_ctx* ctx, int recon);
 
 /* Advance every patch by one van Leer step (Eq. 7, Eq. 8).  dt > 0: that dt for
  * every patch.  dt <= 0: each patch uses cfl * its own CFL limit of its current

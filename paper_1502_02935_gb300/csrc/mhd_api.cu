@@ -39,6 +39,16 @@ struct PatchHost {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// kappa-scheme coefficients of Eq. 13-14 and their FP32 copies
+void set_kappa(PatchDev& D, double kappa) {
+  D.rK1 = (1.0 - kappa) / 4.0;
+  D.rK2 = (1.0 + kappa) / 4.0;
+  D.rb = (3.0 - kappa) / (1.0 - kappa);
+  D.rK1_f = (float)D.rK1;
+  D.rK2_f = (float)D.rK2;
+  D.rb_f = (float)D.rb;
+}
+
 // The caller's dense layout of a patch: U as 5 fields [nz][ny][nx], then the faces Bx
 // [nz][ny][nx+1], By [nz][ny+1][nx], Bz [nz+1][ny][nx].  Row r of it (a run along x) is
 // field f at (j, k), len values long, starting at off in u (cell fields) or b (faces).
@@ -633,6 +643,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     D.err = ctx->err;
     D.index = p;
     D.riemann = RIEMANN_HLLD;
+    set_kappa(D, 1.0 / 3.0);
     D.floors = 0;
     D.rho_floor = D.pr_floor = 0.0;
     D.pr_ceil = INFINITY;
@@ -703,6 +714,17 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   drop_graph(ctx);  // sources are baked into captured launches
   ctx->w_valid = false;
+  return MHD_OK;
+}
+
+int mhd_set_reconstruction(mhd_ctx* ctx, int recon) {
+  if (!ctx) return MHD_ERR_ARG;
+  if (recon < MHD_RECON_KAPPA_THIRD || recon > MHD_RECON_KAPPA_UPWIND)
+    return fail(ctx, MHD_ERR_ARG, "unknown reconstruction");
+  const double kappa = recon == MHD_RECON_KAPPA_ZERO ? 0.0 : (recon == MHD_RECON_KAPPA_UPWIND ? -1.0 : 1.0 / 3.0);
+  for (auto& p : ctx->P) set_kappa(p.dev, kappa);
+  if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
+  drop_graph(ctx);  // the coefficients are part of the captured launches' arguments
   return MHD_OK;
 }
 

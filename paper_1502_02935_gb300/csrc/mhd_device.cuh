@@ -60,6 +60,9 @@ struct PatchDev {
   double rho_floor, pr_floor, pr_ceil;
   unsigned long long* floored;  // count of cells changed by the end-of-step floors
   int riemann;                  // RIEMANN_*
+  // kappa-scheme coefficients K1 = (1 - kappa)/4, K2 = (1 + kappa)/4, b = (3 - kappa)/(1 - kappa)
+  double rK1, rK2, rb;
+  float rK1_f, rK2_f, rb_f;
 };
 
 struct SourceDev {
@@ -189,6 +192,11 @@ template <> struct Ar<float> {
 template <class R> struct Gam;
 template <> struct Gam<double> {
   static __device__ __forceinline__ double get(const PatchDev& P) { return P.gamma; }
+  static __device__ __forceinline__ void kappa(const PatchDev& P, double& K1, double& K2, double& b) {
+    K1 = P.rK1;
+    K2 = P.rK2;
+    b = P.rb;
+  }
   static __device__ __forceinline__ double d(const PatchDev& P, int a) { return P.d[a]; }
   static __device__ __forceinline__ double inv(const PatchDev& P, int a) { return P.inv_d[a]; }
   static __device__ __forceinline__ double lo(const PatchDev& P, int a) { return P.lo[a]; }
@@ -199,6 +207,11 @@ template <> struct Gam<double> {
 };
 template <> struct Gam<float> {
   static __device__ __forceinline__ float get(const PatchDev& P) { return P.gamma_f; }
+  static __device__ __forceinline__ void kappa(const PatchDev& P, float& K1, float& K2, float& b) {
+    K1 = P.rK1_f;
+    K2 = P.rK2_f;
+    b = P.rb_f;
+  }
   static __device__ __forceinline__ float d(const PatchDev& P, int a) { return P.d_f[a]; }
   static __device__ __forceinline__ float inv(const PatchDev& P, int a) { return P.inv_d_f[a]; }
   static __device__ __forceinline__ float lo(const PatchDev& P, int a) { return P.lo_f[a]; }
@@ -493,8 +506,9 @@ __device__ __forceinline__ void riemann(int solver, const R* wl, const R* wr, R 
 }
 
 // --------------------------------------------------------- reconstruction ----
-// kappa = 1/3 compressive minmod scheme (Eq. 12-14 read in the standard form that is
-// third-order upwind biased): K1 = 1/6, K2 = 1/3, b = 4.
+// compressive minmod kappa-scheme (Eq. 12-14 read in the standard form, third-order upwind
+// biased for the paper's kappa = 1/3: K1 = 1/6, K2 = 1/3, b = 4; kappa = 0 and -1 are the
+// second-order variants the text names), coefficients from the patch.
 // minmod(a, b): the smaller magnitude with the common sign when a and b have the same
 // sign, else 0; as max(min(a, b), min(max(a, b), 0)), which is exact (min and max do not
 // round) and needs no product a b (which can underflow)
@@ -503,8 +517,7 @@ template <class R> __device__ __forceinline__ R minmod(R a, R b) {
 }
 
 template <class R>
-__device__ __forceinline__ void kappa_face(R wm1, R w0, R w1, R w2, R& wl, R& wr) {
-  const R K1 = R(1) / R(6), K2 = R(1) / R(3), b = R(4);
+__device__ __forceinline__ void kappa_face(R wm1, R w0, R w1, R w2, R K1, R K2, R b, R& wl, R& wr) {
   const R dwm = w0 - wm1, dw0 = w1 - w0, dwp = w2 - w1;
   wl = w0 + K1 * minmod<R>(dwm, b * dw0) + K2 * minmod<R>(dw0, b * dwm);
   wr = w1 - K1 * minmod<R>(dwp, b * dw0) - K2 * minmod<R>(dw0, b * dwp);
@@ -660,7 +673,7 @@ __device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict
 // (o = -1 left, o = 0 right).  f[0..7]: rho, m_D, m_T1, m_T2, E, B_T1, B_T2 fluxes and the
 // wave-speed scale sigma.
 template <class R, int D, int ORDER, class Get>
-__device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, int solver, R* f) {
+__device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, int solver, const R* kap, R* f) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const int comp[7] = {WR, WVX + D, WVX + T1, WVX + T2, WP, WBX + T1, WBX + T2};
   R wl[7], wr[7];
@@ -672,7 +685,9 @@ __device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, int solve
     }
   } else {
 #pragma unroll
-    for (int m = 0; m < 7; ++m) kappa_face<R>(get(comp[m], -2), get(comp[m], -1), get(comp[m], 0), get(comp[m], 1), wl[m], wr[m]);
+    for (int m = 0; m < 7; ++m)
+      kappa_face<R>(get(comp[m], -2), get(comp[m], -1), get(comp[m], 0), get(comp[m], 1), kap[0], kap[1], kap[2],
+                    wl[m], wr[m]);
     if (!(wl[0] > R(0)) || !(wr[0] > R(0)) || !(wl[4] > R(0)) || !(wr[4] > R(0))) {
 #pragma unroll
       for (int m = 0; m < 7; ++m) {
@@ -701,9 +716,10 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
                                            int i, int j, int k, int solver) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long q = qidx(P, i, j, k), QS = P.QS, st = qstride(P, D);
-  R f[8];
+  R f[8], kap[3];
+  Gam<R>::kappa(P, kap[0], kap[1], kap[2]);
   flux_core<R, D, ORDER>([&](int m, int o) { return W[m * QS + q + o * st]; }, face_bn<R, D>(P, Ub, i, j, k),
-                         Gam<R>::get(P), solver, f);
+                         Gam<R>::get(P), solver, kap, f);
   F[q] = f[0];
   F[(1 + D) * QS + q] = f[1];
   F[(1 + T1) * QS + q] = f[2];

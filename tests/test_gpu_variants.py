@@ -1,0 +1,60 @@
+"""GPU parity of the reconstruction variants of Eq. 12-14 (kappa = 0 and -1, the second-order
+cases the text names) and of the magnetic rotor (Section 3.6) against the FP64 oracle.
+Tolerances as in test_gpu_parity."""
+from __future__ import annotations
+
+import pytest
+
+import oracle
+from paper_1502_02935_gb300 import inputs, mhd
+from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "turbulence_37x29x23": lambda: inputs.turbulence((37, 29, 23), seed=5),
+    "outflow_17x9x5": lambda: inputs.smooth_random(
+        inputs.Geom(17, 9, 5, 0.0, 0.0, 0.0, 0.1, 0.11, 0.13, (1,) * 6, 5.0 / 3.0), 3),
+    "orszag_tang_64x48": lambda: inputs.orszag_tang(64, 48),
+    "rotor_96": lambda: inputs.rotor(96),
+}
+
+
+def _run(st, precision, recon, nsteps, cfl=0.4):
+    g = mhd.Grid(st, precision=precision, cfl=cfl)
+    g.set_reconstruction(recon)
+    ref = st
+    for _ in range(nsteps):
+        dt = oracle.cfl_dt(ref, cfl)
+        g.step(dt)
+        ref = oracle.step(ref, dt, recon=recon)
+    got = g.get_state(0)
+    g.close()
+    return got, ref
+
+
+@pytest.mark.parametrize("recon", ["kappa_zero", "kappa_upwind"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_kappa_variant_matches_oracle(recon, case):
+    got, ref = _run(CASES[case](), "fp64", recon, 3)
+    assert_close(got, ref, FP64_TOL, f"{case} {recon}")
+
+
+@pytest.mark.parametrize("recon", ["kappa_zero", "kappa_upwind"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mixed_kappa_variant_matches_oracle(recon, case):
+    got, ref = _run(CASES[case](), "mixed", recon, 1)
+    assert_close(got, ref, MIXED_TOL, f"{case} {recon}", normalized=True)
+
+
+@pytest.mark.parametrize("precision,tol,nsteps", [("fp64", FP64_TOL, 4), ("mixed", MIXED_TOL, 1)])
+def test_rotor_matches_oracle(precision, tol, nsteps):
+    """The rotor with the default scheme (HLLD, kappa = 1/3)."""
+    got, ref = _run(inputs.rotor(96), precision, "kappa_third", nsteps)
+    assert_close(got, ref, tol, "rotor", normalized=(precision == "mixed"))
+
+
+def test_set_reconstruction_rejects_unknown_value():
+    g = mhd.Grid(inputs.sod(64), precision="fp64", cfl=0.8)
+    assert g.L.mhd_set_reconstruction(g.h, 3) == -1  # MHD_ERR_ARG (the printed form is oracle-only)
+    g.close()
