@@ -474,12 +474,15 @@ def run_table(args):
     ncores = os.cpu_count() or 1
     stream = torch.cuda.Stream()
 
-    def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None, riemann=None):
+    def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None, riemann=None,
+                 recon=None):
         sts = states if isinstance(states, list) else [states]
         g = mhd.Grid(sts if len(sts) > 1 else sts[0], precision=precision, cfl=CFL, flags=flags,
                      stream=stream.cuda_stream)
         if riemann:
             g.set_riemann(riemann)
+        if recon:
+            g.set_reconstruction(recon)
         if src:
             g.set_sources(**src)
         if thermal:
@@ -506,8 +509,10 @@ def run_table(args):
         el = time.perf_counter() - t0
         return sum(st.geom.ncell for st in sts) * steps / el, el
 
-    def gpu_to_time(st, precision, cfl, t_end):
+    def gpu_to_time(st, precision, cfl, t_end, recon=None):
         g = mhd.Grid(st, precision=precision, cfl=cfl, stream=stream.cuda_stream)
+        if recon:
+            g.set_reconstruction(recon)
         t, n = 0.0, 0
         while t < t_end * (1 - 1e-14):
             dt = min(g.cfl_dt(), t_end - t)
@@ -621,6 +626,23 @@ def run_table(args):
         st = inputs.turbulence(256, seed=SEED, b0=0.0)
         table["turbulence 256^3, B = 0 (HLLC / HLL / HLLD)"] = {
             "gpu_mixed_" + s_: gpu_rate(st, "mixed", 10, riemann=s_) for s_ in ("hllc", "hll", "hlld")}
+    if want("rotor"):
+        # magnetic rotor (Section 3.6) with the reconstructions of Eq. 12-14: rates at 512^2,
+        # and the per-field L1 difference from the oracle at t = 0.15 on 256^2
+        st = inputs.rotor(512)
+        rot = {"gpu_mixed_" + r_: gpu_rate(st, "mixed", 100, recon=r_)
+               for r_ in ("kappa_third", "kappa_zero", "kappa_upwind")}
+        rot["gpu_fp64_kappa_third"] = gpu_rate(st, "fp64", 30)
+        r1, _ = oracle_rate(st, 1, 5)
+        small = inputs.rotor(256)
+        oracle.set_threads(1)
+        ref, nref = oracle.run(small, CFL, 0.15)
+        gmx, n = gpu_to_time(small, "mixed", CFL, 0.15)
+        g64, _ = gpu_to_time(small, "fp64", CFL, 0.15)
+        rot.update({"oracle_1core": r1, "oracle_1core_sample": "512^2, 5 steps (one plane: no parallel work)",
+                    "l1_at_t015_256sq": {"fp64": l1(g64, ref), "mixed": l1(gmx, ref)}, "steps": n,
+                    "oracle_steps": nref})
+        table["Rotor 2D 512^2 (kappa = 1/3, 0, -1)"] = rot
     print(json.dumps({"table": table, "host_cores": ncores, "unit": "zone-updates/s"}), flush=True)
     return 0
 
@@ -641,7 +663,7 @@ def main():
     ap.add_argument("--table", action="store_true",
                     help="every workload configuration, GPU and oracle side by side (minutes; no bench line)")
     ap.add_argument("--rows", default="",
-                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas (default all)")
+                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas,rotor (default all)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.table:
