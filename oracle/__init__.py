@@ -29,7 +29,8 @@ class OrcPatch(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
-                ("bc", C.c_int * 6), ("gamma", C.c_double), ("riemann", C.c_int), ("recon", C.c_int)]
+                ("bc", C.c_int * 6), ("gamma", C.c_double), ("riemann", C.c_int), ("recon", C.c_int),
+                ("inflow", (C.c_double * 8) * 6)]
 
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics.  HLLC
@@ -112,10 +113,14 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def patch_struct(g, riemann: str = "hlld", recon: str = "kappa_third") -> OrcPatch:
+def patch_struct(g, riemann: str = "hlld", recon: str = "kappa_third", inflow=None) -> OrcPatch:
+    """``inflow``: {side: [rho, vx, vy, vz, p, Bx, By, Bz]} for the sides whose bc is 2."""
     p = OrcPatch()
     p.riemann = RIEMANN[riemann]
     p.recon = RECON[recon]
+    for side, w in (inflow or {}).items():
+        for m in range(8):
+            p.inflow[int(side)][m] = float(w[m])
     p.nx, p.ny, p.nz = g.nx, g.ny, g.nz
     p.x0, p.y0, p.z0 = g.x0, g.y0, g.z0
     p.dx, p.dy, p.dz = g.dx, g.dy, g.dz
@@ -143,13 +148,14 @@ def _copy_state(st):
 
 
 def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str = "hlld",
-         recon: str = "kappa_third"):
+         recon: str = "kappa_third", inflow=None):
     """``nsteps`` van Leer steps of fixed size dt; returns a new State.  If ``floored``
     is a list, the per-step counts of cells changed by the end-of-step floors are
-    appended to it.  ``riemann``: "hlld", "hllc" or "hll"; ``recon``: a key of RECON."""
+    appended to it.  ``riemann``: "hlld", "hllc" or "hll"; ``recon``: a key of RECON;
+    ``inflow``: the states of the inflow sides (see patch_struct)."""
     L = lib()
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom, riemann, recon), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon, inflow), source_struct(source)
     for _ in range(nsteps):
         n = L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
         if n < 0:
@@ -159,17 +165,17 @@ def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str
     return st.replace(U=U, Bx=Bx, By=By, Bz=Bz)
 
 
-def cfl_dt(st, cfl: float, source=None) -> float:
+def cfl_dt(st, cfl: float, source=None, inflow=None) -> float:
     U, Bx, By, Bz = _copy_state(st)
-    return float(lib().orc_cfl_dt(C.byref(patch_struct(st.geom)), C.byref(source_struct(source)),
+    return float(lib().orc_cfl_dt(C.byref(patch_struct(st.geom, inflow=inflow)), C.byref(source_struct(source)),
                                   _p(U), _p(Bx), _p(By), _p(Bz), cfl))
 
 
 def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None, riemann: str = "hlld",
-        recon: str = "kappa_third"):
+        recon: str = "kappa_third", inflow=None):
     """Advance to t_end with CFL time steps; returns (State, steps)."""
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom, riemann, recon), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon, inflow), source_struct(source)
     n = lib().orc_run(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(cfl),
                       float(t_end), int(max_steps))
     if n < 0:

@@ -46,6 +46,8 @@ typedef struct {
   double d[3], lo[3], gamma;
   int riemann; /* ORC_RIEMANN_* */
   int recon;   /* ORC_RECON_* */
+  int inflow[6];           /* side has an inflow boundary */
+  double in_u[6][NF];      /* its state: conserved cell fields and the three field components */
   long tot;
   int floors;                         /* floors on (rho_floor > 0) */
   double rho_floor, pr_floor, pr_ceil; /* pr_ceil = +inf when no ceiling is set */
@@ -69,13 +71,15 @@ static int make_grid(const orc_patch* p, grid* G) {
     G->g[a] = G->act[a] ? GHOST : 0;
     G->N[a] = n[a] + 2 * G->g[a] + 1;
     int blo = p->bc[2 * a], bhi = p->bc[2 * a + 1];
+    G->inflow[2 * a] = G->inflow[2 * a + 1] = 0;
     if (!G->act[a]) {
       G->per[a] = 1;
     } else {
       if ((blo == ORC_BC_PERIODIC) != (bhi == ORC_BC_PERIODIC)) return -1;
-      if (blo != ORC_BC_PERIODIC && blo != ORC_BC_OUTFLOW) return -1;
-      if (bhi != ORC_BC_PERIODIC && bhi != ORC_BC_OUTFLOW) return -1;
+      if (blo < ORC_BC_PERIODIC || blo > ORC_BC_INFLOW || bhi < ORC_BC_PERIODIC || bhi > ORC_BC_INFLOW) return -1;
       G->per[a] = blo == ORC_BC_PERIODIC;
+      G->inflow[2 * a] = blo == ORC_BC_INFLOW;
+      G->inflow[2 * a + 1] = bhi == ORC_BC_INFLOW;
     }
     G->d[a] = d[a];
     G->lo[a] = lo[a];
@@ -87,6 +91,20 @@ static int make_grid(const orc_patch* p, grid* G) {
   G->riemann = p->riemann;
   if (p->recon < ORC_RECON_KAPPA_THIRD || p->recon > ORC_RECON_PRINTED) return -1;
   G->recon = p->recon;
+  for (int side = 0; side < 6; ++side) {
+    if (!G->inflow[side]) continue;
+    const double* w = p->inflow[side];
+    if (!(w[0] > 0.0) || !(w[4] > 0.0)) return -1;
+    G->in_u[side][RHO] = w[0];
+    G->in_u[side][MX] = w[0] * w[1];
+    G->in_u[side][MY] = w[0] * w[2];
+    G->in_u[side][MZ] = w[0] * w[3];
+    G->in_u[side][EN] = w[4] / (G->gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
+                        0.5 * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+    G->in_u[side][BXF] = w[5];
+    G->in_u[side][BYF] = w[6];
+    G->in_u[side][BZF] = w[7];
+  }
   G->floors = 0;
   G->rho_floor = G->pr_floor = 0.0;
   G->pr_ceil = INFINITY;
@@ -123,6 +141,18 @@ static int src_index(const grid* G, int a, int v, int is_face_axis) {
   return v > n - 1 ? n - 1 : v;
 }
 
+/* Inflow: a cell beyond an inflow side (the first such side in axis order) holds that
+ * side's state, cell fields and the faces it owns alike; the boundary face itself (index
+ * 0 or n along the axis) is a face of the domain and is CT-updated. */
+static int inflow_side(const grid* G, const int c[3], int fa) {
+  for (int a = 0; a < 3; ++a) {
+    int hi = G->n[a] - 1 + (a == fa ? 1 : 0); /* last index inside along a */
+    if (c[a] < 0 && G->inflow[2 * a]) return 2 * a;
+    if (c[a] > hi && G->inflow[2 * a + 1]) return 2 * a + 1;
+  }
+  return -1;
+}
+
 static void fill_ghosts(const grid* G, double* const F[NF]) {
   for (int f = 0; f < NF; ++f) {
     int fa = f >= BXF ? f - BXF : -1; /* face axis of this field */
@@ -132,6 +162,11 @@ static void fill_ghosts(const grid* G, double* const F[NF]) {
       for (int jj = 0; jj < G->N[1]; ++jj)
         for (int ii = 0; ii < G->N[0]; ++ii) {
           int c[3] = {ii - G->g[0], jj - G->g[1], kk - G->g[2]};
+          int side = inflow_side(G, c, fa);
+          if (side >= 0) {
+            q[ixv(G, c)] = G->in_u[side][f];
+            continue;
+          }
           int s[3];
           for (int a = 0; a < 3; ++a) s[a] = src_index(G, a, c[a], a == fa);
           if (s[0] == c[0] && s[1] == c[1] && s[2] == c[2]) continue;

@@ -22,7 +22,9 @@
 extern "C" {
 #endif
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1 };
+/* Boundary conditions (Section 3 prose names free and inflow boundaries): periodic;
+ * outflow = zero-gradient copy; inflow = a fixed state beyond the boundary. */
+enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_INFLOW = 2 };
 /* Riemann solver (Section 2.1: HLL or HLLC for pure gas dynamics, HLLD for MHD).
  * HLLC is the gas-dynamics solver: a face that carries a field (B_n or a transverse
  * component non-zero on either side) takes HLLD, which is HLLC when B = 0. */
@@ -43,6 +45,9 @@ typedef struct {
   double gamma;
   int riemann;         /* ORC_RIEMANN_* (0: HLLD) */
   int recon;           /* ORC_RECON_* (0: kappa = 1/3) */
+  /* primitive state [rho, vx, vy, vz, p, Bx, By, Bz] beyond each side whose bc is
+   * ORC_BC_INFLOW (same side order as bc) */
+  double inflow[6][8];
 } orc_patch;
 
 typedef struct {

@@ -271,6 +271,28 @@ def rotor(n: int = 512, v0: float = 2.0, gamma: float = 1.4) -> State:
     return state_from_prim(g, rho[None], vx[None], vy[None], 0.0, 1.0, 5.0 / math.sqrt(4.0 * math.pi), 0.0, 0.0)
 
 
+def bow_shock(n: int = 400, psi0: float = 5.0, x0: float = 0.1):
+    """Flow through a potential well (Section 3.4): rho = 1, p = 1, vx = 1, gamma = 1.4 on
+    [-0.5, 0.5] (the domain is not given), Psi = -psi0 exp(-(x/x0)^2); steady inflow of the
+    initial state at the left, free (outflow) at the right.  Returns (state, source,
+    inflow)."""
+    g = Geom(n, 1, 1, -0.5, 0.0, 0.0, 1.0 / n, 1.0, 1.0, (2, 1, 0, 0, 0, 0), 1.4)
+    st = state_from_prim(g, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0)
+    src = dict(potential=1, psi0=psi0, xc=0.0, xw=x0)
+    return st, src, {0: (1.0, 1.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0)}
+
+
+def isothermal_well(n: int = 128, psi0: float = 1.0, x0: float = 0.1) -> tuple:
+    """Hydrostatic isothermal gas (p = rho, at rest) in the Gaussian well of the bow-shock
+    test: rho = exp(-Psi) = exp(psi0 exp(-(x/x0)^2)), outflow boundaries on [-0.5, 0.5],
+    gamma = 1.4.  An exact steady state of the equations; the scheme holds it to its
+    truncation error.  Returns (state, source)."""
+    g = Geom(n, 1, 1, -0.5, 0.0, 0.0, 1.0 / n, 1.0, 1.0, (1, 1, 0, 0, 0, 0), 1.4)
+    x = g.centres()[0]
+    rho = np.exp(psi0 * np.exp(-(x / x0) ** 2))[None, None, :]
+    return state_from_prim(g, rho, 0.0, 0.0, 0.0, rho, 0.0, 0.0, 0.0), dict(potential=1, psi0=psi0, xc=0.0, xw=x0)
+
+
 # Floors for the Sedov blast at the paper's resolution: with its 1e8 pressure jump from a
 # five-cell source the plain scheme drives ambient cells ahead of the shock to p < 0 within
 # ten steps (the FP64 oracle too); p/rho >= 1e-6 (ambient 1e-5) keeps it positive.
