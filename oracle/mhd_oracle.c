@@ -48,6 +48,7 @@ typedef struct {
   int recon;   /* ORC_RECON_* */
   int inflow[6];           /* side has an inflow boundary */
   double in_u[6][NF];      /* its state: conserved cell fields and the three field components */
+  double in_w[6][NF];      /* and its primitives rho, vx, vy, vz, p, Bx, By, Bz */
   long tot;
   int floors;                         /* floors on (rho_floor > 0) */
   double rho_floor, pr_floor, pr_ceil; /* pr_ceil = +inf when no ceiling is set */
@@ -101,6 +102,7 @@ static int make_grid(const orc_patch* p, grid* G) {
     G->in_u[side][MZ] = w[0] * w[3];
     G->in_u[side][EN] = w[4] / (G->gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) +
                         0.5 * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+    for (int m = 0; m < NF; ++m) G->in_w[side][m] = w[m];
     G->in_u[side][BXF] = w[5];
     G->in_u[side][BYF] = w[6];
     G->in_u[side][BZF] = w[7];
@@ -187,6 +189,16 @@ static void cons_to_prim(const grid* G, double* const U[NF], double* const W[NF]
   for (int k = -G->g[2]; k < G->n[2] + G->g[2]; ++k)
     for (int j = -G->g[1]; j < G->n[1] + G->g[1]; ++j)
       for (int i = -G->g[0]; i < G->n[0] + G->g[0]; ++i) {
+        {
+          /* a cell beyond an inflow side holds the side's primitive state */
+          int cc[3] = {i, j, k};
+          int side = inflow_side(G, cc, -1);
+          if (side >= 0) {
+            long c0 = ix(G, i, j, k);
+            for (int m = 0; m < NF; ++m) W[m][c0] = G->in_w[side][m];
+            continue;
+          }
+        }
         long c = ix(G, i, j, k);
         double rho = U[RHO][c];
         if (G->floors && rho < G->rho_floor) rho = G->rho_floor;
