@@ -48,7 +48,11 @@ enum {
   MHD_ERR_NOMEM = -7      /* device allocation failed */
 };
 
-enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 };
+/* Boundaries (Section 3 names free and inflow boundaries): periodic; outflow = zero-gradient
+ * copy of the cell fields and transverse faces; inflow = a fixed state beyond the boundary
+ * (mhd_set_inflow).  Normal faces on the boundary itself are CT-updated for outflow and
+ * inflow alike. */
+enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1, MHD_BC_INFLOW = 2 };
 
 enum {
   MHD_PREC_FP64 = 0, /* every stage in FP64 */
@@ -161,6 +165,14 @@ int mhd_set_riemann(mhd_ctx* ctx, int solver);
  * kappa-scheme with K1 = (1 - kappa)/4, K2 = (1 + kappa)/4, b = (3 - kappa)/(1 - kappa)).
  * MHD_ERR_ARG for another value. */
 int mhd_set_reconstruction(mhd_ctx* ctx, int recon);
+
+/* State beyond side `side` (0 x-lo, 1 x-hi, 2 y-lo, 3 y-hi, 4 z-lo, 5 z-hi) of patch
+ * `patch`, whose bc must be MHD_BC_INFLOW: w = [rho, vx, vy, vz, p, Bx, By, Bz] (host
+ * array, copied).  Ghost cells beyond the side hold it, with their faces; a ghost cell
+ * beyond several inflow sides takes the first in the order above.  Until it is set, an
+ * inflow side holds rho = 1, p = 1 at rest without field.  MHD_ERR_ARG if the side is not
+ * an inflow side or rho, p are not positive and finite. */
+int mhd_set_inflow(mhd_ctx* ctx, int patch, int side, const double* w);
 
 /* Advance every patch by one van Leer step (Eq. 7, Eq. 8).  dt > 0: that dt for
  * every patch.  dt <= 0: each patch uses cfl * its own CFL limit of its current

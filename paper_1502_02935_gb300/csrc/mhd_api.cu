@@ -275,7 +275,7 @@ static int validate_patch(const mhd_patch_desc& d, std::string& why) {
     if (!(dd[a] > 0.0) || !std::isfinite(dd[a])) { why = "cell size must be positive"; return -1; }
     if (n[a] > 1) {
       const int lo = d.bc[2 * a], hi = d.bc[2 * a + 1];
-      if ((lo != MHD_BC_PERIODIC && lo != MHD_BC_OUTFLOW) || (hi != MHD_BC_PERIODIC && hi != MHD_BC_OUTFLOW)) {
+      if (lo < MHD_BC_PERIODIC || lo > MHD_BC_INFLOW || hi < MHD_BC_PERIODIC || hi > MHD_BC_INFLOW) {
         why = "unknown boundary condition"; return -1;
       }
       if ((lo == MHD_BC_PERIODIC) != (hi == MHD_BC_PERIODIC)) {
@@ -590,6 +590,12 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
       D.act[a] = n[a] > 1;
       D.per[a] = !D.act[a] || d.bc[2 * a] == MHD_BC_PERIODIC;
       D.nface[a] = (D.act[a] && !D.per[a]) ? n[a] + 1 : n[a];
+      for (int h = 0; h < 2; ++h) {
+        const int side = 2 * a + h;
+        if (D.act[a] && d.bc[side] == MHD_BC_INFLOW) D.inflow_mask |= 1 << side;
+        const double w0[8] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+        for (int m = 0; m < 8; ++m) D.inflow_w[side][m] = w0[m];
+      }
       D.g2[a] = D.act[a] ? 2 : 0;
       D.d[a] = dd[a];
       D.inv_d[a] = 1.0 / dd[a];
@@ -714,6 +720,21 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   drop_graph(ctx);  // sources are baked into captured launches
   ctx->w_valid = false;
+  return MHD_OK;
+}
+
+int mhd_set_inflow(mhd_ctx* ctx, int patch, int side, const double* w) {
+  if (!ctx || !w) return MHD_ERR_ARG;
+  if (patch < 0 || patch >= ctx->np || side < 0 || side > 5) return fail(ctx, MHD_ERR_ARG, "no such patch or side");
+  PatchDev& D = ctx->P[patch].dev;
+  if (!(D.inflow_mask & (1 << side))) return fail(ctx, MHD_ERR_ARG, "side is not an inflow boundary");
+  for (int m = 0; m < 8; ++m)
+    if (!std::isfinite(w[m])) return fail(ctx, MHD_ERR_ARG, "inflow state must be finite");
+  if (!(w[0] > 0.0) || !(w[4] > 0.0)) return fail(ctx, MHD_ERR_ARG, "inflow density and pressure must be > 0");
+  for (int m = 0; m < 8; ++m) D.inflow_w[side][m] = w[m];
+  if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
+  drop_graph(ctx);  // the state is part of the captured launches' arguments
+  ctx->w_valid = false;  // W's ghost shell holds it
   return MHD_OK;
 }
 

@@ -63,6 +63,10 @@ struct PatchDev {
   // kappa-scheme coefficients K1 = (1 - kappa)/4, K2 = (1 + kappa)/4, b = (3 - kappa)/(1 - kappa)
   double rK1, rK2, rb;
   float rK1_f, rK2_f, rb_f;
+  // inflow boundaries: bit s of the mask for side s (x-lo, x-hi, y-lo, ...) and the
+  // primitive state [rho, vx, vy, vz, p, Bx, By, Bz] beyond it
+  int inflow_mask;
+  double inflow_w[6][8];
 };
 
 struct SourceDev {
@@ -106,6 +110,18 @@ __device__ __forceinline__ long long sidx(const PatchDev& P, int i, int j, int k
 __device__ __forceinline__ long long qidx(const PatchDev& P, int i, int j, int k) {
   return (long long)(i + P.g2[0]) +
          (long long)P.QX * ((long long)(j + P.g2[1]) + (long long)P.QY * (k + P.g2[2]));
+}
+
+// the inflow side that a (possibly ghost) cell lies beyond, the first in side order, or -1
+__device__ __forceinline__ int inflow_side(const PatchDev& P, int i, int j, int k) {
+  if (!P.inflow_mask) return -1;
+  const int c[3] = {i, j, k};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] < 0 && (P.inflow_mask >> (2 * a) & 1)) return 2 * a;
+    if (c[a] >= P.n[a] && (P.inflow_mask >> (2 * a + 1) & 1)) return 2 * a + 1;
+  }
+  return -1;
 }
 
 __device__ __forceinline__ long long qstride(const PatchDev& P, int a) {
@@ -620,6 +636,22 @@ template <class R>
 __device__ __forceinline__ R prim_point(const PatchDev& P, const double* __restrict__ U,
                                              R* __restrict__ W, int i, int j, int k, bool store,
                                              bool interior) {
+  const int side = inflow_side(P, i, j, k);
+  if (side >= 0) {
+    // a ghost cell beyond an inflow side: the side's fixed state
+    if (store) {
+      const long long QS = P.QS, q = qidx(P, i, j, k);
+      R w[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) w[m] = Ar<R>::from_d(P.inflow_w[side][m]);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) W[m * QS + q] = w[m];
+      W[WEX * QS + q] = cell_emf<R>(w[WVY], w[WVZ], w[WBY], w[WBZ]);
+      W[WEY * QS + q] = cell_emf<R>(w[WVZ], w[WVX], w[WBZ], w[WBX]);
+      W[WEZ * QS + q] = cell_emf<R>(w[WVX], w[WVY], w[WBX], w[WBY]);
+    }
+    return R(INFINITY);
+  }
   const int ci = cmap(P, 0, i), cj = cmap(P, 1, j), ck = cmap(P, 2, k);
   const long long FS = P.FS;
   const long long c = sidx(P, ci, cj, ck);
@@ -703,6 +735,17 @@ __device__ __forceinline__ void flux_core(const Get& get, R bn, R gam, int solve
 template <class R, int D>
 __device__ __forceinline__ R face_bn(const PatchDev& P, const double* __restrict__ Ub, int i, int j, int k) {
   const int c3[3] = {i, j, k};
+  if (P.inflow_mask) {
+    // the face of a ghost cell beyond an inflow side (along D the face index stays in [0, n])
+    int side = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == D || side >= 0) continue;
+      if (c3[a] < 0 && (P.inflow_mask >> (2 * a) & 1)) side = 2 * a;
+      else if (c3[a] >= P.n[a] && (P.inflow_mask >> (2 * a + 1) & 1)) side = 2 * a + 1;
+    }
+    if (side >= 0) return Ar<R>::from_d(P.inflow_w[side][5 + D]);
+  }
   int s3[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) s3[a] = (a == D) ? fmap(P, a, c3[a]) : cmap(P, a, c3[a]);

@@ -71,7 +71,8 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_cfl_dt_noalloc", "mhd_autotune", "mhd_set_wait_limit", "mhd_set_thermal",
            "mhd_thermal_stats", "mhd_thermal_cells", "mhd_surrogate_harvest", "mhd_surrogate_train",
            "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
-           "mhd_mlp_forward_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction"]
+           "mhd_mlp_forward_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
+           "mhd_set_inflow"]
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics
 RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
@@ -108,6 +109,7 @@ def lib():
     L.mhd_riemann_flux.argtypes = [ip, ip, vp, vp, vp, C.c_double, ip, vp, vp]
     L.mhd_set_riemann.argtypes = [vp, ip]
     L.mhd_set_reconstruction.argtypes = [vp, ip]
+    L.mhd_set_inflow.argtypes = [vp, ip, ip, dp]
     L.mhd_set_profiling.argtypes = [vp, ip]
     L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
     L.mhd_cfl_dt_noalloc.argtypes = [C.POINTER(PatchDesc), C.c_double, vp, vp, vp, vp]
@@ -186,6 +188,11 @@ class Grid:
     def set_riemann(self, solver: str):
         """"hlld" (default), "hllc" or "hll" for the following steps."""
         self._check(self.L.mhd_set_riemann(self.h, RIEMANN[solver]), "mhd_set_riemann")
+
+    def set_inflow(self, patch: int, side: int, w):
+        """Primitive state [rho, vx, vy, vz, p, Bx, By, Bz] beyond an inflow side (bc 2)."""
+        arr = (C.c_double * 8)(*[float(v) for v in w])
+        self._check(self.L.mhd_set_inflow(self.h, int(patch), int(side), arr), "mhd_set_inflow")
 
     def set_reconstruction(self, recon: str):
         """"kappa_third" (default), "kappa_zero" or "kappa_upwind" for the following steps."""
