@@ -475,10 +475,12 @@ def run_table(args):
     stream = torch.cuda.Stream()
 
     def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None, riemann=None,
-                 recon=None):
+                 recon=None, inflow=None):
         sts = states if isinstance(states, list) else [states]
         g = mhd.Grid(sts if len(sts) > 1 else sts[0], precision=precision, cfl=CFL, flags=flags,
                      stream=stream.cuda_stream)
+        for side, w in (inflow or {}).items():
+            g.set_inflow(0, side, w)
         if riemann:
             g.set_riemann(riemann)
         if recon:
@@ -496,23 +498,27 @@ def run_table(args):
         g.close()
         return sum(st.geom.ncell for st in sts) * steps / (ms / 1e3)
 
-    def oracle_rate(states, threads, steps, src=None, thermal=None, cfl=CFL):
+    def oracle_rate(states, threads, steps, src=None, thermal=None, cfl=CFL, inflow=None):
         oracle.set_threads(threads)
         sts = states if isinstance(states, list) else [states]
         t0 = time.perf_counter()
         for st in sts:
             for _ in range(steps):
-                dt = oracle.cfl_dt(st, cfl, source=src)
-                st = oracle.step(st, dt, source=src)
+                dt = oracle.cfl_dt(st, cfl, source=src, inflow=inflow)
+                st = oracle.step(st, dt, source=src, inflow=inflow)
                 if thermal:
                     st, _ = oracle.thermal_apply(st, dt, thermal)
         el = time.perf_counter() - t0
         return sum(st.geom.ncell for st in sts) * steps / el, el
 
-    def gpu_to_time(st, precision, cfl, t_end, recon=None):
+    def gpu_to_time(st, precision, cfl, t_end, recon=None, src=None, inflow=None):
         g = mhd.Grid(st, precision=precision, cfl=cfl, stream=stream.cuda_stream)
         if recon:
             g.set_reconstruction(recon)
+        if src:
+            g.set_sources(**src)
+        for side, w in (inflow or {}).items():
+            g.set_inflow(0, side, w)
         t, n = 0.0, 0
         while t < t_end * (1 - 1e-14):
             dt = min(g.cfl_dt(), t_end - t)
@@ -643,6 +649,24 @@ def run_table(args):
                     "l1_at_t015_256sq": {"fp64": l1(g64, ref), "mixed": l1(gmx, ref)}, "steps": n,
                     "oracle_steps": nref})
         table["Rotor 2D 512^2 (kappa = 1/3, 0, -1)"] = rot
+    if want("bow"):
+        # bow shock (Section 3.4): inflow at the left, Gaussian well, 1D; to the paper's last
+        # time t = 0.375
+        st, src, inflow = inputs.bow_shock(400)
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        ref, nref = oracle.run(st, CFL, 0.375, source=src, inflow=inflow)
+        el = time.perf_counter() - t0
+        g64, n = gpu_to_time(st, "fp64", CFL, 0.375, src=src, inflow=inflow)
+        gmx, _ = gpu_to_time(st, "mixed", CFL, 0.375, src=src, inflow=inflow)
+        u = ref.U[1, 0, 0] / ref.U[0, 0, 0]
+        table["Bow shock 1D 400 cells, t = 0.375"] = {
+            "gpu_fp64": gpu_rate(st, "fp64", 500, src=src, inflow=inflow),
+            "gpu_mixed": gpu_rate(st, "mixed", 500, src=src, inflow=inflow),
+            "gpu_note": "400 cells: launch-latency-bound (graph replay)",
+            "oracle_1core": 400 * nref / el, "steps": n, "oracle_steps": nref,
+            "shock_x_oracle": float(st.geom.centres()[0][int(np.argmax(-np.diff(u)))]),
+            "l1_vs_oracle": {"fp64": l1(g64, ref), "mixed": l1(gmx, ref)}}
     print(json.dumps({"table": table, "host_cores": ncores, "unit": "zone-updates/s"}), flush=True)
     return 0
 
@@ -663,7 +687,7 @@ def main():
     ap.add_argument("--table", action="store_true",
                     help="every workload configuration, GPU and oracle side by side (minutes; no bench line)")
     ap.add_argument("--rows", default="",
-                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas,rotor (default all)")
+                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas,rotor,bow (default all)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.table:
