@@ -75,6 +75,9 @@ def lib():
             L.orc_run.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp,
                                   C.c_double, C.c_double, C.c_int]
             L.orc_run.restype = C.c_int
+            L.orc_step_scalars.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp, C.c_int, dp,
+                                           dp, C.c_double]
+            L.orc_step_scalars.restype = C.c_int
             L.orc_hlld_batch.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_riemann_batch.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_reconstruct_1d.argtypes = [C.c_int, dp, dp, dp]
@@ -163,6 +166,24 @@ def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str
         if floored is not None:
             floored.append(int(n))
     return st.replace(U=U, Bx=Bx, By=By, Bz=Bz)
+
+
+def step_scalars(st, S, dt: float, source=None, riemann: str = "hlld", recon: str = "kappa_third", inflow=None,
+                 inflow_x=None):
+    """One van Leer step that also advects passive scalars: S is rho X, shape
+    (ns, nz, ny, nx); ``inflow_x`` = {side: [X_0, ..., X_ns-1]} beyond inflow sides.
+    Returns (State, S)."""
+    U, Bx, By, Bz = _copy_state(st)
+    S = np.ascontiguousarray(S, dtype=np.float64).copy()
+    ns = S.shape[0]
+    p, s = patch_struct(st.geom, riemann, recon, inflow), source_struct(source)
+    ix = np.zeros(6 * max(ns, 1))
+    for side, xs in (inflow_x or {}).items():
+        ix[int(side) * ns:(int(side) + 1) * ns] = xs
+    n = lib().orc_step_scalars(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), ns, _p(S), _p(ix), float(dt))
+    if n < 0:
+        raise ValueError("orc_step_scalars rejected its arguments")
+    return st.replace(U=U, Bx=Bx, By=By, Bz=Bz), S
 
 
 def cfl_dt(st, cfl: float, source=None, inflow=None) -> float:

@@ -68,6 +68,16 @@ typedef struct {
 int orc_step(const orc_patch* p, const orc_source* s, double* U, double* Bx,
              double* By, double* Bz, double dt);
 
+/* One step of orc_step that also advects ns passive scalars (multi-species gas carried by
+ * the flow): S holds the conserved rho X_s, [ns][nz][ny][nx], updated in place.  Their
+ * face flux is the Riemann mass flux times the upwind X (X_L where the mass flux is >= 0,
+ * else X_R), X = (rho X)/rho reconstructed like the primitives (donor cell in the
+ * predictor, the patch's kappa-scheme in the corrector, without the positivity fallback).
+ * inflow_x[side * ns + s] is X beyond an inflow side (may be NULL: 0).  Returns as
+ * orc_step. */
+int orc_step_scalars(const orc_patch* p, const orc_source* s, double* U, double* Bx, double* By,
+                     double* Bz, int ns, double* S, const double* inflow_x, double dt);
+
 /* cfl * min over interior cells and active axes of d/(|v_d| + c_f,d), from the
  * recovered primitives (with the floors of s when s is not NULL). */
 double orc_cfl_dt(const orc_patch* p, const orc_source* s, const double* U, const double* Bx,
