@@ -174,6 +174,25 @@ int mhd_set_reconstruction(mhd_ctx* ctx, int recon);
  * an inflow side or rho, p are not positive and finite. */
 int mhd_set_inflow(mhd_ctx* ctx, int patch, int side, const double* w);
 
+/* Passive scalars: several gas components carried by the flow.  Each is a conserved
+ * rho X advected with the Riemann mass flux of the step and the upwind X at each face
+ * (X_L where the mass flux is >= 0, else X_R), X = (rho X)/rho reconstructed like the
+ * primitives (donor cell in the predictor, the patch's kappa-scheme in the corrector,
+ * without the positivity fallback), accumulated in FP64; they do not act on the flow. */
+#define MHD_MAX_SCALARS 8
+
+/* n scalars (0 <= n <= MHD_MAX_SCALARS; 0 removes them) on every patch, all rho X = 0.
+ * MHD_ERR_STATE on a context made with MHD_FLAG_PERSISTENT (that step carries none). */
+int mhd_set_scalars(mhd_ctx* ctx, int n);
+
+/* rho X of one patch, dense [n][nz][ny][nx] (access as mhd_set_state / mhd_get_state).
+ * MHD_ERR_STATE without scalars.  The get synchronises. */
+int mhd_set_scalar_state(mhd_ctx* ctx, int patch, const double* S, int on_device);
+int mhd_get_scalar_state(mhd_ctx* ctx, int patch, double* S_out, int on_device);
+
+/* X (n values, host array) beyond an inflow side of a patch (default 0). */
+int mhd_set_inflow_scalars(mhd_ctx* ctx, int patch, int side, const double* X);
+
 /* Advance every patch by one van Leer step (Eq. 7, Eq. 8).  dt > 0: that dt for
  * every patch.  dt <= 0: each patch uses cfl * its own CFL limit of its current
  * state, computed on the device (no host synchronisation).  Asynchronous.
@@ -267,12 +286,12 @@ int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long l
  * per kernel class: 0 recovery+CFL, 1-3 donor-cell HLLD fluxes x/y/z, 4-6 kappa-scheme
  * HLLD fluxes x/y/z, 7 corner EMFs, 8 update, 9 standalone CFL, 10 persistent step,
  * 11 thermal source, 12 end-of-step floors, 13 ghost W fill, 14 corner EMFs fused with the
- * update (patches with three active axes; they launch no class 7 or 8 kernel).  Switching on
- * or off clears the totals. */
+ * update (patches with three active axes; they launch no class 7 or 8 kernel), 15 passive
+ * scalars.  Switching on or off clears the totals. */
 int mhd_set_profiling(mhd_ctx* ctx, int on);
 
 /* Totals since profiling was switched on: ms[c] milliseconds and launches[c] launches of
- * class c, for c < n (n >= 15).  Synchronises. */
+ * class c, for c < n (n >= 16).  Synchronises. */
 int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
 
 /* Autotuner of the persistent batched step (context made with MHD_FLAG_PERSISTENT): times

@@ -35,6 +35,8 @@ struct PatchHost {
   long long ncell = 0, dense = 0;
   void* state = nullptr;
   void* scratch = nullptr;
+  void* sstate = nullptr;   // passive scalars: 2 x ns FP64 fields
+  void* sscratch = nullptr; // their X on the padded box
 };
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -130,6 +132,22 @@ __global__ void k_unpack(PatchDev P, const double* __restrict__ u, const double*
     const double* src = (f < 5 ? u : b) + off;
     double* dst = U + f * P.FS + sidx(P, 0, j, k);
     for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
+  }
+}
+
+// passive scalars between the dense layout [ns][nz][ny][nx] and the state; one CTA per row
+__global__ void k_scalars_io(PatchDev P, double* __restrict__ dense, int to_state) {
+  const long long rows = (long long)P.ns * P.n[2] * P.n[1];
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int m = (int)(r / ((long long)P.n[2] * P.n[1]));
+    const long long rr = r - (long long)m * P.n[2] * P.n[1];
+    const int k = (int)(rr / P.n[1]), j = (int)(rr - (long long)k * P.n[1]);
+    double* st = P.Sn + m * P.FS + sidx(P, 0, j, k);
+    double* de = dense + r * P.n[0];
+    if (to_state)
+      for (int i = threadIdx.x; i < P.n[0]; i += blockDim.x) st[i] = de[i];
+    else
+      for (int i = threadIdx.x; i < P.n[0]; i += blockDim.x) de[i] = st[i];
   }
 }
 
@@ -243,6 +261,8 @@ static void free_ctx(mhd_ctx* ctx) {
   for (auto& p : ctx->P) {
     if (p.state) cudaFree(p.state);
     if (p.scratch) cudaFree(p.scratch);
+    if (p.sstate) cudaFree(p.sstate);
+    if (p.sscratch) cudaFree(p.sscratch);
   }
   if (ctx->therm_stats) cudaFree(ctx->therm_stats);
   if (ctx->mlp) cudaFree(ctx->mlp);
@@ -328,6 +348,12 @@ static void set_parity(mhd_ctx* ctx, int parity) {
     double* b = a + 8 * H.dev.FS;
     H.dev.Un = parity ? b : a;
     H.dev.Uh = parity ? a : b;
+    if (H.sstate) {
+      double* sa = (double*)H.sstate;
+      double* sb = sa + (long long)H.dev.ns * H.dev.FS;
+      H.dev.Sn = parity ? sb : sa;
+      H.dev.Sh = parity ? sa : sb;
+    }
   }
 }
 
@@ -735,6 +761,89 @@ int mhd_set_inflow(mhd_ctx* ctx, int patch, int side, const double* w) {
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   drop_graph(ctx);  // the state is part of the captured launches' arguments
   ctx->w_valid = false;  // W's ghost shell holds it
+  return MHD_OK;
+}
+
+int mhd_set_scalars(mhd_ctx* ctx, int n) {
+  if (!ctx) return MHD_ERR_ARG;
+  if (n < 0 || n > MHD_MAX_SCALARS) return fail(ctx, MHD_ERR_ARG, "scalar count out of range");
+  if (ctx->persistent && n > 0) return fail(ctx, MHD_ERR_STATE, "the persistent step carries no scalars");
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& H : ctx->P) {
+    if (H.sstate) cudaFree(H.sstate);
+    if (H.sscratch) cudaFree(H.sscratch);
+    H.sstate = H.sscratch = nullptr;
+    H.dev.ns = 0;
+    H.dev.Sn = H.dev.Sh = nullptr;
+    H.dev.X = nullptr;
+    if (n == 0) continue;
+    const size_t sb = sizeof(double) * 2 * (size_t)n * (size_t)H.dev.FS;
+    const size_t xb = ctx->be.scratch_elem * (size_t)n * (size_t)H.dev.QS;
+    if (cudaMalloc(&H.sstate, sb) != cudaSuccess) return fail(ctx, MHD_ERR_NOMEM, "scalar state");
+    if (cudaMalloc(&H.sscratch, xb) != cudaSuccess) return fail(ctx, MHD_ERR_NOMEM, "scalar scratch");
+    CK(cudaMemset(H.sstate, 0, sb));
+    CK(cudaMemset(H.sscratch, 0, xb));
+    H.dev.ns = n;
+    H.dev.X = H.sscratch;
+  }
+  set_parity(ctx, ctx->parity);
+  drop_graph(ctx);
+  return MHD_OK;
+}
+
+int mhd_set_scalar_state(mhd_ctx* ctx, int patch, const double* S, int on_device) {
+  if (!ctx || !S || patch < 0 || patch >= ctx->np) return MHD_ERR_ARG;
+  PatchHost& H = ctx->P[patch];
+  if (H.dev.ns == 0) return fail(ctx, MHD_ERR_STATE, "no scalars (mhd_set_scalars)");
+  const size_t bytes = sizeof(double) * (size_t)H.dev.ns * (size_t)H.ncell;
+  const double* src = S;
+  if (!on_device) {
+    src = (const double*)mapped_host(S);
+    if (!src) {
+      CK(cudaMemcpyAsync(ctx->staging, S, bytes, cudaMemcpyHostToDevice, ctx->stream));
+      src = ctx->staging;
+    }
+  }
+  const long long rows = (long long)H.dev.ns * H.dev.n[2] * H.dev.n[1];
+  k_scalars_io<<<grid_rows(rows), 256, 0, ctx->stream>>>(H.dev, (double*)src, 1);
+  ctx->launches += 1;
+  CK(cudaGetLastError());
+  return MHD_OK;
+}
+
+int mhd_get_scalar_state(mhd_ctx* ctx, int patch, double* S_out, int on_device) {
+  if (!ctx || !S_out || patch < 0 || patch >= ctx->np) return MHD_ERR_ARG;
+  PatchHost& H = ctx->P[patch];
+  if (H.dev.ns == 0) return fail(ctx, MHD_ERR_STATE, "no scalars (mhd_set_scalars)");
+  const size_t bytes = sizeof(double) * (size_t)H.dev.ns * (size_t)H.ncell;
+  double* dst = S_out;
+  bool staged = false;
+  if (!on_device) {
+    dst = (double*)mapped_host(S_out);
+    if (!dst) {
+      dst = ctx->staging;
+      staged = true;
+    }
+  }
+  const long long rows = (long long)H.dev.ns * H.dev.n[2] * H.dev.n[1];
+  k_scalars_io<<<grid_rows(rows), 256, 0, ctx->stream>>>(H.dev, dst, 0);
+  ctx->launches += 1;
+  CK(cudaGetLastError());
+  if (staged) CK(cudaMemcpyAsync(S_out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return read_error_word(ctx);
+}
+
+int mhd_set_inflow_scalars(mhd_ctx* ctx, int patch, int side, const double* X) {
+  if (!ctx || !X) return MHD_ERR_ARG;
+  if (patch < 0 || patch >= ctx->np || side < 0 || side > 5) return fail(ctx, MHD_ERR_ARG, "no such patch or side");
+  PatchDev& D = ctx->P[patch].dev;
+  if (!(D.inflow_mask & (1 << side))) return fail(ctx, MHD_ERR_ARG, "side is not an inflow boundary");
+  if (D.ns == 0) return fail(ctx, MHD_ERR_STATE, "no scalars (mhd_set_scalars)");
+  for (int m = 0; m < D.ns; ++m) {
+    if (!std::isfinite(X[m])) return fail(ctx, MHD_ERR_ARG, "inflow scalars must be finite");
+    D.inflow_x[side][m] = X[m];
+  }
+  drop_graph(ctx);
   return MHD_OK;
 }
 

@@ -67,6 +67,14 @@ struct PatchDev {
   // primitive state [rho, vx, vy, vz, p, Bx, By, Bz] beyond it
   int inflow_mask;
   double inflow_w[6][8];
+  // passive scalars (ns of them, 0 when off): conserved rho X in two FP64 buffers (base and
+  // half-step, swapped with Un/Uh), X = (rho X)/rho of the stage's input on the padded box
+  // in the bulk type, and X beyond each inflow side
+  int ns;
+  double* Sn;
+  double* Sh;
+  void* X;
+  double inflow_x[6][8];
 };
 
 struct SourceDev {
@@ -660,6 +668,62 @@ __device__ __forceinline__ R prim_point(const PatchDev& P, const double* __restr
   const double sbz = U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k))] + U[BZF * FS + sidx(P, ci, cj, fmap(P, 2, k + 1))];
   return prim_core<R>(P, U[c], U[MX * FS + c], U[MY * FS + c], U[MZ * FS + c], U[EN * FS + c], sbx, sby, sbz,
                       W, qidx(P, i, j, k), store, interior);
+}
+
+// --------------------------------------------------------- passive scalars --
+// X_s = (rho X_s)/rho at a (possibly ghost) cell of the padded box: beyond an inflow side
+// the side's X, else from the cell the boundary maps give.
+template <class R>
+__device__ __forceinline__ void scalar_prim_point(const PatchDev& P, const double* __restrict__ U,
+                                                  const double* __restrict__ S, R* __restrict__ X, int i, int j,
+                                                  int k) {
+  const long long q = qidx(P, i, j, k), QS = P.QS;
+  const int side = inflow_side(P, i, j, k);
+  if (side >= 0) {
+    for (int m = 0; m < P.ns; ++m) X[m * QS + q] = Ar<R>::from_d(P.inflow_x[side][m]);
+    return;
+  }
+  const long long c = sidx(P, cmap(P, 0, i), cmap(P, 1, j), cmap(P, 2, k));
+  const double irho = 1.0 / U[c];
+  for (int m = 0; m < P.ns; ++m) X[m * QS + q] = Ar<R>::from_d(S[m * P.FS + c] * irho);
+}
+
+// rho X_out = rho X_base - h sum_d [F(c + 1/2) - F(c - 1/2)] / d at interior cell (i, j, k):
+// F = (Riemann mass flux of the stage) * (X_L if it is >= 0 else X_R), X_L and X_R the
+// donor-cell (ORDER 1) or kappa-scheme (ORDER 2) states of X at the face.
+template <class R, int ORDER>
+__device__ __forceinline__ void scalar_update_point(const PatchDev& P, const double* __restrict__ Sb,
+                                                    double* __restrict__ So, const R* __restrict__ X, R h, int i,
+                                                    int j, int k) {
+  const long long s = sidx(P, i, j, k), q = qidx(P, i, j, k), QS = P.QS;
+  R kap[3];
+  Gam<R>::kappa(P, kap[0], kap[1], kap[2]);
+  for (int m = 0; m < P.ns; ++m) {
+    const R* Xm = X + m * QS;
+    R div = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (!P.act[d]) continue;
+      const long long st = qstride(P, d);
+      const R* mflux = (const R*)P.F[d];  // component 0: the mass flux
+      R fx[2];
+#pragma unroll
+      for (int up = 0; up < 2; ++up) {
+        const long long f = q + up * st;  // face f - 1/2 along d
+        R xl, xr;
+        if (ORDER == 1) {
+          xl = Xm[f - st];
+          xr = Xm[f];
+        } else {
+          kappa_face<R>(Xm[f - 2 * st], Xm[f - st], Xm[f], Xm[f + st], kap[0], kap[1], kap[2], xl, xr);
+        }
+        const R mf = mflux[f];
+        fx[up] = mf * (mf >= R(0) ? xl : xr);
+      }
+      div += (fx[1] - fx[0]) * Gam<R>::inv(P, d);
+    }
+    So[m * P.FS + s] = Sb[m * P.FS + s] - Ar<R>::to_d(h * div);
+  }
 }
 
 // ----------------------------------------------------------- end-of-step floors --

@@ -332,6 +332,31 @@ __global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* _
   }
 }
 
+// X of the passive scalars over the padded box, from the stage's input state
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_scalar_prim(PatchDev P, const double* __restrict__ U,
+                                                        const double* __restrict__ S, Range rg) {
+  int i, j, k;
+  if (!range_point(rg, i, j, k)) return;
+  scalar_prim_point<R>(P, U, S, (R*)P.X, i, j, k);
+}
+
+// the stage's scalar update over the interior cells; dt as the stage's update kernel takes it
+template <class R, int ORDER>
+__global__ void __launch_bounds__(kBlock) k_scalar_update(PatchDev P, const double* __restrict__ Sb,
+                                                          double* __restrict__ So, Range rg, StageArgs a) {
+  __shared__ R sh;
+  if (threadIdx.x == 0) {
+    const double dt = a.stage == 0 ? (a.dt_host > 0.0 ? a.dt_host : a.cfl * __longlong_as_double((long long)*P.cfl_min))
+                                   : *P.dt_used;
+    sh = Ar<R>::from_d(a.stage == 0 ? 0.5 * dt : dt);
+  }
+  __syncthreads();
+  int i, j, k;
+  if (!range_point(rg, i, j, k)) return;
+  scalar_update_point<R, ORDER>(P, Sb, So, (const R*)P.X, sh, i, j, k);
+}
+
 // W of the ghost shell from the interior W and U of the current state (see ghost_point).
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_ghost(PatchDev P, const double* __restrict__ U) {
@@ -483,6 +508,15 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     G.W = a.stage == 0 ? P.W2 : P.W;
   }
   int nl = issue_fluxes<R>(Q, a, Usrc, s, prof, !fused);
+  if (P.ns > 0) {
+    // passive scalars, before the update overwrites the corrector's input state in Uh
+    ProfScope ps(prof, KC_SCALARS, s);
+    const Range pr = prim_range(P), ir = interior_range(P);
+    k_scalar_prim<R><<<grid_of(pr), kBlock, 0, s>>>(P, Usrc, a.stage == 0 ? P.Sn : P.Sh, pr);
+    if (a.stage == 0) k_scalar_update<R, 1><<<grid_of(ir), kBlock, 0, s>>>(P, P.Sn, P.Sh, ir, a);
+    else k_scalar_update<R, 2><<<grid_of(ir), kBlock, 0, s>>>(P, P.Sn, P.Sh, ir, a);
+    nl += 2;
+  }
   if (fused) {
     ProfScope ps(prof, KC_EMF_UPDATE, s);
     // planes per CTA: 8, halved (down to 2) while the grid would be under two waves of

@@ -72,7 +72,8 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_thermal_stats", "mhd_thermal_cells", "mhd_surrogate_harvest", "mhd_surrogate_train",
            "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
            "mhd_mlp_forward_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
-           "mhd_set_inflow"]
+           "mhd_set_inflow", "mhd_set_scalars", "mhd_set_scalar_state", "mhd_get_scalar_state",
+           "mhd_set_inflow_scalars"]
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics
 RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
@@ -110,6 +111,10 @@ def lib():
     L.mhd_set_riemann.argtypes = [vp, ip]
     L.mhd_set_reconstruction.argtypes = [vp, ip]
     L.mhd_set_inflow.argtypes = [vp, ip, ip, dp]
+    L.mhd_set_scalars.argtypes = [vp, ip]
+    L.mhd_set_scalar_state.argtypes = [vp, ip, vp, ip]
+    L.mhd_get_scalar_state.argtypes = [vp, ip, vp, ip]
+    L.mhd_set_inflow_scalars.argtypes = [vp, ip, ip, dp]
     L.mhd_set_profiling.argtypes = [vp, ip]
     L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
     L.mhd_cfl_dt_noalloc.argtypes = [C.POINTER(PatchDesc), C.c_double, vp, vp, vp, vp]
@@ -194,6 +199,27 @@ class Grid:
         arr = (C.c_double * 8)(*[float(v) for v in w])
         self._check(self.L.mhd_set_inflow(self.h, int(patch), int(side), arr), "mhd_set_inflow")
 
+    def set_scalars(self, n: int):
+        """n passive scalars (rho X, all zero) on every patch; 0 removes them."""
+        self._check(self.L.mhd_set_scalars(self.h, int(n)), "mhd_set_scalars")
+        self.n_scalars = int(n)
+
+    def set_scalar_state(self, patch: int, S):
+        """rho X of a patch, shape (n, nz, ny, nx)."""
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        self._check(self.L.mhd_set_scalar_state(self.h, patch, S.ctypes.data, 0), "mhd_set_scalar_state")
+        self.sync()
+
+    def get_scalar_state(self, patch: int) -> np.ndarray:
+        g = self.geoms[patch]
+        out = np.empty((self.n_scalars, g.nz, g.ny, g.nx))
+        self._check(self.L.mhd_get_scalar_state(self.h, patch, out.ctypes.data, 0), "mhd_get_scalar_state")
+        return out
+
+    def set_inflow_scalars(self, patch: int, side: int, xs):
+        arr = (C.c_double * len(xs))(*[float(v) for v in xs])
+        self._check(self.L.mhd_set_inflow_scalars(self.h, int(patch), int(side), arr), "mhd_set_inflow_scalars")
+
     def set_reconstruction(self, recon: str):
         """"kappa_third" (default), "kappa_zero" or "kappa_upwind" for the following steps."""
         self._check(self.L.mhd_set_reconstruction(self.h, RECON[recon]), "mhd_set_reconstruction")
@@ -248,7 +274,7 @@ class Grid:
                 "floored": int(m.floored)}
 
     KERNEL_CLASSES = ["recovery", "flux1_x", "flux1_y", "flux1_z", "flux2_x", "flux2_y", "flux2_z",
-                      "emf", "update", "cfl", "persistent", "thermal", "floor", "ghost", "emf_update"]
+                      "emf", "update", "cfl", "persistent", "thermal", "floor", "ghost", "emf_update", "scalars"]
 
     def set_thermal(self, mode, gamma_heat=2e-26, z=0.02, rate_unit=7.13e-31, cap=0.1, nh_per_rho=0.76,
                     t_per_pr=72.7):
