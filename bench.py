@@ -649,6 +649,32 @@ def run_table(args):
                     "l1_at_t015_256sq": {"fp64": l1(g64, ref), "mixed": l1(gmx, ref)}, "steps": n,
                     "oracle_steps": nref})
         table["Rotor 2D 512^2 (kappa = 1/3, 0, -1)"] = rot
+    if want("scalars"):
+        # passive scalars (several gas components carried by the flow) on the 256^3 box:
+        # the cost of 0, 1, 4 and 8 scalars on the mixed path
+        st = inputs.turbulence(256, seed=SEED)
+        row = {}
+        for ns in (0, 1, 4, 8):
+            g = mhd.Grid(st, precision="mixed", cfl=CFL, flags=mhd.FLAG_GRAPH, stream=stream.cuda_stream)
+            if ns:
+                g.set_scalars(ns)
+                g.set_scalar_state(0, np.broadcast_to(st.U[0] * 0.5, (ns,) + st.U[0].shape))
+            for _ in range(3):
+                g.step(-1.0)
+            torch.cuda.synchronize()
+            ms = timed_steps(g, 10, stream)
+            g.close()
+            row[f"gpu_mixed_{ns}_scalars"] = st.geom.ncell * 10 / (ms / 1e3)
+        small = inputs.turbulence(64, seed=SEED)
+        oracle.set_threads(ncores)
+        S = np.broadcast_to(small.U[0] * 0.5, (4,) + small.U[0].shape)
+        t0 = time.perf_counter()
+        ref = small
+        for _ in range(3):
+            ref, S = oracle.step_scalars(ref, S, oracle.cfl_dt(ref, CFL))
+        row["oracle_all_4_scalars"] = small.geom.ncell * 3 / (time.perf_counter() - t0)
+        row["oracle_sample"] = "64^3, 3 steps, 4 scalars"
+        table["turbulence 256^3 with passive scalars"] = row
     if want("bow"):
         # bow shock (Section 3.4): inflow at the left, Gaussian well, 1D; to the paper's last
         # time t = 0.375
@@ -687,7 +713,7 @@ def main():
     ap.add_argument("--table", action="store_true",
                     help="every workload configuration, GPU and oracle side by side (minutes; no bench line)")
     ap.add_argument("--rows", default="",
-                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas,rotor,bow (default all)")
+                    help="with --table: comma-separated subset of C1,C2,C3,C4,C5,gas,rotor,bow,scalars (default all)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.table:

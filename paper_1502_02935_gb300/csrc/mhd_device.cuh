@@ -684,8 +684,9 @@ __device__ __forceinline__ void scalar_prim_point(const PatchDev& P, const doubl
     return;
   }
   const long long c = sidx(P, cmap(P, 0, i), cmap(P, 1, j), cmap(P, 2, k));
-  const double irho = 1.0 / U[c];
-  for (int m = 0; m < P.ns; ++m) X[m * QS + q] = Ar<R>::from_d(S[m * P.FS + c] * irho);
+  // X is stored in the bulk type: the mixed path divides in FP32 (no FP64 division)
+  const R irho = Ar<R>::rcp(Ar<R>::from_d(U[c]));
+  for (int m = 0; m < P.ns; ++m) X[m * QS + q] = Ar<R>::from_d(S[m * P.FS + c]) * irho;
 }
 
 // rho X_out = rho X_base - h sum_d [F(c + 1/2) - F(c - 1/2)] / d at interior cell (i, j, k):
