@@ -769,25 +769,35 @@ int mhd_set_scalars(mhd_ctx* ctx, int n) {
   if (n < 0 || n > MHD_MAX_SCALARS) return fail(ctx, MHD_ERR_ARG, "scalar count out of range");
   if (ctx->persistent && n > 0) return fail(ctx, MHD_ERR_STATE, "the persistent step carries no scalars");
   CK(cudaStreamSynchronize(ctx->stream));
+  auto release = [&]() {
+    for (auto& H : ctx->P) {
+      if (H.sstate) cudaFree(H.sstate);
+      if (H.sscratch) cudaFree(H.sscratch);
+      H.sstate = H.sscratch = nullptr;
+      H.dev.ns = 0;
+      H.dev.Sn = H.dev.Sh = nullptr;
+      H.dev.X = nullptr;
+    }
+  };
+  release();
+  drop_graph(ctx);
+  if (n == 0) return MHD_OK;
   for (auto& H : ctx->P) {
-    if (H.sstate) cudaFree(H.sstate);
-    if (H.sscratch) cudaFree(H.sscratch);
-    H.sstate = H.sscratch = nullptr;
-    H.dev.ns = 0;
-    H.dev.Sn = H.dev.Sh = nullptr;
-    H.dev.X = nullptr;
-    if (n == 0) continue;
     const size_t sb = sizeof(double) * 2 * (size_t)n * (size_t)H.dev.FS;
     const size_t xb = ctx->be.scratch_elem * (size_t)n * (size_t)H.dev.QS;
-    if (cudaMalloc(&H.sstate, sb) != cudaSuccess) return fail(ctx, MHD_ERR_NOMEM, "scalar state");
-    if (cudaMalloc(&H.sscratch, xb) != cudaSuccess) return fail(ctx, MHD_ERR_NOMEM, "scalar scratch");
-    CK(cudaMemset(H.sstate, 0, sb));
-    CK(cudaMemset(H.sscratch, 0, xb));
+    if (cudaMalloc(&H.sstate, sb) != cudaSuccess || cudaMalloc(&H.sscratch, xb) != cudaSuccess ||
+        cudaMemsetAsync(H.sstate, 0, sb, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(H.sscratch, 0, xb, ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      release();  // all patches or none carry scalars
+      return fail(ctx, MHD_ERR_NOMEM, "scalar buffers");
+    }
+  }
+  for (auto& H : ctx->P) {
     H.dev.ns = n;
     H.dev.X = H.sscratch;
   }
   set_parity(ctx, ctx->parity);
-  drop_graph(ctx);
   return MHD_OK;
 }
 
