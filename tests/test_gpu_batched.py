@@ -122,3 +122,24 @@ def test_batch_with_inflow_solvers_and_scalars_matches_oracle(precision, tol):
         err = np.max(np.abs(Sg - Sref)) / np.max(np.abs(Sref))
         assert err <= (1e-12 if precision == "fp64" else 1e-6), (p, err)
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_carries_solver_and_reconstruction(precision):
+    """The persistent step reads the Riemann solver and the kappa-scheme coefficients from its
+    patch tables: with HLLC and kappa = 0 it matches the per-phase launches (to the rounding
+    of differently compiled kernels)."""
+    sts = [inputs.turbulence((24, 20, 12), seed=31, b0=0.0), inputs.blast(16, (0.3, 0.6, 0.45), (0.6, 0.0, 0.8))]
+    a = mhd.Grid(sts, precision=precision, cfl=0.4)
+    b = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_PERSISTENT | mhd.FLAG_GRAPH)
+    for g in (a, b):
+        g.set_riemann("hllc")
+        g.set_reconstruction("kappa_zero")
+    for _ in range(3):
+        a.step(-1.0)
+        b.step(-1.0)
+    tol = 3 * FP64_TOL if precision == "fp64" else 1e-6
+    for p, (sa, sb) in enumerate(zip(_all_states(a, len(sts)), _all_states(b, len(sts)))):
+        assert_close(sb, sa, tol, f"patch {p}", normalized=(precision == "mixed"))
+    a.close()
+    b.close()
