@@ -400,3 +400,78 @@ def test_restart_is_bitwise(precision):
         c.close()
         for f in ("U", "Bx", "By", "Bz"):
             assert np.array_equal(getattr(sa, f), getattr(sc, f)), (flags, f)
+
+
+def _window(st: inputs.State, c, h):
+    """(2h+1)^3 window of a non-periodic state around interior cell c (at least h + 1 cells
+    from every boundary), as an outflow patch at the same coordinates."""
+    g = st.geom
+    sl = [slice(c[a] - h, c[a] + h + 1) for a in range(3)]
+    fl = [slice(c[a] - h, c[a] + h + 2) for a in range(3)]
+    U = st.U[:, sl[2], sl[1], sl[0]]
+    Bx = st.Bx[sl[2], sl[1], fl[0]]
+    By = st.By[sl[2], fl[1], sl[0]]
+    Bz = st.Bz[fl[2], sl[1], sl[0]]
+    lo = (g.x0 + (c[0] - h) * g.dx, g.y0 + (c[1] - h) * g.dy, g.z0 + (c[2] - h) * g.dz)
+    gs = inputs.Geom(2 * h + 1, 2 * h + 1, 2 * h + 1, lo[0], lo[1], lo[2], g.dx, g.dy, g.dz, (1,) * 6, g.gamma)
+    return inputs.State(gs, np.ascontiguousarray(U), np.ascontiguousarray(Bx), np.ascontiguousarray(By),
+                        np.ascontiguousarray(Bz))
+
+
+def _sampled_compare(got, out, c, h, tol, precision, M, what):
+    floor = 1e-3 if precision == "fp64" else 1.0
+    for f, name in enumerate(("rho", "mx", "my", "mz", "E")):
+        a, b = got.U[f, c[2], c[1], c[0]], out.U[f, h, h, h]
+        assert abs(a - b) <= tol * max(abs(b) if precision == "fp64" else 0.0, floor * M[name]), (what, c, f, a, b)
+    for name in ("Bx", "By", "Bz"):
+        a, b = getattr(got, name)[c[2], c[1], c[0]], getattr(out, name)[h, h, h]
+        assert abs(a - b) <= tol * max(abs(b) if precision == "fp64" else 0.0, floor * M[name]), (what, c, name, a, b)
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_TOL), ("fp64", FP64_TOL)])
+def test_full_size_disc_sampled_parity(precision, tol):
+    """The 512 x 512 x 128 disc in the configuration the bench's disc leg runs (log
+    potential, floors, plain thermal source, graph replay): one device-CFL step, compared at
+    sampled cells with the oracle step + thermal update of an 11^3 window around each."""
+    st = inputs.disc(512, 512, 128)
+    src = dict(inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+    th = inputs.DISC_THERMAL
+    g = mhd.Grid(st, precision=precision, cfl=0.4, flags=mhd.FLAG_GRAPH)
+    g.set_sources(**src)
+    g.set_thermal(mhd.THERMAL_PLAIN, **th)
+    dt = g.cfl_dt()
+    g.step(dt)
+    got = g.get_state(0)
+    g.close()
+    rng = np.random.default_rng(12)
+    h = 5
+    samples = [(int(rng.integers(8, 504)), int(rng.integers(8, 504)), int(rng.integers(8, 120))) for _ in range(8)]
+    samples += [(256, 256, 64), (200, 300, 63), (300, 210, 66), (256, 100, 64)]  # disc plane and centre
+    M = {name: m for name, _, m in _fields(got)}
+    for c in samples:
+        win = _window(st, c, h)
+        out = oracle.step(win, dt, source=src)
+        out, _ = oracle.thermal_apply(out, dt, th)
+        _sampled_compare(got, out, c, h, tol, precision, M, "disc")
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_TOL), ("fp64", FP64_TOL)])
+def test_full_size_blast_batch_sampled_parity(precision, tol):
+    """The 64-patch blast batch the bench's batched leg runs (per-phase graphs, patches on
+    their streams, each patch its own CFL dt): one step, one sampled cell in each of 16
+    patches against the oracle on a periodic 11^3 window with that patch's dt."""
+    sts = inputs.blast_batch(64, seed=1502)
+    g = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_GRAPH)
+    dts = g.cfl_dt_patches()
+    g.step(-1.0)
+    rng = np.random.default_rng(13)
+    h = 5
+    for p in rng.choice(64, 16, replace=False):
+        st = sts[p]
+        got = g.get_state(int(p))
+        M = {name: m for name, _, m in _fields(got)}
+        n = (st.geom.nx, st.geom.ny, st.geom.nz)
+        c = tuple(int(rng.integers(0, n[a])) for a in range(3))
+        out = oracle.step(_subbox(st, c, h), dts[p])
+        _sampled_compare(got, out, c, h, tol, precision, M, f"patch {p}")
+    g.close()
