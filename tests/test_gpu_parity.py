@@ -455,13 +455,16 @@ def test_full_size_disc_sampled_parity(precision, tol):
         _sampled_compare(got, out, c, h, tol, precision, M, "disc")
 
 
+@pytest.mark.parametrize("scheme", ["per_phase", "persistent"])
 @pytest.mark.parametrize("precision,tol", [("mixed", MIXED_TOL), ("fp64", FP64_TOL)])
-def test_full_size_blast_batch_sampled_parity(precision, tol):
-    """The 64-patch blast batch the bench's batched leg runs (per-phase graphs, patches on
-    their streams, each patch its own CFL dt): one step, one sampled cell in each of 16
+def test_full_size_blast_batch_sampled_parity(precision, tol, scheme):
+    """The 64-patch blast batch the bench's batched leg runs, in both of its schemes
+    (per-phase graphs with the patches on their streams; one persistent launch under a
+    graph), each patch with its own CFL dt: one step, one sampled cell in each of 16
     patches against the oracle on a periodic 11^3 window with that patch's dt."""
     sts = inputs.blast_batch(64, seed=1502)
-    g = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_GRAPH)
+    flags = mhd.FLAG_GRAPH | (mhd.FLAG_PERSISTENT if scheme == "persistent" else 0)
+    g = mhd.Grid(sts, precision=precision, cfl=0.4, flags=flags)
     dts = g.cfl_dt_patches()
     g.step(-1.0)
     rng = np.random.default_rng(13)
