@@ -345,6 +345,11 @@ int mhd_mlp_forward(long long n, const float* xs, const float* params, float* y,
  * MHD_ERR_TIMEOUT if the bounded wait for the MMA ran out. */
 int mhd_mlp_forward_tc(long long n, const float* xs, const float* params, float* y, void* stream);
 int mhd_mlp_grad(long long n, const float* rows, const float* params, float* grad, float* loss_sum, void* stream);
+/* The same gradient with the three 64-wide products of the backward pass (Z2 = H1 W2^T,
+ * dH1 = dZ2 W2, dW2 = dZ2^T H1) on tcgen05 tensor cores, 128 rows per CTA; the kernel
+ * mhd_surrogate_train uses.  MHD_ERR_TIMEOUT if a bounded wait for the MMAs ran out. */
+int mhd_mlp_grad_tc(long long n, const float* rows, const float* params, float* grad, float* loss_sum,
+                    void* stream);
 
 /* Largest patch (nx*ny*nz cells) that mhd_cfl_dt_noalloc accepts. */
 #define MHD_NOALLOC_MAX_CELLS 8388608

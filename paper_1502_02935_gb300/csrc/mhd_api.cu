@@ -223,6 +223,7 @@ struct mhd_ctx {
   // surrogate
   float* mlp = nullptr;  // params | grads | adam m | adam v | loss (4 * kNParam + 1 floats)
   __nv_bfloat16* w2h = nullptr;
+  long long* train_step = nullptr;  // step index of the training run (device)
   float* dataset = nullptr;
   unsigned long long* ds_count = nullptr;
   long long ds_cap = 0;
@@ -267,6 +268,7 @@ static void free_ctx(mhd_ctx* ctx) {
   if (ctx->therm_stats) cudaFree(ctx->therm_stats);
   if (ctx->mlp) cudaFree(ctx->mlp);
   if (ctx->w2h) cudaFree(ctx->w2h);
+  if (ctx->train_step) cudaFree(ctx->train_step);
   if (ctx->dataset) cudaFree(ctx->dataset);
   if (ctx->ds_count) cudaFree(ctx->ds_count);
   if (ctx->fb_list) cudaFree(ctx->fb_list);
@@ -1083,7 +1085,8 @@ int mhd_set_thermal(mhd_ctx* ctx, const mhd_thermal_desc* d) {
 static int ensure_mlp(mhd_ctx* ctx) {
   if (ctx->mlp) return MHD_OK;
   if (cudaMalloc(&ctx->mlp, sizeof(float) * (4 * (size_t)kNParam + 1)) != cudaSuccess ||
-      cudaMalloc(&ctx->w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess)
+      cudaMalloc(&ctx->w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess ||
+      cudaMalloc(&ctx->train_step, sizeof(long long)) != cudaSuccess)
     return fail(ctx, MHD_ERR_NOMEM, "surrogate parameters");
   CK(cudaMemsetAsync(ctx->mlp, 0, sizeof(float) * (4 * (size_t)kNParam + 1), ctx->stream));
   ctx->mdev.p = ctx->mlp;
@@ -1187,19 +1190,45 @@ int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned
   float* loss = v + kNParam;
   const long long steps_per_epoch = std::max<long long>(1, rows / batch);
   const long long total = steps_per_epoch * epochs;
-  for (long long stp = 0; stp < total; ++stp) {
-    CK(cudaMemsetAsync(grad, 0, sizeof(float) * kNParam, ctx->stream));
-    if (stp == total - steps_per_epoch) CK(cudaMemsetAsync(loss, 0, sizeof(float), ctx->stream));
-    // cosine decay of the learning rate from lr to lr/20 over the run
-    const double lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * (double)stp / (double)total)));
-    if (mlp_grad(ctx->mdev, ctx->dataset, rows, seed, stp, batch, grad, loss, ctx->stream) ||
-        mlp_adam(ctx->mlp, grad, m, v, (float)lr_t, stp + 1, ctx->w2h, ctx->stream))
-      return cuda_fail(ctx, cudaGetLastError(), "training launch");
-    ctx->launches += 2;
+  // Each step is two launches: the gradient of one minibatch (tcgen05) and the Adam update,
+  // which also applies the cosine learning-rate decay from lr to lr/20, clears the gradient
+  // block and advances the step index held on the device.  The launches do not depend on
+  // the host, so a chunk of up to 256 steps is captured once as a graph and replayed; the
+  // mean loss is taken over the last epoch.
+  CK(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->train_step, 0, sizeof(long long), ctx->stream));
+  const long long loss_from = total - steps_per_epoch;
+  auto issue = [&](long long n) -> bool {
+    for (long long q = 0; q < n; ++q)
+      if (mlp_grad_tc(ctx->mdev, ctx->dataset, rows, seed, 0, ctx->train_step, loss_from, batch, grad, loss,
+                      ctx->err, ctx->stream) ||
+          mlp_adam_sched(ctx->mlp, grad, m, v, lr, total, ctx->train_step, ctx->w2h, ctx->stream))
+        return false;
+    return true;
+  };
+  const long long chunk = std::min<long long>(total, 256);
+  if (mlp_grad_tc_setup()) return cuda_fail(ctx, cudaGetLastError(), "training kernel attributes");
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  const bool captured = issue(chunk);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (!captured) return cuda_fail(ctx, cudaGetLastError(), "training launch");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+  cudaGraphExec_t gexec;
+  e = cudaGraphInstantiate(&gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+  for (long long q = 0; q + chunk <= total; q += chunk) {
+    e = cudaGraphLaunch(gexec, ctx->stream);
+    if (e != cudaSuccess) break;
   }
+  cudaGraphExecDestroy(gexec);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  if (!issue(total % chunk)) return cuda_fail(ctx, cudaGetLastError(), "training launch");
+  ctx->launches += 2 * total;
   float lsum = 0.f;
   CK(cudaMemcpyAsync(&lsum, loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  if ((rc = read_error_word(ctx))) return rc;
   if (loss_out) *loss_out = lsum / (double)(steps_per_epoch * batch);
   if (rows_out) *rows_out = rows;
   ctx->trained = true;
@@ -1462,6 +1491,28 @@ int mhd_mlp_grad(long long n, const float* rows, const float* params, float* gra
   if (mlp_refresh(params, w2h, s) || mlp_grad(unit_mlp(params, w2h), rows, n, 0ull, 0, (int)n, grad, loss_sum, s))
     return MHD_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
+}
+
+int mhd_mlp_grad_tc(long long n, const float* rows, const float* params, float* grad, float* loss_sum,
+                    void* stream) {
+  if (n < 1 || n > (1 << 20) || !rows || !params || !grad || !loss_sum) return MHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  static __nv_bfloat16* w2h = nullptr;
+  static int* err = nullptr;
+  if (!w2h && cudaMalloc(&w2h, sizeof(__nv_bfloat16) * kHid * kHid) != cudaSuccess) return MHD_ERR_NOMEM;
+  if (!err && cudaMalloc(&err, sizeof(int)) != cudaSuccess) return MHD_ERR_NOMEM;
+  if (cudaMemsetAsync(grad, 0, sizeof(float) * kNParam, s) != cudaSuccess ||
+      cudaMemsetAsync(loss_sum, 0, sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess)
+    return MHD_ERR_CUDA;
+  if (mlp_refresh(params, w2h, s) ||
+      mlp_grad_tc(unit_mlp(params, w2h), rows, n, 0ull, 0, nullptr, 0, (int)n, grad, loss_sum, err, s))
+    return MHD_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MHD_ERR_CUDA;
+  return h ? MHD_ERR_TIMEOUT : MHD_OK;
 }
 
 int mhd_thermal_cells(long long n, const double* T0, const double* nh, const double* ce, const double* dt,

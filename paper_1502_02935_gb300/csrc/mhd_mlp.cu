@@ -1,11 +1,10 @@
 // mhd_mlp.cu -- training and inference kernels of the thermal surrogate (mhd_mlp.cuh).
 //
 // Training: each minibatch row is drawn from the harvested set with a counter-based hash
-// of (seed, step, row); one CTA of 4 warps takes 64 rows, runs the forward pass, the
-// backward pass (the two 64x64 products of the backward pass, dW2 = dz2^T h1 and
-// dh1 = dz2 W2, also on the tensor cores) and adds its gradient contributions into one
-// FP32 gradient block.  Adam then updates the FP32 master weights and refreshes the BF16
-// copy of W2.
+// of (seed, step, row).  k_mlp_grad_tc (mhd_mlp_tc.cu) computes a minibatch's loss and
+// gradient on tcgen05; k_mlp_grad below is the same computation on mma.sync (64 rows per
+// CTA of 4 warps; dW2 = dz2^T h1 and dh1 = dz2 W2 also on the tensor cores), kept as the
+// cross-check.  k_adam_sched then updates the FP32 master weights and the BF16 copy of W2.
 //
 // Inference (thermal mode SURROGATE): per interior cell, features -> network -> change of
 // log10 T (k_thermal_surrogate_tc in mhd_mlp_tc.cu, on tcgen05; k_thermal_surrogate below is
@@ -19,14 +18,6 @@
 #include "mhd_thermal.cuh"
 
 namespace mhd {
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  // splitmix64 finaliser
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 // ------------------------------------------------------------------- forward --
 // Unit-level forward: standardised inputs xs[n][4] -> y[n].
@@ -212,12 +203,11 @@ __global__ void __launch_bounds__(128) k_mlp_grad(MlpDev M, const float* __restr
   for (int q = threadIdx.x; q < kHid; q += blockDim.x) atomicAdd(grad + kOffB1 + q, T.gb1[q]);
 }
 
-__global__ void k_adam(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float b1c, float b2c, __nv_bfloat16* __restrict__ W2h) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= kNParam) return;
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8) on parameter q; b1c, b2c the bias corrections.
+__device__ __forceinline__ void adam_param(int q, float* __restrict__ p, float gq, float* __restrict__ m,
+                                           float* __restrict__ v, float lr, float b1c, float b2c,
+                                           __nv_bfloat16* __restrict__ W2h) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float gq = grad[q];
   const float mq = b1 * m[q] + (1.f - b1) * gq;
   const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
   m[q] = mq;
@@ -225,6 +215,31 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ grad, fl
   const float pq = p[q] - lr * (mq / b1c) / (sqrtf(vq / b2c) + eps);
   p[q] = pq;
   if (q >= kOffW2 && q < kOffW2 + kHid * kHid) W2h[q - kOffW2] = __float2bfloat16_rn(pq);
+}
+
+// The Adam step of a training run replayed as a graph: the step index comes from device
+// memory, the learning rate follows the cosine decay from lr0 to lr0/20 over `total` steps,
+// the gradient block is cleared for the next step and the index advanced.  One CTA.
+__global__ void __launch_bounds__(1024) k_adam_sched(float* __restrict__ p, float* __restrict__ grad,
+                                                     float* __restrict__ m, float* __restrict__ v, double lr0,
+                                                     long long total, long long* __restrict__ step_dev,
+                                                     __nv_bfloat16* __restrict__ W2h) {
+  __shared__ float sched[3];
+  const long long stp = *step_dev;
+  if (threadIdx.x == 0) {  // one thread: FP64 is slow on this part
+    const double pi = 3.14159265358979323846;
+    sched[0] = (float)(lr0 * (0.05 + 0.95 * 0.5 * (1.0 + cos(pi * (double)stp / (double)total))));
+    sched[1] = 1.f - powf(0.9f, (float)(stp + 1));
+    sched[2] = 1.f - powf(0.999f, (float)(stp + 1));
+  }
+  __syncthreads();
+  const float lr = sched[0], b1c = sched[1], b2c = sched[2];
+  for (int q = threadIdx.x; q < kNParam; q += blockDim.x) {
+    adam_param(q, p, grad[q], m, v, lr, b1c, b2c, W2h);
+    grad[q] = 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *step_dev = stp + 1;
 }
 
 __global__ void k_refresh_w2h(const float* __restrict__ p, __nv_bfloat16* __restrict__ W2h) {
@@ -270,10 +285,9 @@ int mlp_grad(const MlpDev& M, const float* data, long long nrows, unsigned long 
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int mlp_adam(float* p, const float* grad, float* m, float* v, float lr, long long t, __nv_bfloat16* W2h,
-             cudaStream_t s) {
-  const float b1c = 1.f - powf(0.9f, (float)t), b2c = 1.f - powf(0.999f, (float)t);
-  k_adam<<<(kNParam + 255) / 256, 256, 0, s>>>(p, grad, m, v, lr, b1c, b2c, W2h);
+int mlp_adam_sched(float* p, float* grad, float* m, float* v, double lr0, long long total, long long* step_dev,
+                   __nv_bfloat16* W2h, cudaStream_t s) {
+  k_adam_sched<<<1, 1024, 0, s>>>(p, grad, m, v, lr0, total, step_dev, W2h);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -6,10 +6,11 @@
 // S = th_scale(th_dlin(x)) (mhd_thermal.cuh); the change applied is q S.
 //
 // The 64x64 layer runs on the tensor cores: BF16 operands (activations h1 and weights W2
-// rounded to BF16), FP32 accumulation.  Inference in the thermal step uses tcgen05.mma with
-// the accumulator in tensor memory (mhd_mlp_tc.cu); training, whose backward pass needs
-// the transposed products as well, uses warp-level mma.sync m16n8k16 (mhd_mlp.cu).  The
-// 4-wide input layer and the 64-wide output layer are FP32 FMAs.  Master weights are FP32.
+// rounded to BF16), FP32 accumulation.  Inference in the thermal step and training both use
+// tcgen05.mma with the accumulators in tensor memory (mhd_mlp_tc.cu); the warp-level
+// mma.sync m16n8k16 kernels of mhd_mlp.cu compute the same products and serve as the
+// cross-check of the tcgen05 ones.  The 4-wide input layer and the 64-wide output layer are
+// FP32 FMAs.  Master weights are FP32.
 // Parameter block layout (floats): W1[64][4], b1[64], W2[64][64] (row = output), b2[64],
 // w3[64], b3[1].
 #pragma once
@@ -31,6 +32,16 @@ struct MlpDev {
   float qmax;                // fallback when |y| > qmax
   float dmax;                // or when the change |y S| > dmax (or is not finite)
 };
+
+// Minibatch row of training step `step`, position r: mix64(seed ^ mix64(step * (2^32 + 1) + r))
+// modulo the number of harvested rows, mix64 being the splitmix64 finaliser.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  // splitmix64 finaliser
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
 
 __device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);

@@ -71,7 +71,7 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_cfl_dt_noalloc", "mhd_autotune", "mhd_set_wait_limit", "mhd_set_thermal",
            "mhd_thermal_stats", "mhd_thermal_cells", "mhd_surrogate_harvest", "mhd_surrogate_train",
            "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
-           "mhd_mlp_forward_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
+           "mhd_mlp_forward_tc", "mhd_mlp_grad_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
            "mhd_set_inflow", "mhd_set_scalars", "mhd_set_scalar_state", "mhd_get_scalar_state",
            "mhd_set_inflow_scalars"]
 
@@ -131,6 +131,7 @@ def lib():
     L.mhd_mlp_forward.argtypes = [C.c_longlong, vp, vp, vp, vp]
     L.mhd_mlp_grad.argtypes = [C.c_longlong, vp, vp, vp, vp, vp]
     L.mhd_mlp_forward_tc.argtypes = [C.c_longlong, vp, vp, vp, vp]
+    L.mhd_mlp_grad_tc.argtypes = [C.c_longlong, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("mhd_destroy", "mhd_last_error", "mhd_launch_count"):
             getattr(L, name).restype = C.c_int
@@ -435,7 +436,7 @@ def mlp_forward(xs, params, tcgen05: bool = False) -> np.ndarray:
     return y.cpu().numpy()
 
 
-def mlp_grad(xs, targets, params):
+def mlp_grad(xs, targets, params, tcgen05: bool = False):
     import torch
     t = np.asarray(targets, dtype=np.float32)[:, None]
     rows = np.concatenate([np.asarray(xs, dtype=np.float32), t, np.zeros_like(t)], axis=1)  # harvested-row layout
@@ -443,8 +444,9 @@ def mlp_grad(xs, targets, params):
     p = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float32)).cuda()
     g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
-    rc = lib().mhd_mlp_grad(rows.shape[0], r.data_ptr(), p.data_ptr(), g.data_ptr(), loss.data_ptr(),
-                            torch.cuda.current_stream().cuda_stream)
+    fn = lib().mhd_mlp_grad_tc if tcgen05 else lib().mhd_mlp_grad
+    rc = fn(rows.shape[0], r.data_ptr(), p.data_ptr(), g.data_ptr(), loss.data_ptr(),
+            torch.cuda.current_stream().cuda_stream)
     if rc != 0:
         raise MHDError(rc, "mhd_mlp_grad")
     return float(loss.item()), g.cpu().numpy()
