@@ -19,6 +19,7 @@ host cores (a bounded sample of the workload).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -98,7 +99,9 @@ def load_peaks():
 
 # ---------------------------------------------------------------- clocks ----
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi every 50 ms into a file; `stop(t0, t1)` keeps the samples whose timestamps
+    fall inside the timed window [t0, t1] (host wall clock), else the one nearest to it."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -113,12 +116,21 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.device), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(self.device), "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def wait_first(self, timeout: float = 3.0):
+        """Block until nvidia-smi has written its first line (its start-up takes a while)."""
+        t = time.time()
+        while self.proc is not None and time.time() - t < timeout:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
+
+    def stop(self, t0: float, t1: float):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -127,25 +139,27 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() in ("active", "1"):
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if not inside:
+            inside = [min(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in inside for nm, v in zip(names, r[3]) if v.lower() in ("active", "1")}
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[0][2],
+                "reasons": sorted(reasons), "samples": len(inside),
+                "in_window": t0 <= inside[0][0] <= t1}
 
 
 # ------------------------------------------------------------ distributed ----
@@ -351,11 +365,17 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     barrier(pg)
     torch.cuda.synchronize()
-    l0 = grid.launch_count()
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.wait_first()
+    grid.step(-1.0)  # one more untimed step once the sampler runs
+    torch.cuda.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    l0 = grid.launch_count()
+    t_start = time.time()
     ms = timed_steps(grid, args.steps, stream)
-    clk = clocks.stop()
+    clk = clocks.stop(t_start, time.time())
     torch.cuda.synchronize()
     barrier(pg)
     launches = grid.launch_count() - l0
