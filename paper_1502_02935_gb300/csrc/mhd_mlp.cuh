@@ -43,6 +43,17 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
+// The hidden activation of every surrogate kernel (training and inference, tcgen05 and
+// mma.sync alike): the single-instruction hardware approximation tanh.approx.f32.  Its error
+// against the exact tanh stays below 1e-3 (a GPU test sweeps it against libm), under the
+// BF16 rounding that h1 takes for the tensor cores anyway and an order below the fit error
+// of the trained network.
+__device__ __forceinline__ float mlp_tanh(float z) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(z));
+  return r;
+}
+
 __device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
 }
@@ -101,7 +112,7 @@ __device__ __forceinline__ void mlp_layer1(MlpSmem& S, int r0) {
   for (int c = c0; c < c0 + 32; ++c) {
     const float z = S.b1[c] + S.W1[c * 4 + 0] * x0 + S.W1[c * 4 + 1] * x1 + S.W1[c * 4 + 2] * x2 +
                     S.W1[c * 4 + 3] * x3;
-    const float h = tanhf(z);
+    const float h = mlp_tanh(z);
     S.h1f[row * kHid + c] = h;
     S.h1b[row * kHid + c] = __float2bfloat16_rn(h);
   }
@@ -125,10 +136,10 @@ __device__ __forceinline__ void mlp_head(const MlpSmem& S, float acc[8][4], floa
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const int c = nt * 8 + 2 * t;
-    acc[nt][0] = tanhf(acc[nt][0] + S.b2[c]);
-    acc[nt][1] = tanhf(acc[nt][1] + S.b2[c + 1]);
-    acc[nt][2] = tanhf(acc[nt][2] + S.b2[c]);
-    acc[nt][3] = tanhf(acc[nt][3] + S.b2[c + 1]);
+    acc[nt][0] = mlp_tanh(acc[nt][0] + S.b2[c]);
+    acc[nt][1] = mlp_tanh(acc[nt][1] + S.b2[c + 1]);
+    acc[nt][2] = mlp_tanh(acc[nt][2] + S.b2[c]);
+    acc[nt][3] = mlp_tanh(acc[nt][3] + S.b2[c + 1]);
     s0 += S.w3[c] * acc[nt][0] + S.w3[c + 1] * acc[nt][1];
     s1 += S.w3[c] * acc[nt][2] + S.w3[c + 1] * acc[nt][3];
   }

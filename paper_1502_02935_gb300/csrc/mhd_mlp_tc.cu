@@ -54,7 +54,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float tc_tanh(float z) { return tanhf(z); }
+__device__ __forceinline__ float tc_tanh(float z) { return mlp_tanh(z); }
 
 __device__ __forceinline__ unsigned long long tc_ns() {
   unsigned long long t;

@@ -57,6 +57,24 @@ def test_mlp_forward_tcgen05_matches_mma_sync():
 
 
 @pytest.mark.parametrize("tcgen05", [False, True], ids=["mma_sync", "tcgen05"])
+def test_hidden_activation_error_bound(tcgen05):
+    """The hidden activation is the hardware tanh.approx.f32.  With W1 = W2 = 0 and w3 = e_0
+    the network returns exactly the device's tanh(b2[0]); swept over [-8, 8] against libm's
+    tanh (FP64) the error stays below 1e-3."""
+    H = 64
+    P = {"W1": np.zeros((H, 4)), "b1": np.zeros(H), "W2": np.zeros((H, H)), "b2": np.zeros(H),
+         "w3": np.eye(H)[0], "b3": np.zeros(1)}
+    X = np.zeros((130, 4), dtype=np.float32)  # one full 128-row tile and a tail
+    err = 0.0
+    for z in np.linspace(-8.0, 8.0, 81):
+        P["b2"][0] = z
+        y = mhd.mlp_forward(X, mhd.mlp_pack(P), tcgen05=tcgen05)
+        assert np.all(y == y[0])
+        err = max(err, abs(float(y[0]) - float(np.tanh(np.float64(np.float32(z))))))
+    assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("tcgen05", [False, True], ids=["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("n", [512, 37, 333, 4097])
 def test_mlp_gradients_match_oracle(tcgen05, n):
     """Whole tiles (512), one partial tile (37) and ragged counts over several 128-row tiles."""
