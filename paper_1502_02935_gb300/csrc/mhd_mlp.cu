@@ -7,10 +7,10 @@
 // cross-check.  k_adam_sched then updates the FP32 master weights and the BF16 copy of W2.
 //
 // Inference (thermal mode SURROGATE): per interior cell, features -> network -> change of
-// log10 T (k_thermal_surrogate_tc in mhd_mlp_tc.cu, on tcgen05; k_thermal_surrogate below is
-// the same step on mma.sync); a cell whose standardised features leave [-1, 1] or whose
-// predicted change exceeds the stated bound is appended to a fallback list that the plain
-// FP64 integrator then handles, so the divergent fallback stays out of the network kernel.
+// log10 T (k_thermal_surrogate_tc in mhd_mlp_tc.cu, on tcgen05).  A cell whose standardised
+// features leave [-1, 1] or whose predicted change exceeds the stated bound is appended to a
+// fallback list that the plain FP64 integrator then handles (k_thermal_fallback below), so
+// the divergent fallback stays out of the network kernel.
 #include <cuda_bf16.h>
 
 #include "mhd_mlp.cuh"

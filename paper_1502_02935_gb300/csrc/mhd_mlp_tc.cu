@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(long long n, const float
 
 // Surrogate thermal step, one interior cell per thread, 128 cells per tile; cells outside
 // the training range or over the bound go to the fallback list (see mhd_mlp.cu).
-__global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, ThermalDev th, MlpDev M,
+__global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, ThermalDev th, MlpDev M,
                                                               int* __restrict__ fb_list,
                                                               unsigned long long* __restrict__ fb_count) {
   __shared__ TcSmem S;
@@ -212,23 +212,29 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
   const double dt = *P.dt_used;
   const float ldt = log10f((float)dt);
   const DlinConst dc = th_dlin_const(th, P.gm1);
-  const double cef = th_cef(P, th);
+  // FP32 copies: only the pressure needs FP64 (the cancellation in E - kinetic - magnetic);
+  // T and n_H feed FP32 features, and the energy change is an FP32 increment added to the
+  // FP64 energy, as the fluxes of the step are
+  const float cef = (float)th_cef(P, th), tpp = (float)th.t_per_pr, npr = (float)th.nh_per_rho;
   const float zf = (float)th.z;
+  const float kLn10 = 2.302585093f;
   for (long long base = (long long)blockIdx.x * kTcRows; base < nc; base += (long long)gridDim.x * kTcRows) {
     const long long c = base + threadIdx.x;
     int i = 0, j = 0, k = 0;
     bool inrange = false;
-    double T = 0.0, nh = 0.0, ce = 0.0;
+    float tf = 0.f, rf = 0.f;
     float x[4] = {0.f, 0.f, 0.f, 0.f}, dl = 0.f;
     if (c < nc) {
       i = (int)(c % P.n[0]);
       const long long r = c / P.n[0];
       j = (int)(r % P.n[1]);
       k = (int)(r / P.n[1]);
-      th_cell(P, th, P.Un, i, j, k, cef, T, nh, ce);
-      // features in FP32 (integer-pipe conversions; the clamp lets a NaN through to fall back)
-      const float tf = d2f_alu(T);
-      const float raw[4] = {log10f(d2f_alu(nh)), log10f(tf < 10.0f ? 10.0f : (tf > 1e8f ? 1e8f : tf)), ldt, zf};
+      double rho, irho;
+      const double p = th_pressure(P, P.Un, i, j, k, rho, irho);
+      // T and n_H in FP32 (integer-pipe conversions); the clamp lets a NaN through to fall back
+      rf = d2f_alu(rho);
+      tf = tpp * d2f_alu(p) * d2f_alu(irho);
+      const float raw[4] = {log10f(npr * rf), log10f(tf < 10.0f ? 10.0f : (tf > 1e8f ? 1e8f : tf)), ldt, zf};
       dl = th_scale(th_dlin(dc, raw[0], raw[1], raw[2]));
       inrange = true;
 #pragma unroll
@@ -249,9 +255,14 @@ __global__ void __launch_bounds__(128) k_thermal_surrogate_tc(PatchDev P, Therma
       live = 1;
       const float d = y * dl;  // predicted change of log10 T
       if (inrange && fabsf(y) <= M.qmax && fabsf(d) <= M.dmax) {
-        const double T0 = th_clamp(T);
-        const double T1 = th_clamp(T0 * f2d_alu(exp10f(d)));
-        P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);
+        // T1 = clamp(clamp(T) 10^d); the change T1 - T without cancellation when no clamp
+        // acts (T0 (10^d - 1) = T0 expm1(d ln 10))
+        const float T0 = tf < 10.0f ? 10.0f : (tf > 1e8f ? 1e8f : tf);
+        const float T1 = T0 * exp10f(d);
+        const float dT = (T0 != tf || !(T1 >= 10.0f && T1 <= 1e8f))
+                             ? (T1 < 10.0f ? 10.0f : (T1 > 1e8f ? 1e8f : T1)) - tf
+                             : T0 * expm1f(d * kLn10);
+        P.Un[EN * P.FS + sidx(P, i, j, k)] += f2d_alu(cef * rf * dT);
       } else {
         fb_list[atomicAdd(fb_count, 1ull)] = (int)c;
         fb = 1;

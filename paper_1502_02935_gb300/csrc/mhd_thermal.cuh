@@ -161,17 +161,24 @@ __device__ __forceinline__ double th_cef(const PatchDev& P, const ThermalDev& th
   return 1.0 / (th.t_per_pr * P.gm1);
 }
 
-__device__ __forceinline__ void th_cell(const PatchDev& P, const ThermalDev& th, const double* __restrict__ U,
-                                        int i, int j, int k, double cef, double& T, double& nh, double& ce) {
+// Pressure (FP64) of interior cell (i, j, k), with its density and 1/density.
+__device__ __forceinline__ double th_pressure(const PatchDev& P, const double* __restrict__ U, int i, int j, int k,
+                                              double& rho, double& irho) {
   const long long FS = P.FS, c = sidx(P, i, j, k);
-  const double rho = U[c];
-  const double irho = inv_density<float>(rho);
+  rho = U[c];
+  irho = inv_density<float>(rho);
   const double mx = U[MX * FS + c], my = U[MY * FS + c], mz = U[MZ * FS + c];
   const double sbx = U[BXF * FS + c] + U[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)];
   const double sby = U[BYF * FS + c] + U[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)];
   const double sbz = U[BZF * FS + c] + U[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))];
-  const double p = P.gm1 * U[EN * FS + c] - P.hgm1 * ((mx * mx + my * my + mz * mz) * irho) -
-                   P.egm1 * (sbx * sbx + sby * sby + sbz * sbz);
+  return P.gm1 * U[EN * FS + c] - P.hgm1 * ((mx * mx + my * my + mz * mz) * irho) -
+         P.egm1 * (sbx * sbx + sby * sby + sbz * sbz);
+}
+
+__device__ __forceinline__ void th_cell(const PatchDev& P, const ThermalDev& th, const double* __restrict__ U,
+                                        int i, int j, int k, double cef, double& T, double& nh, double& ce) {
+  double rho, irho;
+  const double p = th_pressure(P, U, i, j, k, rho, irho);
   T = th.t_per_pr * p * irho;
   nh = th.nh_per_rho * rho;
   ce = rho * cef;
