@@ -469,17 +469,25 @@ static int issue_persistent_step(mhd_ctx* ctx, double dt) {
   return MHD_OK;
 }
 
+// The thermal term changes E after the step's recovery.  On the mixed path the surrogate
+// kernels recover W (and the CFL limit) of each cell they update, and the ghost shell of W
+// is filled after them, so the next step starts without a recovery pass.  Otherwise the
+// next step recovers W first.
 static int issue_thermal_all(mhd_ctx* ctx) {
   if (ctx->thermal.mode == TH_OFF) return MHD_OK;
-  ctx->w_valid = false;  // E changes after the recovery of the step
+  ctx->w_valid = false;
+  const bool fuse_w = ctx->thermal.mode == TH_SURROGATE && ctx->be.scratch_elem == 4 && !ctx->persistent;
   for (auto& p : ctx->P) {
     ProfScope ps(ctx->profiling && ctx->prof.n < ProfRec::kMax ? &ctx->prof : nullptr, KC_THERMAL, ctx->stream);
+    if (fuse_w) CK(cudaMemsetAsync(p.dev.cfl_min, 0xFF, sizeof(unsigned long long), ctx->stream));
     int rc = ctx->thermal.mode == TH_SURROGATE
-                 ? issue_surrogate(p.dev, ctx->thermal, ctx->mdev, ctx->fb_list, ctx->fb_count, ctx->sms,
-                                   ctx->stream, &ctx->launches)
+                 ? issue_surrogate(p.dev, ctx->thermal, ctx->mdev, ctx->fb_list, ctx->fb_count,
+                                   fuse_w ? (float*)p.dev.W : nullptr, ctx->sms, ctx->stream, &ctx->launches)
                  : issue_thermal(p.dev, ctx->thermal, ctx->stream, &ctx->launches);
+    if (!rc && fuse_w) rc = ctx->be.ghost_w(p.dev, ctx->stream, &ctx->launches);
     if (rc) return cuda_fail(ctx, cudaGetLastError(), "thermal launch");
   }
+  ctx->w_valid = fuse_w;
   return MHD_OK;
 }
 

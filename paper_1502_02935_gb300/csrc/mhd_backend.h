@@ -42,6 +42,8 @@ struct Backend {
   int (*prim)(const PatchDev&, cudaStream_t, long long* launches, ProfRec* prof);
   // CFL limit of the current state into the patch's cfl_min slot
   int (*cfl)(const PatchDev&, cudaStream_t, long long* launches);
+  // W of the ghost shell from the interior W and the current state Un
+  int (*ghost_w)(const PatchDev&, cudaStream_t, long long* launches);
   // unit-level Riemann fluxes (solver: 0 HLLD, 1 HLLC, 2 HLL)
   int (*riemann)(int solver, int n, const double* wl, const double* wr, const double* bn, double gamma,
                  double* flux, cudaStream_t s);

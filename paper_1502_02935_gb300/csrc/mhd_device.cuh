@@ -1141,4 +1141,28 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
   return (unsigned long long)__double_as_longlong(x);
 }
 
+// Block minimum of v in its own type (FP32 compares on the mixed path), then one
+// ordered-bits atomicMin of its exact double value per block (deterministic).
+template <class T>
+__device__ __forceinline__ void block_min_atomic(T v, unsigned long long* slot) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  __shared__ T red[32];  // one per warp, up to 1024 threads
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(INFINITY);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w < v ? w : v;
+    }
+    if (lane == 0 && v < T(INFINITY)) atomicMin(slot, dbits(Ar<T>::to_d(v)));
+  }
+}
+
 }  // namespace mhd

@@ -40,29 +40,6 @@ __device__ __forceinline__ bool range_point(const Range& rg, int& i, int& j, int
   return true;
 }
 
-// Block minimum of v in its own type (FP32 compares on the mixed path), then one
-// ordered-bits atomicMin of its exact double value per block (deterministic).
-template <class T>
-__device__ __forceinline__ void block_min_atomic(T v, unsigned long long* slot) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    T w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w < v ? w : v;
-  }
-  __shared__ T red[kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(INFINITY);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      T w = __shfl_xor_sync(0xffffffffu, v, o);
-      v = w < v ? w : v;
-    }
-    if (lane == 0 && v < T(INFINITY)) atomicMin(slot, dbits(Ar<T>::to_d(v)));
-  }
-}
 
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_prim(PatchDev P, const double* __restrict__ U, Range rg,
@@ -564,6 +541,17 @@ static int issue_prim(const PatchDev& P, cudaStream_t s, long long* launches, Pr
 }
 
 template <class R>
+static int issue_ghost_w(const PatchDev& P, cudaStream_t s, long long* launches) {
+  const long long ng = ghost_count(P);
+  if (ng <= 0) return 0;
+  long long blocks = (ng + kBlock - 1) / kBlock;
+  if (blocks > 65535) blocks = 65535;
+  k_ghost<R><<<(unsigned)blocks, kBlock, 0, s>>>(P, P.Un);
+  *launches += 1;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class R>
 static int issue_cfl(const PatchDev& P, cudaStream_t s, long long* launches) {
   const Range r = interior_range(P);
   k_prim<R><<<grid_of(r), kBlock, 0, s>>>(P, P.Un, r, 0, 1);
@@ -585,6 +573,7 @@ template <class R> Backend make_backend() {
   b.stage = &issue_stage<R>;
   b.prim = &issue_prim<R>;
   b.cfl = &issue_cfl<R>;
+  b.ghost_w = &issue_ghost_w<R>;
   b.riemann = &issue_riemann<R>;
   b.persistent = &issue_persistent<R>;
   b.occupancy = &persistent_occupancy<R>;

@@ -248,10 +248,13 @@ __global__ void k_refresh_w2h(const float* __restrict__ p, __nv_bfloat16* __rest
 }
 
 // -------------------------------------------------------- surrogate thermal --
-// Plain FP64 integrator on the listed cells (grid-stride over the device-side count).
+// Plain FP64 integrator on the listed cells (grid-stride over the device-side count); with
+// Wst, each cell's W and the CFL limit as in k_thermal_surrogate_tc.
 __global__ void __launch_bounds__(256) k_thermal_fallback(PatchDev P, ThermalDev th, const int* __restrict__ fb_list,
-                                                          const unsigned long long* __restrict__ fb_count) {
+                                                          const unsigned long long* __restrict__ fb_count,
+                                                          float* __restrict__ Wst) {
   const long long n = (long long)*fb_count;
+  float lim = INFINITY;
   const double dt = *P.dt_used;
   const double cef = th_cef(P, th);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -264,9 +267,11 @@ __global__ void __launch_bounds__(256) k_thermal_fallback(PatchDev P, ThermalDev
     int st, nsub;
     const double T1 = th_integrate(T, nh, ce, dt, th, &st, &nsub);
     P.Un[EN * P.FS + sidx(P, i, j, k)] += ce * (T1 - T);
+    if (Wst) lim = fminf(lim, prim_point<float>(P, P.Un, Wst, i, j, k, true, true));
     if (st & (TST_SUBSTEP_CAP | TST_NEWTON_CAP)) atomicAdd(th.stats + 2, 1ull);
     atomicAdd(th.stats + 1, (unsigned long long)nsub);
   }
+  if (Wst) block_min_atomic(lim, P.cfl_min);
 }
 
 // ------------------------------------------------------------ host side ----
@@ -297,10 +302,10 @@ int mlp_refresh(const float* p, __nv_bfloat16* W2h, cudaStream_t s) {
 }
 
 int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
-                    unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches) {
+                    unsigned long long* fb_count, float* Wst, int sms, cudaStream_t s, long long* launches) {
   if (cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), s) != cudaSuccess) return -1;
-  if (issue_surrogate_tc(P, th, M, fb_list, fb_count, sms, s, launches)) return -1;
-  k_thermal_fallback<<<(unsigned)(sms * 4), 256, 0, s>>>(P, th, fb_list, fb_count);
+  if (issue_surrogate_tc(P, th, M, fb_list, fb_count, Wst, sms, s, launches)) return -1;
+  k_thermal_fallback<<<(unsigned)(sms * 4), 256, 0, s>>>(P, th, fb_list, fb_count, Wst);
   *launches += 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -19,8 +19,11 @@ int mlp_adam_sched(float* p, float* grad, float* m, float* v, double lr0, long l
 int mlp_refresh(const float* p, __nv_bfloat16* W2h, cudaStream_t s);
 int mlp_forward_tc(long long n, const float* xs, const float* p, const __nv_bfloat16* W2h, float* y, int* err,
                    int sms, cudaStream_t s);
+// Wst != nullptr (mixed path): the kernels also store W of the updated cells there and the
+// CFL limit into the patch's slot, which the caller resets; the caller then fills W's ghost
+// shell.
 int issue_surrogate_tc(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
-                       unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches);
+                       unsigned long long* fb_count, float* Wst, int sms, cudaStream_t s, long long* launches);
 int issue_surrogate(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
-                    unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches);
+                    unsigned long long* fb_count, float* Wst, int sms, cudaStream_t s, long long* launches);
 }  // namespace mhd

@@ -201,10 +201,14 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(long long n, const float
 }
 
 // Surrogate thermal step, one interior cell per thread, 128 cells per tile; cells outside
-// the training range or over the bound go to the fallback list (see mhd_mlp.cu).
+// the training range or over the bound go to the fallback list (see mhd_mlp.cu).  With Wst,
+// each updated cell also stores its W (the recovery of the new state) there and the block's
+// CFL limit goes into the patch's (reset) slot: the recovery that would otherwise start the
+// next step.
 __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, ThermalDev th, MlpDev M,
                                                               int* __restrict__ fb_list,
-                                                              unsigned long long* __restrict__ fb_count) {
+                                                              unsigned long long* __restrict__ fb_count,
+                                                              float* __restrict__ Wst) {
   __shared__ TcSmem S;
   const uint32_t taddr = tc_setup(S, M.p, M.W2h);
   uint32_t phase = 0;
@@ -218,6 +222,7 @@ __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, The
   const float cef = (float)th_cef(P, th), tpp = (float)th.t_per_pr, npr = (float)th.nh_per_rho;
   const float zf = (float)th.z;
   const float kLn10 = 2.302585093f;
+  float lim = INFINITY;
   for (long long base = (long long)blockIdx.x * kTcRows; base < nc; base += (long long)gridDim.x * kTcRows) {
     const long long c = base + threadIdx.x;
     int i = 0, j = 0, k = 0;
@@ -263,6 +268,7 @@ __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, The
                              ? (T1 < 10.0f ? 10.0f : (T1 > 1e8f ? 1e8f : T1)) - tf
                              : T0 * expm1f(d * kLn10);
         P.Un[EN * P.FS + sidx(P, i, j, k)] += f2d_alu(cef * rf * dT);
+        if (Wst) lim = fminf(lim, prim_point<float>(P, P.Un, Wst, i, j, k, true, true));
       } else {
         fb_list[atomicAdd(fb_count, 1ull)] = (int)c;
         fb = 1;
@@ -275,6 +281,7 @@ __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, The
       if (nlive) atomicAdd(th.stats + 0, (unsigned long long)nlive);
     }
   }
+  if (Wst) block_min_atomic(lim, P.cfl_min);
   tc_teardown(taddr);
 }
 
@@ -622,11 +629,11 @@ int mlp_forward_tc(long long n, const float* xs, const float* p, const __nv_bflo
 
 namespace mhd {
 int issue_surrogate_tc(const PatchDev& P, const ThermalDev& th, const MlpDev& M, int* fb_list,
-                       unsigned long long* fb_count, int sms, cudaStream_t s, long long* launches) {
+                       unsigned long long* fb_count, float* Wst, int sms, cudaStream_t s, long long* launches) {
   const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
   long long blocks = (nc + kTcRows - 1) / kTcRows;
   if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
-  k_thermal_surrogate_tc<<<(unsigned)blocks, 128, 0, s>>>(P, th, M, fb_list, fb_count);
+  k_thermal_surrogate_tc<<<(unsigned)blocks, 128, 0, s>>>(P, th, M, fb_list, fb_count, Wst);
   *launches += 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -198,3 +198,29 @@ def test_surrogate_thermal_step_on_disc():
     print("surrogate L1(T) vs plain", l1, "fallback fraction", fb)
     assert l1 <= 1e-2, l1
     assert fb < 0.5, fb
+
+
+def test_recovery_in_surrogate_kernels_equals_recovery_pass():
+    """On the mixed path the surrogate kernels recover W and the CFL limit of the cells they
+    update, and fill W's ghost shell after them, so the next step starts without the recovery
+    pass.  Restarting that step from the same state through set_state, which makes the step
+    begin with the recovery pass, gives the same state bit for bit."""
+    th = inputs.DISC_THERMAL
+    g = mhd.Grid(inputs.disc(48, 48, 16), precision="mixed", cfl=0.4)
+    g.set_sources(**inputs.DISC_POTENTIAL, **inputs.DISC_FLOORS)
+    g.set_thermal(mhd.THERMAL_PLAIN, **th)
+    g.surrogate_harvest(1 << 18, stride=1)
+    for _ in range(4):
+        g.step(-1.0)
+    g.surrogate_train(epochs=20, batch=4096, lr=3e-3, seed=1502)
+    g.set_thermal(mhd.THERMAL_SURROGATE, **th)
+    g.step(-1.0)
+    s1 = g.get_state(0)
+    g.step(-1.0)  # starts from the W the surrogate kernels stored
+    a = g.get_state(0)
+    g.set_state(0, s1)
+    g.step(-1.0)  # starts with the recovery pass
+    b = g.get_state(0)
+    g.close()
+    assert np.array_equal(a.U, b.U)
+    assert np.array_equal(a.faces_flat(), b.faces_flat())
