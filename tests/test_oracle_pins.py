@@ -526,6 +526,28 @@ def test_point_symmetry_orszag_tang():
     assert np.max(np.abs(By + By[:, ::-1, ::-1])) <= 1e-12
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_blast_reflection_symmetry(axis):
+    """A blast centred in a periodic box with a uniform field along x is invariant under the
+    reflection of any axis: the normal velocity and, across the field, the normal field flip
+    sign (a polar vector); along the field the transverse field flips instead, the polar
+    reflection composed with the global B -> -B under which the equations are invariant.
+    A symmetric scheme keeps the symmetry to roundoff after 20 steps."""
+    st = inputs.blast(24, (0.5, 0.5, 0.5), (1.0, 0.0, 0.0))
+    for _ in range(20):
+        st = oracle.step(st, oracle.cfl_dt(st, 0.4))
+    sgn = np.ones(5)
+    sgn[1 + axis] = -1.0
+    mU = np.flip(st.U, axis=3 - axis) * sgn[:, None, None, None]
+    assert np.max(np.abs(st.U - mU)) <= 1e-12 * np.max(np.abs(st.U))
+    faces = [st.Bx, st.By, st.Bz]
+    bmax = max(np.max(np.abs(b)) for b in faces)
+    assert np.max(np.abs(st.By)) > 0.1 * bmax  # the blast has bent the field
+    for c, b in enumerate(faces):
+        s = (1.0 if c == axis else -1.0) if axis == 0 else (-1.0 if c == axis else 1.0)
+        assert np.max(np.abs(b - s * np.flip(b, axis=2 - axis))) <= 1e-12 * bmax, c
+
+
 def test_cyclic_axis_permutation_3d():
     """Relabelling the axes x -> y -> z -> x commutes with the step: the scheme treats
     the three directions by cyclic permutation (text after Eq. 11)."""
@@ -612,6 +634,21 @@ def test_plane_parallel_reduction(axis):
     assert np.max(np.abs(U - U[:, :1, :1, :1] * 0 - np.broadcast_to(
         U[(slice(None),) + tuple(slice(0, 1) if a != 2 - axis else slice(None) for a in range(3))],
         U.shape))) == 0.0
+
+
+def test_brio_wu_self_convergence():
+    """Brio-Wu (Section 3.4) has no closed-form solution: the 100-, 200- and 400-cell runs to
+    t = 0.1 converge to a 3200-cell run of the same scheme.  The L1 difference in rho (the
+    fine run averaged onto each grid) falls by at least 1.5 per doubling, as expected of a
+    solution with shocks and contacts; measured 8.7e-3, 5.0e-3, 2.6e-3."""
+    ref, _ = oracle.run(inputs.brio_wu(3200), 0.8, 0.1)
+    rho_ref = ref.U[0, 0, 0, :]
+    errs = []
+    for n in (100, 200, 400):
+        out, _ = oracle.run(inputs.brio_wu(n), 0.8, 0.1)
+        errs.append(np.mean(np.abs(out.U[0, 0, 0, :] - rho_ref.reshape(n, 3200 // n).mean(axis=1))))
+    assert errs[0] / errs[1] >= 1.5 and errs[1] / errs[2] >= 1.5, errs
+    assert errs[2] <= 4e-3, errs
 
 
 def test_sod_converges_to_exact_solution():
