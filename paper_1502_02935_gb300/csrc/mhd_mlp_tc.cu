@@ -1,7 +1,8 @@
-// mhd_mlp_tc.cu -- the surrogate's 64x64 layer on the 5th-generation tensor cores
-// (tcgen05.mma with the accumulator in tensor memory).
+// mhd_mlp_tc.cu -- the surrogate's 64-wide products on the 5th-generation tensor cores
+// (tcgen05.mma with the accumulators in tensor memory): inference (k_mlp_forward_tc, and
+// k_thermal_surrogate_tc in the thermal step) and training (k_mlp_grad_tc, further down).
 //
-// One CTA of 128 threads takes 128 rows.  Each thread computes its row of h1 =
+// Inference: one CTA of 128 threads takes 128 rows.  Each thread computes its row of h1 =
 // tanh(W1 x + b1) in FP32 and stores it as BF16 into shared memory in the canonical
 // K-major layout without swizzle: 8-row x 16-byte core matrices, the two core matrices
 // of one 16-wide K chunk 128 bytes apart (leading byte offset) and consecutive 8-row
