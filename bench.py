@@ -696,7 +696,7 @@ def run_table(args):
         row["oracle_sample"] = "64^3, 3 steps, 4 scalars"
         table["turbulence 256^3 with passive scalars"] = row
     if want("bow"):
-        # bow shock (Section 3.4): inflow at the left, Gaussian well, 1D; to the paper's last
+        # bow shock (Section 3.3): inflow at the left, Gaussian well, 1D; to the paper's last
         # time t = 0.375
         st, src, inflow = inputs.bow_shock(400)
         oracle.set_threads(1)

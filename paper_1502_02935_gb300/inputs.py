@@ -272,7 +272,7 @@ def rotor(n: int = 512, v0: float = 2.0, gamma: float = 1.4) -> State:
 
 
 def bow_shock(n: int = 400, psi0: float = 5.0, x0: float = 0.1):
-    """Flow through a potential well (Section 3.4): rho = 1, p = 1, vx = 1, gamma = 1.4 on
+    """Flow through a potential well (Section 3.3): rho = 1, p = 1, vx = 1, gamma = 1.4 on
     [-0.5, 0.5] (the domain is not given), Psi = -psi0 exp(-(x/x0)^2); steady inflow of the
     initial state at the left, free (outflow) at the right.  Returns (state, source,
     inflow)."""

@@ -1,5 +1,5 @@
 """GPU parity of the fixed-inflow boundary and the gravity source of the bow-shock test
-(Section 3.4) against the FP64 oracle.  Tolerances as in test_gpu_parity."""
+(Section 3.3) against the FP64 oracle.  Tolerances as in test_gpu_parity."""
 from __future__ import annotations
 
 import numpy as np

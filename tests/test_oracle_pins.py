@@ -378,7 +378,7 @@ def test_well_hydrostatic_residual_is_second_order():
 
 
 def test_bow_shock_moves_upstream_of_the_well_minimum():
-    """Bow-shock test of Section 3.4 (inflow at the left, free boundary at the right, well
+    """Bow-shock test of Section 3.3 (inflow at the left, free boundary at the right, well
     Psi0 = 5, x0 = 0.1): the shock that forms in the well moves upstream across the minimum
     and sits on the front (upstream) edge of the well at t = 0.375, as the paper describes."""
     st, src, inflow = inputs.bow_shock(400)
