@@ -235,6 +235,18 @@ def sod(n: int = 200) -> State:
                            0.0, 0.0, 0.0)
 
 
+def shu_osher(n: int = 800, amp: float = 0.2) -> State:
+    """Shu-Osher problem (Section 3.2) with B = 0, gamma = 1.4, on [0, 1], outflow: the printed
+    state rho = 3.857143, p = 10.33333, u = 2.629369 for x < 0.125, and rho = 1 + amp sin(16 pi x),
+    p = 1, u = 0 beyond.  amp = 0 leaves the shock alone."""
+    g = Geom(n, 1, 1, 0.0, 0.0, 0.0, 1.0 / n, 1.0, 1.0, (1, 1, 0, 0, 0, 0), 1.4)
+    x = g.centres()[0]
+    left = (x < 0.125)[None, None, :]
+    rho = np.where(left, 3.857143, 1.0 + amp * np.sin(16.0 * math.pi * x)[None, None, :])
+    return state_from_prim(g, rho, np.where(left, 2.629369, 0.0), 0.0, 0.0, np.where(left, 10.33333, 1.0),
+                           0.0, 0.0, 0.0)
+
+
 def sedov(nx: int = 512, ny: int = 768, r0: float = 0.01, e0: float = 1.0, p0: float = 1e-5,
           gamma: float = 1.4) -> State:
     """2D Sedov-Taylor blast (Section 3.7) with B = 0 on [-0.5, 0.5] x [-0.75, 0.75] (cells

@@ -651,6 +651,39 @@ def test_brio_wu_self_convergence():
     assert errs[2] <= 4e-3, errs
 
 
+def test_shu_osher_shock_moves_at_the_rankine_hugoniot_speed():
+    """Section 3.2 prints the state behind the Shu-Osher shock (tests/golden/
+    shu_osher_post_shock.json).  It is the Rankine-Hugoniot state of a Mach 3 shock running
+    into rho = 1, p = 1 at rest: rho ratio (g+1)M^2/((g-1)M^2+2), pressure ratio
+    (2gM^2-(g-1))/(g+1), u = s (1 - 1/rho ratio), s = M sqrt(g).  Without the density wave
+    ahead (amp = 0), the oracle moves that shock at s.  At t = 0.1 its density midpoint lies
+    within half a cell of 0.125 + s t at 400, 800 and 1600 cells (measured 0.17-0.18 cells,
+    the fixed offset of the captured profile).  Behind it the flow is supersonic (u > c), so
+    every wave the start-up of the discrete shock emits runs right, the slowest at u - c; the
+    state upstream of that wave (x < 0.15; u - c puts it at 0.19 by t = 0.1) is the printed
+    one to roundoff."""
+    gold = json.load(open(os.path.join(GOLDEN, "shu_osher_post_shock.json")))
+    g, b = gold["gamma"], gold["behind"]
+    M = 3.0
+    s = M * math.sqrt(g * gold["ahead"]["p"] / gold["ahead"]["rho"])
+    r_ratio = (g + 1) * M * M / ((g - 1) * M * M + 2)
+    assert abs(b["rho"] - r_ratio) <= 1e-6
+    assert abs(b["p"] - (2 * g * M * M - (g - 1)) / (g + 1)) <= 1e-5
+    assert abs(b["u"] - s * (1.0 - 1.0 / r_ratio)) <= 1e-6
+    for n in (400, 800, 1600):
+        st = inputs.shu_osher(n, amp=0.0)
+        out, _ = oracle.run(st, 0.8, 0.1)
+        rho = out.U[0, 0, 0, :]
+        x = st.geom.centres()[0]
+        mid = 0.5 * (b["rho"] + gold["ahead"]["rho"])
+        k = int(np.where(rho >= mid)[0].max())
+        xs = x[k] + (rho[k] - mid) / (rho[k] - rho[k + 1]) * (x[k + 1] - x[k])
+        assert abs(xs - (gold["x_shock"] + s * 0.1)) <= 0.5 / n, (n, xs)
+        up = x < 0.15
+        assert np.max(np.abs(rho[up] / b["rho"] - 1.0)) <= 1e-12, n
+        assert np.max(np.abs(out.U[1, 0, 0, up] / rho[up] / b["u"] - 1.0)) <= 1e-12, n
+
+
 def test_sod_converges_to_exact_solution():
     """Sod tube with B = 0 (Section 3.1; pure gas dynamics of the same scheme): L1 error
     in rho against the exact Riemann solution at t = 0.5 falls with resolution."""
