@@ -45,6 +45,7 @@ def _hydro(n, bc, seed):
 
 CASES = {
     "sod_300": lambda: inputs.sod(300),
+    "shu_osher_400": lambda: inputs.shu_osher(400),
     "hydro_periodic_37x29x23": lambda: _hydro((37, 29, 23), (0,) * 6, 7),
     "hydro_outflow_17x9x5": lambda: _hydro((17, 9, 5), (1,) * 6, 8),
     "sedov_64x96": lambda: inputs.sedov(64, 96, r0=0.08),
