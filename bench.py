@@ -214,6 +214,13 @@ def oracle_sample(target_s: float = 15.0, n: int = 64, max_steps: int = 50):
                       f"{el:.1f} s wall on {cores} host threads (FP64, plain C, OpenMP)"}
 
 
+def workload_config(n: int, world: int) -> dict:
+    """The workload both arms report: the problem, its size and the parallel layout."""
+    return {"workload": f"turbulence_{n}^3 periodic MHD, gamma=5/3, B=(0.1,0,0), rms Mach 2, CFL {CFL}",
+            "cells": n ** 3, "global_batch": world, "seq_len": 0,
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return 0
@@ -221,8 +228,8 @@ def run_reference(args, world, rank, pg):
     line = {"impl": "reference", "metric": "zone-updates/s", "value": cb["value"], "unit": "zone-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "turbulence_256^3 (oracle timed on a 64^3 sample of the same recipe)",
-                       "global_batch": 1, "seq_len": 0, "parallelism": "replicas"},
+            "config": dict(workload_config(args.n, args.gpus),
+                           sample="the FP64 oracle timed on a 64^3 box of the same recipe, on the host cores"),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -459,11 +466,9 @@ def run_ours(args, world, rank, local, pg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded solenoidal turbulence, no dataset)",
-        "config": {"workload": f"turbulence_{n}^3 periodic MHD, gamma=5/3, B=(0.1,0,0), rms Mach 2, CFL {CFL}, "
-                               "mixed precision (FP32 bulk, FP64 recovery+accumulation), graph replay",
-                   "cells": zones, "global_batch": world, "seq_len": 0,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (state 1.1 GB/replica, no flush)"},
+        "config": dict(workload_config(n, world),
+                       path="mixed precision (FP32 bulk, FP64 recovery+accumulation), graph replay",
+                       l2="inputs larger than L2 (state 1.1 GB/replica, no flush)"),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes},
