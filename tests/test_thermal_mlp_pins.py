@@ -24,6 +24,43 @@ LT = [1.0, 2.0, 3.0, 3.8, 4.0, 4.2, 5.0, 5.4, 6.0, 7.0, 8.0]
 TH = dict(rate_unit=5.4e-31, nh_per_rho=0.76, t_per_pr=72.7, cap=0.1, gamma_heat=2e-26, z=0.02)
 
 
+# The stand-in cooling table as defined for this build (log10 T [K], log10 Lambda [erg cm^3/s])
+# at Z = 0.02; Lambda is a power law in T between neighbouring knots, continued beyond the
+# end knots with the end segments' slopes, and scales as (0.2 + 0.8 Z / 0.02).
+LL = [-28.5, -27.0, -26.2, -25.9, -23.5, -21.8, -21.3, -21.2, -22.0, -22.7, -22.6]
+
+
+@pytest.mark.parametrize("z", [0.02, 0.0, 0.04])
+def test_cooling_table_knots_segments_and_metallicity(z):
+    """The stand-in Lambda(T, Z) against its definition: the printed value at every knot;
+    continuity across every interior knot (1e-12 relative); on each side of a knot the slope
+    of the segment on that side (a segment search shifted by one index fails here); the
+    midpoint of each segment on the straight line in log-log; the end segments continued
+    below 10 K and above 1e8 K; the metallicity scale 0.2 + 0.8 Z / 0.02."""
+    scale = 0.2 + 0.8 * z / 0.02
+    lam, _ = oracle.cooling([10.0 ** t for t in LT], z)
+    want = np.array([10.0 ** l for l in LL]) * scale
+    assert np.max(np.abs(lam / want - 1.0)) <= 1e-12
+    slopes = [(LL[k + 1] - LL[k]) / (LT[k + 1] - LT[k]) for k in range(len(LT) - 1)]
+    for k in range(1, len(LT) - 1):
+        t = 10.0 ** LT[k]
+        lo, s_lo = oracle.cooling([t * (1 - 1e-13)], z)
+        hi, s_hi = oracle.cooling([t * (1 + 1e-13)], z)
+        # the two sides differ only by the 2e-13 step in T along slopes of up to 12
+        assert abs(lo[0] / hi[0] - 1.0) <= 1e-12 + 1e-13 * (abs(s_lo[0]) + abs(s_hi[0])), (k, lo, hi)
+        assert s_lo[0] == pytest.approx(slopes[k - 1], rel=1e-14), k
+        assert s_hi[0] == pytest.approx(slopes[k], rel=1e-14), k
+    mids = [0.5 * (LT[k] + LT[k + 1]) for k in range(len(LT) - 1)]
+    lam, sl = oracle.cooling([10.0 ** t for t in mids], z)
+    wmid = np.array([10.0 ** (0.5 * (LL[k] + LL[k + 1])) for k in range(len(LT) - 1)]) * scale
+    assert np.max(np.abs(lam / wmid - 1.0)) <= 1e-12
+    assert np.max(np.abs(sl - np.array(slopes))) <= 1e-14
+    lam, sl = oracle.cooling([10.0 ** 0.5, 10.0 ** 8.5], z)
+    wend = np.array([10.0 ** (LL[0] - 0.5 * slopes[0]), 10.0 ** (LL[-1] + 0.5 * slopes[-1])]) * scale
+    assert np.max(np.abs(lam / wend - 1.0)) <= 1e-12
+    assert sl[0] == pytest.approx(slopes[0], rel=1e-14) and sl[1] == pytest.approx(slopes[-1], rel=1e-14)
+
+
 def test_power_law_cooling_closed_form_first_order():
     th = dict(TH, gamma_heat=0.0)
     T0 = 10 ** 5.95
