@@ -362,7 +362,11 @@ int mhd_mlp_grad_tc(long long n, const float* rows, const float* params, float* 
  *   cfl      : Courant number, > 0.
  *   U, Bface : device pointers to the state in the host format above (FP64).
  *   dt_out   : device pointer; receives cfl * min over cells and active axes of
- *              d / (|v_d| + c_fast,d), computed in FP64 as mhd_cfl_dt of an FP64 context.
+ *              d / (|v_d| + c_fast,d), computed in FP64 as mhd_cfl_dt of an FP64 context
+ *              without floors (density and pressure floors set by mhd_set_sources are
+ *              not applied here).  If any cell has rho <= 0, p <= 0 or a non-finite
+ *              value, *dt_out is NaN: the call is asynchronous, so the failure that
+ *              mhd_cfl_dt returns as a status arrives here in the result.
  *   stream   : cudaStream_t or NULL; the call is asynchronous on it.
  * Scratch is a fixed 32 KiB __device__ array inside the library, held by every GPU
  * that loads it until the process exits; the call allocates and frees nothing.

@@ -46,8 +46,13 @@ struct DenseDesc {
   double gamma;
 };
 
+// Minimum that keeps a NaN: a cell whose state cannot give a limit poisons the result.
+__device__ __forceinline__ double nan_min(double a, double b) { return (a < b || a != a) ? a : b; }
+
 // CFL limit min over active axes of d / (|v_d| + c_fast,d) at cell (i, j, k), in FP64,
-// from the dense host-format arrays: the same formula as the step's recovery phase.
+// from the dense host-format arrays: the same formula as the step's recovery phase,
+// without density or pressure floors.  A cell with rho <= 0, p <= 0 or a non-finite
+// value has no limit: it returns NaN.
 __device__ double cell_limit(const DenseDesc& D, const double* __restrict__ U,
                              const double* __restrict__ Bx, const double* __restrict__ By,
                              const double* __restrict__ Bz, int i, int j, int k) {
@@ -66,6 +71,7 @@ __device__ double cell_limit(const DenseDesc& D, const double* __restrict__ U,
   const double v[3] = {mx * irho, my * irho, mz * irho};
   const double b[3] = {sbx * 0.5, sby * 0.5, sbz * 0.5};
   const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  if (!(rho > 0.0) || !(p > 0.0) || !(fabs(e) < INFINITY) || !(bb < INFINITY) || !(m2 < INFINITY)) return NAN;
   double lim = INFINITY;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -81,8 +87,7 @@ __device__ double block_min(double v) {
   __shared__ double red[kBlock / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w < v ? w : v;
+    v = nan_min(__shfl_xor_sync(0xffffffffu, v, o), v);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) red[warp] = v;
@@ -91,8 +96,7 @@ __device__ double block_min(double v) {
   if (warp == 0) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double w = __shfl_xor_sync(0xffffffffu, v, o);
-      v = w < v ? w : v;
+      v = nan_min(__shfl_xor_sync(0xffffffffu, v, o), v);
     }
   }
   return v;
@@ -113,8 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_cfl_partials(DenseDesc D, const doub
     const long long q = c / D.n[0];
     const int j = (int)(q % D.n[1]);
     const int k = (int)(q / D.n[1]);
-    const double t = cell_limit(D, U, Bx, By, Bz, i, j, k);
-    lim = t < lim ? t : lim;
+    lim = nan_min(cell_limit(D, U, Bx, By, Bz, i, j, k), lim);
   }
   lim = block_min(lim);
   if (threadIdx.x == 0) partials[blockIdx.x] = lim;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kBlock) k_cfl_partials(DenseDesc D, const doub
 __global__ void __launch_bounds__(kBlock) k_cfl_final(const double* __restrict__ partials, int nblocks,
                                                       double cfl, double* __restrict__ dt_out) {
   double lim = INFINITY;
-  for (int b = threadIdx.x; b < nblocks; b += kBlock) lim = partials[b] < lim ? partials[b] : lim;
+  for (int b = threadIdx.x; b < nblocks; b += kBlock) lim = nan_min(partials[b], lim);
   lim = block_min(lim);
   if (threadIdx.x == 0) *dt_out = cfl * lim;
 }

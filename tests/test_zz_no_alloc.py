@@ -7,6 +7,8 @@ library, so this test checks that two calls in a row (different states, one arra
 each agree with mhd_cfl_dt of an FP64 context, and that a patch larger than the
 fixed scratch is refused.  The file name makes pytest collect it last.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -48,3 +50,21 @@ def test_noalloc_refuses_patches_beyond_the_fixed_scratch():
     dummy = torch.zeros(1, dtype=torch.float64, device="cuda")
     rc = mhd.cfl_dt_noalloc(g, 0.4, dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), 0)
     assert rc == -1
+
+
+def test_noalloc_reports_a_cell_without_a_limit_as_nan():
+    """A cell with negative pressure has no CFL limit; mhd_cfl_dt returns that as a status.
+    The allocation-free call is asynchronous, so it reports it in the result: dt is NaN
+    (not the minimum over the other cells)."""
+    import torch
+    st = inputs.turbulence((20, 16, 12), seed=23)
+    U = st.U.copy()
+    U[4, 5, 7, 9] = 0.0  # E = 0 with rho, m > 0: p < 0 at one cell
+    st = st.replace(U=U)
+    Ud, Bd = _device_state(st)
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rc = mhd.cfl_dt_noalloc(st.geom, 0.4, Ud.data_ptr(), Bd.data_ptr(), dt_dev.data_ptr(), stream.cuda_stream)
+    assert rc == 0
+    stream.synchronize()
+    assert math.isnan(float(dt_dev.item()))
