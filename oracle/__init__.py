@@ -30,7 +30,14 @@ class OrcPatch(C.Structure):
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
                 ("bc", C.c_int * 6), ("gamma", C.c_double), ("riemann", C.c_int), ("recon", C.c_int),
-                ("inflow", (C.c_double * 8) * 6)]
+                ("inflow", (C.c_double * 8) * 6), ("upwind_eps", C.c_double)]
+
+
+# Width of Eq. 11's "no contact motion" band (|F_rho| <= eps rho_max max|S|): zero to the
+# precision of FP64 data after the pressure recovery's cancellation (the default), and the
+# same reading for data rounded to FP32 (the bulk arithmetic of the mixed path).
+EQ11_EPS_FP64 = 2.0 ** -32
+EQ11_EPS_FP32 = 64 * 2.0 ** -23
 
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics.  HLLC
@@ -78,6 +85,8 @@ def lib():
             L.orc_step_scalars.argtypes = [C.POINTER(OrcPatch), C.POINTER(OrcSource), dp, dp, dp, dp, C.c_int, dp,
                                            dp, C.c_double]
             L.orc_step_scalars.restype = C.c_int
+            L.orc_stage_emf.argtypes = [C.POINTER(OrcPatch), dp, dp, dp, dp, C.c_int, dp]
+            L.orc_stage_emf.restype = C.c_int
             L.orc_hlld_batch.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_riemann_batch.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp]
             L.orc_reconstruct_1d.argtypes = [C.c_int, dp, dp, dp]
@@ -116,9 +125,12 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def patch_struct(g, riemann: str = "hlld", recon: str = "kappa_third", inflow=None) -> OrcPatch:
-    """``inflow``: {side: [rho, vx, vy, vz, p, Bx, By, Bz]} for the sides whose bc is 2."""
+def patch_struct(g, riemann: str = "hlld", recon: str = "kappa_third", inflow=None,
+                 eq11_eps: float | None = None) -> OrcPatch:
+    """``inflow``: {side: [rho, vx, vy, vz, p, Bx, By, Bz]} for the sides whose bc is 2;
+    ``eq11_eps``: width of Eq. 11's no-motion band (None: EQ11_EPS_FP64)."""
     p = OrcPatch()
+    p.upwind_eps = float(EQ11_EPS_FP64 if eq11_eps is None else eq11_eps)
     p.riemann = RIEMANN[riemann]
     p.recon = RECON[recon]
     for side, w in (inflow or {}).items():
@@ -151,14 +163,15 @@ def _copy_state(st):
 
 
 def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str = "hlld",
-         recon: str = "kappa_third", inflow=None):
+         recon: str = "kappa_third", inflow=None, eq11_eps=None):
     """``nsteps`` van Leer steps of fixed size dt; returns a new State.  If ``floored``
     is a list, the per-step counts of cells changed by the end-of-step floors are
     appended to it.  ``riemann``: "hlld", "hllc" or "hll"; ``recon``: a key of RECON;
-    ``inflow``: the states of the inflow sides (see patch_struct)."""
+    ``inflow``: the states of the inflow sides (see patch_struct); ``eq11_eps``: width
+    of Eq. 11's no-motion band (None: EQ11_EPS_FP64)."""
     L = lib()
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom, riemann, recon, inflow), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon, inflow, eq11_eps), source_struct(source)
     for _ in range(nsteps):
         n = L.orc_step(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
         if n < 0:
@@ -169,14 +182,14 @@ def step(st, dt: float, source=None, nsteps: int = 1, floored=None, riemann: str
 
 
 def step_scalars(st, S, dt: float, source=None, riemann: str = "hlld", recon: str = "kappa_third", inflow=None,
-                 inflow_x=None):
+                 inflow_x=None, eq11_eps=None):
     """One van Leer step that also advects passive scalars: S is rho X, shape
     (ns, nz, ny, nx); ``inflow_x`` = {side: [X_0, ..., X_ns-1]} beyond inflow sides.
     Returns (State, S)."""
     U, Bx, By, Bz = _copy_state(st)
     S = np.ascontiguousarray(S, dtype=np.float64).copy()
     ns = S.shape[0]
-    p, s = patch_struct(st.geom, riemann, recon, inflow), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon, inflow, eq11_eps), source_struct(source)
     ix = np.zeros(6 * max(ns, 1))
     for side, xs in (inflow_x or {}).items():
         ix[int(side) * ns:(int(side) + 1) * ns] = xs
@@ -192,11 +205,23 @@ def cfl_dt(st, cfl: float, source=None, inflow=None) -> float:
                                   _p(U), _p(Bx), _p(By), _p(Bz), cfl))
 
 
+def stage_emf(st, order: int = 1, eq11_eps=None) -> np.ndarray:
+    """The corner EMFs (Eq. 9-11) of one stage for the state given: order 1 is the
+    predictor's donor-cell stage, order 2 the corrector's.  Returns E of shape
+    (3, nz, ny, nx); E[c][k, j, i] is the edge along axis c at cell (i, j, k)'s low corner."""
+    U, Bx, By, Bz = _copy_state(st)
+    nx, ny, nz = st.geom.nx, st.geom.ny, st.geom.nz
+    E = np.zeros((3, nz, ny, nx))
+    if lib().orc_stage_emf(C.byref(patch_struct(st.geom, eq11_eps=eq11_eps)), _p(U), _p(Bx), _p(By), _p(Bz), int(order), _p(E)) != 0:
+        raise ValueError("orc_stage_emf rejected its arguments")
+    return E
+
+
 def run(st, cfl: float, t_end: float, max_steps: int = 10 ** 9, source=None, riemann: str = "hlld",
-        recon: str = "kappa_third", inflow=None):
+        recon: str = "kappa_third", inflow=None, eq11_eps=None):
     """Advance to t_end with CFL time steps; returns (State, steps)."""
     U, Bx, By, Bz = _copy_state(st)
-    p, s = patch_struct(st.geom, riemann, recon, inflow), source_struct(source)
+    p, s = patch_struct(st.geom, riemann, recon, inflow, eq11_eps), source_struct(source)
     n = lib().orc_run(C.byref(p), C.byref(s), _p(U), _p(Bx), _p(By), _p(Bz), float(cfl),
                       float(t_end), int(max_steps))
     if n < 0:

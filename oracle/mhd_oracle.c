@@ -37,6 +37,10 @@ enum { WR = 0, WVX = 1, WVY = 2, WVZ = 3, WP = 4, WBX = 5, WBY = 6, WBZ = 7 };
 
 #define GHOST 3
 
+/* Default width of Eq. 11's "no contact motion" band, relative to the face's mass-flux
+ * scale (see the corner EMFs below). */
+#define UPWIND_EPS_FP64 (1.0 / 4294967296.0)
+
 typedef struct {
   int n[3];     /* interior cells */
   int g[3];     /* ghost layers (GHOST on active axes, 0 on trivial ones) */
@@ -46,6 +50,7 @@ typedef struct {
   double d[3], lo[3], gamma;
   int riemann; /* ORC_RIEMANN_* */
   int recon;   /* ORC_RECON_* */
+  double upwind_eps; /* width of Eq. 11's "no contact motion" band, relative to sigma */
   int inflow[6];           /* side has an inflow boundary */
   double in_u[6][NF];      /* its state: conserved cell fields and the three field components */
   double in_w[6][NF];      /* and its primitives rho, vx, vy, vz, p, Bx, By, Bz */
@@ -92,6 +97,8 @@ static int make_grid(const orc_patch* p, grid* G) {
   G->riemann = p->riemann;
   if (p->recon < ORC_RECON_KAPPA_THIRD || p->recon > ORC_RECON_PRINTED) return -1;
   G->recon = p->recon;
+  if (!(p->upwind_eps >= 0.0) || !(p->upwind_eps < 1.0)) return -1;
+  G->upwind_eps = p->upwind_eps > 0.0 ? p->upwind_eps : UPWIND_EPS_FP64;
   for (int side = 0; side < 6; ++side) {
     if (!G->inflow[side]) continue;
     const double* w = p->inflow[side];
@@ -636,15 +643,19 @@ static void compute_fluxes(const grid* G, int d, int order, double* const W[NF],
  * the corrections is the one for which a flow that varies along one axis only
  * gives back the face EMF exactly; the upwind side in Eq. 11 is chosen by the sign
  * of the Riemann mass flux F_rho through that face.  Eq. 11's "otherwise" (no
- * contact motion) is read as |F_rho| <= UPWIND_EPS * sigma, sigma = max(rho_L, rho_R)
- * max(|S_L|, |S_R|) the face's mass-flux scale: a mass flux that is zero in exact
- * arithmetic comes out as a few rounding errors of sigma, with either sign.
+ * contact motion, F_rho = 0) is taken as zero to the precision of the data: |F_rho| <=
+ * eps * sigma, sigma = max(rho_L, rho_R) max(|S_L|, |S_R|) the face's mass-flux scale.
+ * A mass flux that is zero in exact arithmetic comes out of the HLLD formulas as rounding
+ * of sigma, of either sign, and that rounding includes the one of the recovered pressure:
+ * p = (gamma-1)(E - kinetic - magnetic) keeps a relative error of about 2^-52 times
+ * E / (thermal energy), which reaches 1e3-1e4 at Mach 30-100 or low beta.  The default
+ * eps = 2^-32 (UPWIND_EPS_FP64) lies two orders above that rounding; any slower motion is
+ * upwinded.  A patch may set another eps (orc_patch.upwind_eps): the same reading for
+ * data rounded to FP32 takes 64 * 2^-23.
  * If only one of a, b is active the edge EMF is that axis' face EMF. */
-#define UPWIND_EPS 1e-5
-
-static double upwind(double fr, double sigma, double left, double right) {
-  if (fr > UPWIND_EPS * sigma) return left;
-  if (fr < -UPWIND_EPS * sigma) return right;
+static double upwind(double fr, double sigma, double eps, double left, double right) {
+  if (fr > eps * sigma) return left;
+  if (fr < -eps * sigma) return right;
   return 0.5 * (left + right);
 }
 
@@ -694,16 +705,16 @@ static void compute_emf(const grid* G, double* const W[NF], double* const Fl[3][
           }
           double da = G->d[a], db = G->d[b];
           /* d/db on a-face (a-1/2, b): between face point b and corner b-1/2 -> (b-1/4) */
-          double dEdb_q = upwind(Fl[a][RHO][o], Fl[a][BXF + a][o], 2.0 * (ec[1] - Eb_am) / db,
+          double dEdb_q = upwind(Fl[a][RHO][o], Fl[a][BXF + a][o], G->upwind_eps, 2.0 * (ec[1] - Eb_am) / db,
                                  2.0 * (ec[0] - Eb_a) / db);
           /* d/db on a-face (a-1/2, b-1): between corner b-1/2 and face point b-1 -> (b-3/4) */
-          double dEdb_3q = upwind(Fl[a][RHO][ob], Fl[a][BXF + a][ob], 2.0 * (Eb_am - ec[3]) / db,
+          double dEdb_3q = upwind(Fl[a][RHO][ob], Fl[a][BXF + a][ob], G->upwind_eps, 2.0 * (Eb_am - ec[3]) / db,
                                   2.0 * (Eb_a - ec[2]) / db);
           /* d/da on b-face (a, b-1/2) -> (a-1/4) */
-          double dEda_q = upwind(Fl[b][RHO][o], Fl[b][BXF + b][o], 2.0 * (ec[2] - Ea_bm) / da,
+          double dEda_q = upwind(Fl[b][RHO][o], Fl[b][BXF + b][o], G->upwind_eps, 2.0 * (ec[2] - Ea_bm) / da,
                                  2.0 * (ec[0] - Ea_b) / da);
           /* d/da on b-face (a-1, b-1/2) -> (a-3/4) */
-          double dEda_3q = upwind(Fl[b][RHO][oa], Fl[b][BXF + b][oa], 2.0 * (Ea_bm - ec[3]) / da,
+          double dEda_3q = upwind(Fl[b][RHO][oa], Fl[b][BXF + b][oa], G->upwind_eps, 2.0 * (Ea_bm - ec[3]) / da,
                                   2.0 * (Ea_b - ec[1]) / da);
           E[o] = 0.25 * (Ea_b + Ea_bm + Eb_a + Eb_am) + db / 8.0 * (dEdb_3q - dEdb_q) +
                  da / 8.0 * (dEda_3q - dEda_q);
@@ -1081,6 +1092,32 @@ int orc_step(const orc_patch* p, const orc_source* s, double* U, double* Bx, dou
   store_state(&G, w.Un, U, Bout);
   free(w.block);
   return floored > 2147483647L ? 2147483647 : (int)floored;
+}
+
+/* The corner EMFs of one stage (Eq. 9-11) for the state given, without updating it:
+ * order 1 is the predictor's donor-cell stage, order 2 the corrector's reconstruction.
+ * E[c][k][j][i] receives E_c at the cell's low edge along c (for E_z: (i-1/2, j-1/2, k)). */
+int orc_stage_emf(const orc_patch* p, const double* U, const double* Bx, const double* By,
+                  const double* Bz, int order, double* E) {
+  grid G;
+  work w;
+  if (order < 1 || order > 2 || make_grid(p, &G) || work_alloc(&G, &w)) return -1;
+  set_floors(&G, NULL);
+  const double* Bin[3] = {Bx, By, Bz};
+  load_state(&G, U, Bin, w.Un);
+  fill_ghosts(&G, w.Un);
+  cons_to_prim(&G, w.Un, w.W);
+  for (int d = 0; d < 3; ++d)
+    if (G.act[d]) compute_fluxes(&G, d, order, w.W, w.Un, w.Fl[d]);
+  compute_emf(&G, w.W, w.Fl, w.Ed);
+  long nc = (long)G.n[0] * G.n[1] * G.n[2];
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < G.n[2]; ++k)
+      for (int j = 0; j < G.n[1]; ++j)
+        for (int i = 0; i < G.n[0]; ++i)
+          E[c * nc + host_cell(&G, i, j, k)] = w.Ed[c][ix(&G, i, j, k)];
+  free(w.block);
+  return 0;
 }
 
 double orc_cfl_dt(const orc_patch* p, const orc_source* s, const double* U, const double* Bx,

@@ -48,6 +48,11 @@ typedef struct {
   /* primitive state [rho, vx, vy, vz, p, Bx, By, Bz] beyond each side whose bc is
    * ORC_BC_INFLOW (same side order as bc) */
   double inflow[6][8];
+  /* Eq. 11 takes the mean of the two one-sided EMF derivatives where the face's mass flux
+   * is zero; here: where |F_rho| <= upwind_eps * rho_max * max|S|.  0 takes 2^-32, zero to
+   * the precision of FP64 data after the pressure recovery's cancellation; 64 * 2^-23 is
+   * the same reading for data rounded to FP32. */
+  double upwind_eps;
 } orc_patch;
 
 typedef struct {
@@ -77,6 +82,13 @@ int orc_step(const orc_patch* p, const orc_source* s, double* U, double* Bx,
  * orc_step. */
 int orc_step_scalars(const orc_patch* p, const orc_source* s, double* U, double* Bx, double* By,
                      double* Bz, int ns, double* S, const double* inflow_x, double dt);
+
+/* The corner EMFs E_x, E_y, E_z of one stage (Eq. 9-11) for the state given: order 1 is
+ * the predictor's donor-cell stage, order 2 the corrector's reconstruction.  E holds
+ * [3][nz][ny][nx]; E[c] at cell (i, j, k) is the edge along c at the cell's low corner
+ * (E_z at (i-1/2, j-1/2, k)).  The state is not changed.  Returns 0, or -1 on bad arguments. */
+int orc_stage_emf(const orc_patch* p, const double* U, const double* Bx, const double* By,
+                  const double* Bz, int order, double* E);
 
 /* cfl * min over interior cells and active axes of d/(|v_d| + c_f,d), from the
  * recovered primitives (with the floors of s when s is not NULL). */

@@ -841,11 +841,18 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
 // -------------------------------------------------------------- phase: EMF ----
 // Corner EMF E_C at edge (A-1/2, B-1/2), (A, B, C) cyclic (Eq. 9-11): mean of the four
 // face EMFs plus upwinded one-sided corrections, the upwind side given by the sign of
-// the Riemann mass flux F_rho; Eq. 11's "otherwise" is |F_rho| <= 1e-5 sigma (a flux
-// that is zero in exact arithmetic comes out as rounding noise of either sign);
-// (db/8) * 2/db = 1/4.
+// the Riemann mass flux F_rho.  Eq. 11's "otherwise" (F_rho = 0) is read as zero to the
+// precision of the data the flux was computed from: |F_rho| <= eps_R sigma.  FP64 path:
+// eps = 2^-32, two orders above the rounding of FP64 data after the pressure recovery's
+// cancellation (relative error ~2^-52 E / thermal energy, up to 1e3-1e4).  FP32 bulk of
+// the mixed path: eps = 64 * 2^-23, the same reading for data rounded to FP32.  A flux that
+// is zero in exact arithmetic comes out as rounding of sigma, of either sign; (db/8) * 2/db
+// = 1/4.
+template <class R> struct UpwindEps;
+template <> struct UpwindEps<double> { static constexpr double v = 1.0 / 4294967296.0; };
+template <> struct UpwindEps<float> { static constexpr float v = 64.0f * 1.1920928955078125e-7f; };
 template <class R> __device__ __forceinline__ R upwind(R fr, R sigma, R left, R right) {
-  const R t = R(1e-5) * sigma;
+  const R t = UpwindEps<R>::v * sigma;
   return fr > t ? left : (fr < -t ? right : R(0.5) * (left + right));
 }
 

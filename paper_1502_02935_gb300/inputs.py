@@ -168,6 +168,33 @@ def smooth_random(g: Geom, seed: int, bamp: float = 0.5) -> State:
     return state_from_prim(g, rho, vx, vy, vz, p, Bx, By, Bz)
 
 
+def slow_contact(n=(24, 16, 12), u: float = 3e-6, seed: int = 7) -> State:
+    """Density contacts carried slowly along x on a periodic box: rho alternates between 1
+    and 2 in x-blocks of seeded widths, vx = u everywhere, and vy, vz, p, By(z), Bz(y) and a
+    uniform Bx vary only across x, so that every x-face of the initial state holds an
+    isolated contact whose mass flux is about u / (2 c_f) of the face's scale."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    g = Geom(nx, ny, nz, 0.0, 0.0, 0.0, 1.0 / nx, 1.0 / ny, 1.0 / nz, (0,) * 6, 5.0 / 3.0)
+    cuts = np.sort(rng.choice(np.arange(1, nx), size=3, replace=False))
+    rho_x = np.ones(nx)
+    for m, c in enumerate(cuts):
+        if m % 2 == 0:
+            rho_x[c:] = 2.0
+        else:
+            rho_x[c:] = 1.0
+    x, y, z = g.centres()
+    Y, Z = y[None, :, None], z[:, None, None]
+    ph = rng.uniform(0, 2 * np.pi, 6)
+    vy = 0.3 * np.sin(2 * np.pi * Y + ph[0]) * np.cos(2 * np.pi * Z + ph[1]) + 0 * x[None, None, :]
+    vz = 0.2 * np.cos(2 * np.pi * Y + ph[2]) + 0.1 * np.sin(4 * np.pi * Z + ph[3]) + 0 * x[None, None, :]
+    p = 1.0 + 0.1 * np.sin(2 * np.pi * Y + ph[4]) * np.sin(2 * np.pi * Z + ph[5]) + 0 * x[None, None, :]
+    rho = rho_x[None, None, :] * np.ones((nz, ny, 1))
+    By = (0.5 + 0.2 * np.sin(2 * np.pi * z))[:, None, None] * np.ones((1, ny + 1, nx))
+    Bz = (-0.3 + 0.25 * np.cos(2 * np.pi * y))[None, :, None] * np.ones((nz + 1, 1, nx))
+    return state_from_prim(g, rho, u, vy, vz, p, 0.6, By, Bz)
+
+
 # ---------------------------------------------------------------- workloads --
 
 def brio_wu(n: int = 800, axis: int = 0, transverse: int = 1) -> State:

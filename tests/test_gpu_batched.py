@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs, mhd
-from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+from tests.test_gpu_parity import EQ11, FP64_TOL, MIXED_TOL, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +57,7 @@ def test_persistent_per_patch_dt_matches_oracle(precision, tol):
     for p, st in enumerate(sts):
         want_dt = oracle.cfl_dt(st, 0.4)
         assert abs(dts[p] - want_dt) <= (1e-14 if precision == "fp64" else 1e-6) * want_dt
-        ref = oracle.step(st, dts[p])
+        ref = oracle.step(st, dts[p], eq11_eps=EQ11[precision])
         assert_close(g.get_state(p), ref, tol, f"patch {p}", normalized=(precision == "mixed"))
     g.close()
 
@@ -116,6 +116,7 @@ def test_batch_with_inflow_solvers_and_scalars_matches_oracle(precision, tol):
         want_dt = oracle.cfl_dt(st, 0.4, inflow=infl)
         assert abs(dts[p] - want_dt) <= (1e-14 if precision == "fp64" else 1e-6) * want_dt
         ref, Sref = oracle.step_scalars(st, S[p], dts[p], riemann="hllc", recon="kappa_zero", inflow=infl,
+                                        eq11_eps=EQ11[precision],
                                         inflow_x=xs if p == 1 else None)
         assert_close(g.get_state(p), ref, tol, f"patch {p}", normalized=(precision == "mixed"))
         Sg = g.get_scalar_state(p)

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs, mhd
-from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+from tests.test_gpu_parity import EQ11, FP64_TOL, MIXED_TOL, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +54,7 @@ def _run(case, precision, nsteps, cfl=0.4):
     for _ in range(nsteps):
         dt = oracle.cfl_dt(ref, cfl, source=src, inflow=inflow)
         g.step(dt)
-        ref = oracle.step(ref, dt, source=src, inflow=inflow)
+        ref = oracle.step(ref, dt, source=src, inflow=inflow, eq11_eps=EQ11[precision])
     got = g.get_state(0)
     g.close()
     return got, ref

@@ -26,6 +26,11 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-6
+# The oracle each path is held to at these tolerances: Eq. 11's no-motion band read for the
+# precision of the path's data (FP64: 2^-32 of the mass-flux scale, the oracle's default;
+# mixed: 64 * 2^-23, FP32 rounding).  What the mixed path's reading costs against the
+# FP64 reading is measured separately (test_mixed_against_the_fp64_reading_of_eq11).
+EQ11 = {"fp64": None, "mixed": oracle.EQ11_EPS_FP32}
 
 
 def _fields(st):
@@ -64,6 +69,7 @@ CASES = {
     "orszag_tang_64x48": lambda: (inputs.orszag_tang(64, 48), None),
     "turbulence_37x29x23": lambda: (inputs.turbulence((37, 29, 23), seed=5), None),
     "blast_24": lambda: (inputs.blast(24, (0.3, 0.6, 0.45), (0.6, 0.0, 0.8)), None),
+    "slow_contact_24x16x12": lambda: (inputs.slow_contact((24, 16, 12)), None),
     "outflow_17x9x5": lambda: (inputs.smooth_random(_geom((17, 9, 5), (1,) * 6), 3), None),
     "mixed_bc_13x11x6": lambda: (inputs.smooth_random(_geom((13, 11, 6), (1, 1, 0, 0, 1, 1)), 4), None),
     "disc_gravity_20x18x8": lambda: (
@@ -85,7 +91,7 @@ def _run_pair(st, src, precision, nsteps, cfl=0.4, counts=None):
         dt = oracle.cfl_dt(ref, cfl, source=src)
         dts.append(dt)
         g.step(dt)
-        ref = oracle.step(ref, dt, source=src, floored=floored)
+        ref = oracle.step(ref, dt, source=src, floored=floored, eq11_eps=EQ11[precision])
     got = g.get_state(0)
     if counts is not None:
         counts.extend([g.metrics()["floored"], sum(floored)])
@@ -107,11 +113,55 @@ def test_fp64_multi_step_parity(case):
     assert_close(got, ref, 5 * FP64_TOL, case)
 
 
-@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("case", sorted(c for c in CASES if c != "slow_contact_24x16x12"))
 def test_mixed_one_step_parity(case):
     st, src = CASES[case]()
     got, ref, _ = _run_pair(st, src, "mixed", 1)
     assert_close(got, ref, MIXED_TOL, case, normalized=True)
+
+
+def test_mixed_one_step_parity_slow_contact():
+    """The slowly moving contacts put the corrector's x-face mass fluxes around 1e-6 to 1e-5
+    of their scale, across the edge of the mixed path's no-motion band (64 * 2^-23 = 7.6e-6):
+    there FP32 rounding of the flux decides between the mean and the upwind side, against the
+    oracle's FP64 flux under the same band.  Measured 7.6e-6 of the field's scale (B); bound
+    2e-5."""
+    st, src = CASES["slow_contact_24x16x12"]()
+    got, ref, _ = _run_pair(st, src, "mixed", 1)
+    assert_close(got, ref, 2e-5, "slow_contact_24x16x12", normalized=True)
+
+
+def _l1(a, b):
+    return float(np.sum(np.abs(a - b)) / max(np.sum(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mixed_against_the_fp64_reading_of_eq11(case):
+    """The mixed path's per-field error against the FP64 oracle under its default reading of
+    Eq. 11 (no-motion band 2^-32 of the mass-flux scale), one step.  Where a face's mass flux
+    lies between 2^-32 and 64 * 2^-23 of its scale the mixed path takes the mean of the two
+    one-sided EMF derivatives where the oracle upwinds: FP32 fluxes cannot tell such a motion
+    from rounding.  The edges involved change the face field by up to a few 1e-4 of B's scale
+    on the blast (measured 1.0e-3 of it after the flux and energy updates) and leave the
+    L1 error of every field at rounding level (<= 4e-7), except on the slowly moving contacts,
+    which put every x-face into that range (L1 2.4e-5 in the momentum).  Bounds: max 2e-3 of
+    the scale; L1 1e-6, and 5e-5 on the slow contacts."""
+    st, src = CASES[case]()
+    dt = oracle.cfl_dt(st, 0.4, source=src)
+    g = mhd.Grid(st, precision="mixed", cfl=0.4)
+    if src:
+        g.set_sources(**src)
+    g.step(dt)
+    got = g.get_state(0)
+    g.close()
+    ref = oracle.step(st, dt, source=src)
+    for name, (_, nm) in errors(got, ref).items():
+        assert nm <= 2e-3, (case, name, nm)
+    l1_bound = 5e-5 if case.startswith("slow_contact") else 1e-6
+    for name, a, b in (("rho", got.U[0], ref.U[0]), ("m", got.U[1:4], ref.U[1:4]), ("E", got.U[4], ref.U[4]),
+                       ("B", got.faces_flat(), ref.faces_flat())):
+        if np.any(b):
+            assert _l1(a, b) <= l1_bound, (case, name, _l1(a, b))
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("mixed", 1e-6)])
@@ -205,7 +255,7 @@ def test_full_size_turbulence_sampled_parity(precision, tol):
     floor = 1e-3 if precision == "fp64" else 1.0
     for c in samples:
         sub = _subbox(st, c, h)
-        out = oracle.step(sub, dt)
+        out = oracle.step(sub, dt, eq11_eps=EQ11[precision])
         for f, name in enumerate(("rho", "mx", "my", "mz", "E")):
             a = got.U[f, c[2], c[1], c[0]]
             b = out.U[f, h, h, h]
@@ -450,7 +500,7 @@ def test_full_size_disc_sampled_parity(precision, tol):
     M = {name: m for name, _, m in _fields(got)}
     for c in samples:
         win = _window(st, c, h)
-        out = oracle.step(win, dt, source=src)
+        out = oracle.step(win, dt, source=src, eq11_eps=EQ11[precision])
         out, _ = oracle.thermal_apply(out, dt, th)
         _sampled_compare(got, out, c, h, tol, precision, M, "disc")
 
@@ -475,7 +525,7 @@ def test_full_size_blast_batch_sampled_parity(precision, tol, scheme):
         M = {name: m for name, _, m in _fields(got)}
         n = (st.geom.nx, st.geom.ny, st.geom.nz)
         c = tuple(int(rng.integers(0, n[a])) for a in range(3))
-        out = oracle.step(_subbox(st, c, h), dts[p])
+        out = oracle.step(_subbox(st, c, h), dts[p], eq11_eps=EQ11[precision])
         _sampled_compare(got, out, c, h, tol, precision, M, f"patch {p}")
     g.close()
 

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs, mhd
-from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+from tests.test_gpu_parity import EQ11, FP64_TOL, MIXED_TOL, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +68,7 @@ def _run(st, precision, solver, nsteps, cfl=0.4):
     for _ in range(nsteps):
         dt = oracle.cfl_dt(ref, cfl)
         g.step(dt)
-        ref = oracle.step(ref, dt, riemann=solver)
+        ref = oracle.step(ref, dt, riemann=solver, eq11_eps=EQ11[precision])
     got = g.get_state(0)
     g.close()
     return got, ref

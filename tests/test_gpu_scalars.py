@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs, mhd
-from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+from tests.test_gpu_parity import EQ11, FP64_TOL, MIXED_TOL, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,8 @@ def test_scalars_match_oracle(case, precision, recon):
     for _ in range(nsteps):
         dt = oracle.cfl_dt(ref, 0.4, inflow=inflow)
         g.step(dt)
-        ref, Sref = oracle.step_scalars(ref, Sref, dt, recon=recon, inflow=inflow, inflow_x=inflow_x)
+        ref, Sref = oracle.step_scalars(ref, Sref, dt, recon=recon, inflow=inflow, inflow_x=inflow_x,
+                                        eq11_eps=EQ11[precision])
     got, Sg = g.get_state(0), g.get_scalar_state(0)
     g.close()
     tol = FP64_TOL if precision == "fp64" else MIXED_TOL

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs, mhd
-from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+from tests.test_gpu_parity import EQ11, FP64_TOL, MIXED_TOL, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,7 @@ def test_disc_step_with_plain_thermal_matches_oracle(precision, tol):
     got = g.get_state(0)
     stats = g.thermal_stats()
     g.close()
-    ref = oracle.step(st, dt, source=inputs.DISC_POTENTIAL)
+    ref = oracle.step(st, dt, source=inputs.DISC_POTENTIAL, eq11_eps=EQ11[precision])
     ref, status = oracle.thermal_apply(ref, dt, TH)
     assert stats["cells"] == st.geom.ncell and stats["capped"] == 0
     assert_close(got, ref, tol, precision, normalized=(precision == "mixed"))

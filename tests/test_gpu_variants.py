@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs, mhd
-from tests.test_gpu_parity import FP64_TOL, MIXED_TOL, assert_close
+from tests.test_gpu_parity import EQ11, FP64_TOL, MIXED_TOL, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +26,7 @@ def _run(st, precision, recon, nsteps, cfl=0.4):
     for _ in range(nsteps):
         dt = oracle.cfl_dt(ref, cfl)
         g.step(dt)
-        ref = oracle.step(ref, dt, recon=recon)
+        ref = oracle.step(ref, dt, recon=recon, eq11_eps=EQ11[precision])
     got = g.get_state(0)
     g.close()
     return got, ref
@@ -69,7 +69,7 @@ def test_rotor_per_step_matches_oracle(precision, recon):
         g.step(dt)
         got = g.get_state(0)
         g.close()
-        ref = oracle.step(ref, dt, recon=recon)
+        ref = oracle.step(ref, dt, recon=recon, eq11_eps=EQ11[precision])
         assert_close(got, ref, ROTOR_TOL[precision], f"rotor {recon}", normalized=True)
 
 

@@ -658,6 +658,86 @@ def test_plane_parallel_reduction(axis):
         U.shape))) == 0.0
 
 
+def _slow_contact_state(u):
+    """4 x 4 periodic plane: a density contact (rho = 1 in columns 0-1, 2 in columns 2-3)
+    carried at vx = u, vy varying by row, p and B = (0.6, 0.8, 0) uniform.  Every x-face
+    holds an isolated contact, whose HLLD flux is the exact upwind physical flux."""
+    g = inputs.Geom(4, 4, 1, 0.0, 0.0, 0.0, 0.25, 0.25, 1.0, (0,) * 6, 5.0 / 3.0)
+    rho = np.where(np.arange(4)[None, None, :] < 2, 1.0, 2.0) * np.ones((1, 4, 4))
+    vy = np.array([0.1, 0.3, -0.2, 0.05])[None, :, None] * np.ones((1, 4, 4))
+    return inputs.state_from_prim(g, rho, u, vy, 0.0, 1.0, 0.6, 0.8, 0.0), rho[0], vy[0]
+
+
+def _eq10_edge_ez(u, rho, vy, gam, bx=0.6, by=0.8, mean_on_x_faces=False):
+    """Eq. 10-11 evaluated by hand at every z-edge (i-1/2, j-1/2) of the donor-cell stage of
+    the slow-contact state.  x-face EMFs from the exact contact flux, y-face EMFs and mass
+    fluxes from the HLLD unit (pinned above), cell EMFs E_z = -(vx By - vy Bx); the upwind
+    side by the sign of the mass flux, the mean only where it is exactly zero (or, with
+    ``mean_on_x_faces``, on every x-face: what a threshold above the contact's motion does)."""
+    n = 4
+    ec = -(u * by - vy * bx)                         # (j, i)
+    ea = np.empty((n, n))                            # E_z on x-face (i-1/2, j)
+    fa = np.empty((n, n))                            # F_rho there
+    for j in range(n):
+        for i in range(n):
+            wl = np.array([rho[j, i - 1], u, vy[j, i - 1], 0.0, 1.0, 0.0, by, 0.0])
+            f = textbook.physical_flux(wl if u >= 0 else np.r_[rho[j, i], wl[1:]], bx, gam)
+            ea[j, i] = -f[6]
+            fa[j, i] = f[0]
+    eb = np.empty((n, n))                            # E_z on y-face (i, j-1/2)
+    fb = np.empty((n, n))
+    for j in range(n):
+        for i in range(n):
+            # y-normal frame: [rho, vy, vz, vx, p, -, Bz, Bx], normal field By
+            wl = np.array([rho[j - 1, i], vy[j - 1, i], 0.0, u, 1.0, 0.0, 0.0, bx])
+            wr = np.array([rho[j, i], vy[j, i], 0.0, u, 1.0, 0.0, 0.0, bx])
+            f = oracle.hlld(wl, wr, by, gam)[0]
+            eb[j, i] = f[7]
+            fb[j, i] = f[0]
+
+    def pick(fr, left, right):
+        return left if fr > 0 else (right if fr < 0 else 0.5 * (left + right))
+
+    fx = np.zeros_like(fa) if mean_on_x_faces else fa
+    E = np.empty((n, n))
+    for j in range(n):
+        for i in range(n):
+            im, jm = i - 1, j - 1
+            d_bq = pick(fx[j, i], ec[j, im] - eb[j, im], ec[j, i] - eb[j, i])
+            d_b3q = pick(fx[jm, i], eb[j, im] - ec[jm, im], eb[j, i] - ec[jm, i])
+            d_aq = pick(fb[j, i], ec[jm, i] - ea[jm, i], ec[j, i] - ea[j, i])
+            d_a3q = pick(fb[j, im], ea[jm, i] - ec[jm, im], ea[j, i] - ec[j, im])
+            E[j, i] = (0.25 * (ea[j, i] + ea[jm, i] + eb[j, i] + eb[j, im])
+                       + 0.25 * (d_b3q - d_bq) + 0.25 * (d_a3q - d_aq))
+    return E
+
+
+@pytest.mark.parametrize("u", [3e-6, -3e-6, 0.0])
+def test_corner_emf_upwinds_a_slowly_moving_contact(u):
+    """Eq. 11: the one-sided EMF derivatives of the corner formula come from the upwind side
+    of each face, and only a face without contact motion takes their mean.  A contact moving
+    at |vx| = 3e-6 carries a mass flux of about 1e-6 of the face's mass-flux scale
+    rho_max max|S|, four orders above the 2^-32 band of the FP64 reading; the oracle must
+    upwind it, and takes the mean at u = 0.  Checked against Eq. 10-11 evaluated by hand
+    from exactly known face fluxes.  With the band widened to FP32 rounding (64 * 2^-23,
+    the mixed path's reading) the same edges take the mean: the two readings differ there
+    by 5e-5 to 5e-4, eleven orders above the agreement asked."""
+    st, rho, vy = _slow_contact_state(u)
+    got = oracle.stage_emf(st, order=1)[2, 0]
+    want = _eq10_edge_ez(u, rho, vy, st.geom.gamma)
+    assert np.max(np.abs(got - want)) <= 1e-15
+    wide = oracle.stage_emf(st, order=1, eq11_eps=oracle.EQ11_EPS_FP32)[2, 0]
+    if u != 0.0:
+        sigma = 2.0 * 1.3  # rho_max times a lower bound of max|S| (c_f > 1.3 for rho <= 2)
+        assert oracle.EQ11_EPS_FP64 < abs(u) * 2.0 / sigma < oracle.EQ11_EPS_FP32
+        mean = _eq10_edge_ez(u, rho, vy, st.geom.gamma, mean_on_x_faces=True)
+        assert np.max(np.abs(wide - mean)) <= 1e-15
+        gap = np.abs(got[:, [0, 2]] - mean[:, [0, 2]])
+        assert np.min(gap) > 1e-4 * np.max(np.abs(got))  # measured 4e-4 to 4e-3 of it
+    else:
+        assert np.max(np.abs(wide - want)) <= 1e-15
+
+
 def test_brio_wu_self_convergence():
     """Brio-Wu (Section 3.4) has no closed-form solution: the 100-, 200- and 400-cell runs to
     t = 0.1 converge to a 3200-cell run of the same scheme.  The L1 difference in rho (the
