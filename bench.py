@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_CELLS = 256
+REF_SAMPLE_N = 64  # edge of the box the oracle arm times (the full box takes minutes per step)
 CFL = 0.4
 SEED = 1502
 # measured peaks (driver-written) with the recipe's fallback
@@ -70,10 +71,14 @@ KCLASS = {
 # FP64 pipe operations per clock per SM: the nominal 1.25 TFLOP/s of the part is
 # 152 SMs x 2 FMAs x 2 flops x ~2.06 GHz.  (A DFMA probe measured 1.0 TFLOP/s.)
 FP64_OPS_PER_SM_CLK = 2
+# The step's algorithmic HBM bytes per cell: read the 8 FP64 fields of U^n, write U^n+1.
+ALG_BYTES_PER_CELL = 128.0
 # DRAM bytes (read + write) per item of the dominant kernel, from one ncu capture of the
 # EMF + update kernel on turbulence 192^3 (2.195 GB per launch over 192^3 cells, planes
 # marched as on 256^3); scaled by the items of a launch.  Retake it when the kernel changes.
 MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 2.195e9 / 192 ** 3}
+MEASURED_DRAM_NOTE = {"emf_update": "ncu dram__bytes_read.sum + dram__bytes_write.sum at turbulence 192^3, "
+                                    "per cell, scaled to this launch"}
 
 
 def units_per_launch(cls: str, n: int) -> int:
@@ -224,12 +229,13 @@ def workload_config(n: int, world: int) -> dict:
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return 0
-    cb = oracle_sample(target_s=max(5.0, min(60.0, 2.0 * args.steps)))
+    cb = oracle_sample(target_s=max(5.0, min(60.0, 2.0 * args.steps)), n=REF_SAMPLE_N)
     line = {"impl": "reference", "metric": "zone-updates/s", "value": cb["value"], "unit": "zone-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args.n, args.gpus),
-                           sample="the FP64 oracle timed on a 64^3 box of the same recipe, on the host cores"),
+            "config": dict(workload_config(REF_SAMPLE_N, args.gpus),
+                           sample=f"the FP64 oracle timed on a {REF_SAMPLE_N}^3 box of the {args.n}^3 workload's "
+                                  f"recipe, on the host cores"),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -420,10 +426,19 @@ def run_ours(args, world, rank, local, pg):
         best = max(cand, key=lambda r: cand[r]["frac"])
         roofs[k] = dict(cand[best], others={r: round(cand[r]["frac"], 4) for r in cand if r != best})
     dom = max(roofs, key=lambda k: prof[k][0])
-    roof = dict(roofs[dom])
+    # The headline roofline of the dominant kernel on the algorithmic bytes of the step's
+    # definition: 128 B per cell (read the 8 FP64 fields of U^n, write those of U^n+1) times
+    # the n^3 cells one launch advances, over that kernel's mean event-timed launch.
+    t_dom = prof[dom][0] / prof[dom][1] / 1e3
+    alg_bytes = ALG_BYTES_PER_CELL * zones
     per_point = MEASURED_DRAM_BYTES_PER_POINT.get(dom)
-    roof.update({"traffic": per_point * units_per_launch(dom, n) if per_point else None, "kernel": dom,
-                 "traffic_note": "ncu DRAM bytes per cell at 192^3, scaled to this launch" if per_point else None})
+    roof = {"bound": "hbm", "achieved": alg_bytes / t_dom / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": alg_bytes / t_dom / 1e9 / hbm_peak, "kernel": dom, "launch_ms": t_dom * 1e3,
+            "alg_bytes_per_launch": alg_bytes, "peak_note": f"{peak_kind} hbm_gbs",
+            "traffic": per_point * units_per_launch(dom, n) if per_point else None,
+            "traffic_note": MEASURED_DRAM_NOTE.get(dom),
+            "step_frac": value / world * ALG_BYTES_PER_CELL / (hbm_peak * 1e9),
+            "access_model": roofs[dom]}
     shares = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
 
     # plain FP64 path on the same box
@@ -474,7 +489,7 @@ def run_ours(args, world, rank, local, pg):
                 "d2h_bytes_per_step": io_bytes},
         "gpu_launches": launches,
         "roofline": roof,
-        "hbm_alg_frac": value / world * 128.0 / (hbm_peak * 1e9),
+        "hbm_alg_frac": value / world * ALG_BYTES_PER_CELL / (hbm_peak * 1e9),
         "fp64_path": {"value": fp64_value, "unit": "zone-updates/s", "steps": k64},
         "kernel_shares": shares,
         "kernel_rooflines": roofs,
