@@ -274,12 +274,20 @@ int mhd_thermal_stats(mhd_ctx* ctx, unsigned long long* out4);
  *
  * mhd_surrogate_rows: copy up to max_rows harvested rows (6 floats each, in ring order) to
  * the host buffer rows_out; count_out (may be NULL) receives the number of rows held.
- * MHD_ERR_STATE if harvesting was never set up.  Synchronises the context's stream. */
+ * MHD_ERR_STATE if harvesting was never set up.  Synchronises the context's stream.
+ *
+ * mhd_surrogate_fallback_cells: the cells that the last surrogate thermal phase (of the
+ * context's last patch) handed to the plain integrator, as interior cell indices
+ * i + nx (j + ny k) in no particular order: up to max_cells of them into the host buffer
+ * cells_out; count_out (may be NULL) receives how many there were.  MHD_ERR_STATE before the
+ * first surrogate phase.  Synchronises the context's stream.  A diagnostic of the fallback
+ * rule (Section 3.10 stand-in; the paper has no surrogate). */
 int mhd_surrogate_harvest(mhd_ctx* ctx, long long capacity, int stride);
 int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double qmax,
                         double* loss_out, long long* rows_out);
 int mhd_surrogate_params(mhd_ctx* ctx, float* params_out, float* range_out);
 int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long long* count_out);
+int mhd_surrogate_fallback_cells(mhd_ctx* ctx, int* cells_out, long long max_cells, long long* count_out);
 
 /* Per-kernel timing.  While on, every launch is bracketed by a CUDA event pair on the
  * context's stream (steps are not replayed from a graph) and the elapsed times are summed

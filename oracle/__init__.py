@@ -114,6 +114,13 @@ def _bind_thermal(L):
     L.orc_thermal_apply.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(OrcThermal), dp, dp, dp, dp,
                                     C.c_double]
     L.orc_thermal_apply.restype = C.c_int
+    L.orc_surrogate_apply.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(OrcThermal), dp, dp, dp, dp, dp,
+                                      dp, C.c_double, ip, dp]
+    L.orc_surrogate_apply.restype = C.c_int
+    L.orc_bf16_round.argtypes = [C.c_long, dp, dp]
+    L.orc_mlp_forward_bf16.argtypes = [C.c_long, dp, dp, dp]
+    L.orc_mlp_forward_bf16.restype = None
+    L.orc_bf16_round.restype = None
     L.orc_mlp_forward.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, dp]
     L.orc_mlp_forward.restype = None
     L.orc_mlp_backward.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -313,6 +320,43 @@ def thermal_apply(st, dt: float, th: dict):
     t = thermal_struct(th)
     rc = lib().orc_thermal_apply(g.nx, g.ny, g.nz, g.gamma, C.byref(t), _p(U), _p(Bx), _p(By), _p(Bz), float(dt))
     return st.replace(U=U), int(rc)
+
+
+def bf16_round(v):
+    """Round to the nearest BF16 value (8 significant bits, ties to even), in FP64."""
+    v = np.ascontiguousarray(np.atleast_1d(v), dtype=np.float64)
+    out = np.empty_like(v)
+    lib().orc_bf16_round(v.size, _p(v), _p(out))
+    return out
+
+
+def mlp_forward_bf16(X, params):
+    """The surrogate network as the step evaluates it (FP64, h1 and W2 rounded to BF16) on
+    standardised rows X[n][4]; params: the 4545 values W1, b1, W2, b2, w3, b3."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 4)
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    assert prm.size == 4545
+    Y = np.empty(X.shape[0])
+    lib().orc_mlp_forward_bf16(X.shape[0], _p(X), _p(prm), _p(Y))
+    return Y
+
+
+def surrogate_apply(st, dt: float, th: dict, params, rng):
+    """The surrogate thermal update of a State as the step applies it (see
+    orc_surrogate_apply): ``params`` the 4545 network parameters (W1, b1, W2, b2, w3, b3),
+    ``rng`` the 10 range values (lo[4], s[4], qmax, dmax).  Returns (State, fallback mask
+    (nz, ny, nx), features (nz, ny, nx, 6) = standardised x[4], q, S, integrator status)."""
+    U, Bx, By, Bz = _copy_state(st)
+    g = st.geom
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    rg = np.ascontiguousarray(rng, dtype=np.float64)
+    assert prm.size == 4545 and rg.size == 10
+    fb = np.zeros((g.nz, g.ny, g.nx), dtype=np.int32)
+    feat = np.zeros((g.nz, g.ny, g.nx, 6))
+    t = thermal_struct(th)
+    rc = lib().orc_surrogate_apply(g.nx, g.ny, g.nz, g.gamma, C.byref(t), _p(prm), _p(rg), _p(U), _p(Bx), _p(By),
+                                   _p(Bz), float(dt), fb.ctypes.data_as(C.POINTER(C.c_int)), _p(feat))
+    return st.replace(U=U), fb.astype(bool), feat, int(rc)
 
 
 # --------------------------------------------------------------------- MLP ----

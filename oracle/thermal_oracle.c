@@ -240,3 +240,115 @@ double orc_mlp_backward(long n, const double* X, const double* Tg, const double*
   }
   return loss / (double)n;
 }
+
+/* -------------------------------------------------- surrogate thermal step ----
+ * The learned replacement of the integration above, as the step applies it per cell
+ * (Section 3.10 via S of Eq. 2; the network is the project's stand-in for the tabulated
+ * integration).  For each cell:
+ *   T, n_H, c_e as in orc_thermal_apply; Tc = T clamped to [10, 1e8] K;
+ *   features (log10 n_H, log10 Tc, log10 dt, Z), standardised x_s = (x - lo) s - 1;
+ *   explicit estimate D = rate(Tc) dt / (Tc ln 10) and its saturated scale S = D / (1 + |D|);
+ *   q = network(x_s), in FP64 with the hidden activations h1 and the weights W2 rounded to
+ *   BF16 (the operands of the 64 x 64 layer), the change of log10 T is d = q S;
+ *   fallback to the plain integrator when a standardised feature leaves [-1, 1], |q| > qmax,
+ *   |d| > dmax, or d is not finite;
+ *   otherwise T1 = Tc 10^d and dT = T1 - T, written Tc expm1(d ln 10) when no clamp acts
+ *   (Tc = T and T1 inside [10, 1e8]) and clamp(T1) - T otherwise; E += c_e dT. */
+
+/* round to the nearest BF16 value (8 significant bits), ties to even */
+static double bf16_round(double v) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  int e;
+  double m = frexp(v, &e); /* v = m 2^e, 0.5 <= |m| < 1 */
+  return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+void orc_bf16_round(long n, const double* v, double* out) {
+  for (long q = 0; q < n; ++q) out[q] = bf16_round(v[q]);
+}
+
+static double net_forward_bf16(const double* x, const double* W1, const double* b1, const double* W2b,
+                               const double* b2, const double* w3, double b3) {
+  double h1[HID];
+  for (int a = 0; a < HID; ++a) {
+    double z = b1[a];
+    for (int k = 0; k < 4; ++k) z += W1[a * 4 + k] * x[k];
+    h1[a] = bf16_round(tanh(z));
+  }
+  double y = b3;
+  for (int a = 0; a < HID; ++a) {
+    double z = b2[a];
+    for (int k = 0; k < HID; ++k) z += W2b[a * HID + k] * h1[k];
+    y += w3[a] * tanh(z);
+  }
+  return y;
+}
+
+/* The surrogate's network on rows X[n][4] (already standardised), as the step evaluates it:
+ * FP64 with h1 and W2 rounded to BF16.  params as below. */
+void orc_mlp_forward_bf16(long n, const double* X, const double* params, double* Y) {
+  const double *W1 = params, *b1 = W1 + HID * 4, *W2 = b1 + HID, *b2 = W2 + HID * HID, *w3 = b2 + HID;
+  double W2b[HID * HID];
+  for (int a = 0; a < HID * HID; ++a) W2b[a] = bf16_round(W2[a]);
+  for (long q = 0; q < n; ++q) Y[q] = net_forward_bf16(X + 4 * q, W1, b1, W2b, b2, w3, w3[HID]);
+}
+
+/* params: W1[64][4], b1[64], W2[64][64], b2[64], w3[64], b3 (4545 values); range: lo[4],
+ * s[4], qmax, dmax.  U is updated in place.  fallback[c] (may be NULL) receives 1 where the
+ * cell took the integrator; feat[6 c + 0..5] (may be NULL) the standardised features, q and S.
+ * Returns the integrator's status bits OR-ed over the fallback cells. */
+int orc_surrogate_apply(int nx, int ny, int nz, double gamma, const orc_thermal* q, const double* params,
+                        const double* range, double* U, const double* Bx, const double* By, const double* Bz,
+                        double dt, int* fallback, double* feat) {
+  th_par P = par_of(q);
+  const double *W1 = params, *b1 = W1 + HID * 4, *W2 = b1 + HID, *b2 = W2 + HID * HID, *w3 = b2 + HID;
+  const double b3 = w3[HID];
+  double W2b[HID * HID];
+  for (int a = 0; a < HID * HID; ++a) W2b[a] = bf16_round(W2[a]);
+  long nc = (long)nx * ny * nz;
+  int any = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : any)
+  for (long c = 0; c < nc; ++c) {
+    int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long)nx * ny));
+    double rho = U[c], mx = U[nc + c], my = U[2 * nc + c], mz = U[3 * nc + c], e = U[4 * nc + c];
+    double bx = 0.5 * (Bx[i + (long)(nx + 1) * (j + (long)ny * k)] + Bx[i + 1 + (long)(nx + 1) * (j + (long)ny * k)]);
+    double by = 0.5 * (By[i + (long)nx * (j + (long)(ny + 1) * k)] + By[i + (long)nx * (j + 1 + (long)(ny + 1) * k)]);
+    double bz = 0.5 * (Bz[i + (long)nx * (j + (long)ny * k)] + Bz[i + (long)nx * (j + (long)ny * (k + 1))]);
+    double vx = mx / rho, vy = my / rho, vz = mz / rho;
+    double p = (gamma - 1.0) * (e - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * (bx * bx + by * by + bz * bz));
+    double T = q->t_per_pr * p / rho;
+    double nh = q->nh_per_rho * rho;
+    double ce = rho / (q->t_per_pr * (gamma - 1.0));
+    double Tc = clampT(T);
+    double raw[4] = {log10(nh), log10(Tc), log10(dt), q->z};
+    double xs[4];
+    int inside = 1;
+    for (int f = 0; f < 4; ++f) {
+      xs[f] = (raw[f] - range[f]) * range[4 + f] - 1.0;
+      inside = inside && xs[f] >= -1.0 && xs[f] <= 1.0;
+    }
+    double D = rate(Tc, nh, ce, &P, NULL) * dt / (Tc * log(10.0));
+    double S = D / (1.0 + fabs(D));
+    double y = net_forward_bf16(xs, W1, b1, W2b, b2, w3, b3);
+    double d = y * S;
+    int fb = !(inside && fabs(y) <= range[8] && fabs(d) <= range[9]);
+    double dT;
+    if (fb) {
+      int st;
+      dT = integrate(T, nh, ce, dt, &P, &st) - T;
+      any |= st;
+    } else {
+      double T1 = Tc * pow(10.0, d);
+      if (Tc != T || !(T1 >= T_MIN && T1 <= T_MAX)) dT = clampT(T1) - T;
+      else dT = Tc * expm1(d * log(10.0));
+    }
+    U[4 * nc + c] = e + ce * dT;
+    if (fallback) fallback[c] = fb;
+    if (feat) {
+      for (int f = 0; f < 4; ++f) feat[6 * c + f] = xs[f];
+      feat[6 * c + 4] = y;
+      feat[6 * c + 5] = S;
+    }
+  }
+  return any;
+}

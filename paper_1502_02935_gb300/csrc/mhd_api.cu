@@ -1140,6 +1140,18 @@ int mhd_surrogate_rows(mhd_ctx* ctx, float* rows_out, long long max_rows, long l
   return MHD_OK;
 }
 
+int mhd_surrogate_fallback_cells(mhd_ctx* ctx, int* cells_out, long long max_cells, long long* count_out) {
+  if (!ctx || max_cells < 0 || (max_cells > 0 && !cells_out)) return MHD_ERR_ARG;
+  if (!ctx->fb_list || !ctx->fb_count) return fail(ctx, MHD_ERR_STATE, "the surrogate has not run");
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, ctx->fb_count, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const long long n = (long long)cnt < max_cells ? (long long)cnt : max_cells;
+  if (n > 0) CK(cudaMemcpy(cells_out, ctx->fb_list, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost));
+  if (count_out) *count_out = (long long)cnt;
+  return MHD_OK;
+}
+
 int mhd_surrogate_train(mhd_ctx* ctx, int epochs, int batch, double lr, unsigned long long seed, double qmax,
                         double* loss_out, long long* rows_out) {
   if (!ctx || epochs < 1 || batch < 64 || batch > (1 << 20) || !(lr > 0.0) || seed == 0) return MHD_ERR_ARG;

@@ -73,7 +73,7 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
            "mhd_mlp_forward_tc", "mhd_mlp_grad_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
            "mhd_set_inflow", "mhd_set_scalars", "mhd_set_scalar_state", "mhd_get_scalar_state",
-           "mhd_set_inflow_scalars"]
+           "mhd_set_inflow_scalars", "mhd_surrogate_fallback_cells"]
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics
 RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
@@ -128,6 +128,7 @@ def lib():
                                       C.POINTER(C.c_longlong)]
     L.mhd_surrogate_params.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.mhd_surrogate_rows.argtypes = [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
+    L.mhd_surrogate_fallback_cells.argtypes = [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
     L.mhd_mlp_forward.argtypes = [C.c_longlong, vp, vp, vp, vp]
     L.mhd_mlp_grad.argtypes = [C.c_longlong, vp, vp, vp, vp, vp]
     L.mhd_mlp_forward_tc.argtypes = [C.c_longlong, vp, vp, vp, vp]
@@ -306,6 +307,15 @@ class Grid:
         self._check(self.L.mhd_surrogate_rows(self.h, buf.ctypes.data, buf.shape[0], C.byref(held)),
                     "mhd_surrogate_rows")
         return buf[:min(buf.shape[0], held.value)].copy()
+
+    def surrogate_fallback_cells(self, max_cells: int) -> np.ndarray:
+        """Interior cell indices i + nx (j + ny k) that the last surrogate thermal phase
+        handed to the plain integrator (at most max_cells; unordered)."""
+        buf = np.zeros(max(int(max_cells), 0), dtype=np.int32)
+        held = C.c_longlong()
+        self._check(self.L.mhd_surrogate_fallback_cells(self.h, buf.ctypes.data, buf.size, C.byref(held)),
+                    "mhd_surrogate_fallback_cells")
+        return buf[:min(buf.size, held.value)].copy()
 
     def thermal_stats(self) -> dict:
         out = (C.c_ulonglong * 4)()

@@ -171,3 +171,122 @@ def test_mlp_backward_matches_torch_autograd():
     assert abs(L.item() - loss) < 1e-14
     for k in P:
         assert np.max(np.abs(tp[k].grad.numpy() - G[k])) < 1e-13
+
+
+# ------------------------------------------------------- surrogate thermal step ----
+
+def test_bf16_rounding_matches_torch_and_ties_to_even():
+    """The oracle's BF16 rounding (8 significant bits, nearest, ties to even) equals torch's
+    float32 -> bfloat16 conversion on random FP32 values over 60 binades, and takes the even
+    neighbour at exact ties."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    v = (rng.uniform(-1, 1, 200000) * 2.0 ** rng.integers(-30, 30, 200000)).astype(np.float32)
+    want = torch.tensor(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(oracle.bf16_round(v.astype(np.float64)), want)
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 0.75 + 2 ** -9, 0.0])
+    assert np.array_equal(oracle.bf16_round(ties), [1.0, 1 + 2 ** -6, -1.0, 0.75, 0.0])
+
+
+def _unit_network(b3=1.0):
+    """All weights zero and b3 = 1: the network returns q = 1 exactly."""
+    p = np.zeros(4545)
+    p[-1] = b3
+    return p
+
+
+def _cells(st, th):
+    g = st.geom
+    bx, by, bz = st.bcc()
+    rho = st.U[0]
+    p = (g.gamma - 1) * (st.U[4] - 0.5 * (st.U[1] ** 2 + st.U[2] ** 2 + st.U[3] ** 2) / rho
+                         - 0.5 * (bx * bx + by * by + bz * bz))
+    T = th["t_per_pr"] * p / rho
+    nh = th["nh_per_rho"] * rho
+    ce = rho / (th["t_per_pr"] * (g.gamma - 1))
+    return T, nh, ce
+
+
+def _wide_range(st, th, dt, qmax=10.0, dmax=10.0):
+    T, nh, _ = _cells(st, th)
+    raw = [np.log10(nh), np.log10(np.clip(T, 10.0, 1e8)), np.full(T.shape, np.log10(dt)), np.full(T.shape, th["z"])]
+    lo = [float(r.min()) - 0.1 for r in raw]
+    s = [2.0 / (float(r.max()) + 0.1 - l) for r, l in zip(raw, lo)]
+    return np.array(lo + s + [qmax, dmax])
+
+
+def test_surrogate_step_with_unit_network_is_the_explicit_change():
+    """With a network that returns q = 1 the applied change of log10 T is S = D / (1 + |D|),
+    D = rate(T) dt / (T ln 10): to first order in D the explicit Euler change rate(T) dt of
+    the isochoric equation, with rate = (n_H Gamma - n_H^2 Lambda(T, Z)) / (rate_unit c_e).
+    The remainder is second order, |dT - rate dt| <= 5 D^2 T (ln 10 D^2 from the saturation,
+    (ln 10 D)^2 / 2 from the exponential)."""
+    th = inputs.DISC_THERMAL
+    st = inputs.disc(24, 24, 12)
+    dt = 2e-7
+    out, fb, feat, _ = oracle.surrogate_apply(st, dt, th, _unit_network(), _wide_range(st, th, dt))
+    assert not fb.any()
+    T, nh, ce = _cells(st, th)
+    lam, _ = oracle.cooling(T.ravel(), th["z"])
+    rate = (nh * th["gamma_heat"] - nh * nh * lam.reshape(T.shape)) / (th["rate_unit"] * ce)
+    D = rate * dt / (T * math.log(10.0))
+    assert np.max(np.abs(D)) < 0.05 and np.max(np.abs(D)) > 1e-4
+    assert np.max(np.abs(feat[..., 5] - D / (1 + np.abs(D)))) <= 1e-12 * np.max(np.abs(D))
+    dT = (out.U[4] - st.U[4]) / ce
+    assert np.all(np.abs(dT - rate * dt) <= 5 * D * D * T + 1e-12 * T)
+    assert np.all(feat[..., 4] == 1.0)
+
+
+def test_surrogate_step_features_and_fallback_bounds():
+    """The standardised features are (log10 n_H - lo) s - 1, (log10 T - lo) s - 1, ...; a cell
+    whose feature leaves [-1, 1], whose |q| exceeds qmax, or whose change |q S| exceeds dmax,
+    takes the plain integrator and ends bit for bit where the plain thermal update puts it;
+    every other cell takes the network's change."""
+    th = inputs.DISC_THERMAL
+    st = inputs.disc(24, 24, 12)
+    dt = 2e-7
+    T, nh, _ = _cells(st, th)
+    rng = _wide_range(st, th, dt)
+    plain, _ = oracle.thermal_apply(st, dt, th)
+    # feature definition
+    _, fb, feat, _ = oracle.surrogate_apply(st, dt, th, _unit_network(), rng)
+    assert np.allclose(feat[..., 0], (np.log10(nh) - rng[0]) * rng[4] - 1.0, rtol=0, atol=1e-13)
+    # (T carries the rounding of the pressure recovery's cancellation, ~1e-13 on the floor gas)
+    assert np.allclose(feat[..., 1], (np.log10(np.clip(T, 10, 1e8)) - rng[1]) * rng[5] - 1.0, rtol=0, atol=1e-11)
+    assert np.allclose(feat[..., 2], (math.log10(dt) - rng[2]) * rng[6] - 1.0, rtol=0, atol=1e-13)
+    # density range cut at its median: the denser half leaves [-1, 1] and falls back
+    ln = np.log10(nh)
+    med = float(np.median(ln))
+    cut = rng.copy()
+    cut[4] = 2.0 / (med - cut[0])
+    out, fb, _, _ = oracle.surrogate_apply(st, dt, th, _unit_network(), cut)
+    want_fb = (ln - cut[0]) * cut[4] - 1.0 > 1.0
+    assert 0 < want_fb.sum() < want_fb.size and np.array_equal(fb, want_fb)
+    assert np.array_equal(out.U[4][fb], plain.U[4][fb])
+    assert not np.array_equal(out.U[4][~fb], plain.U[4][~fb])
+    # |q| = 1 above qmax, and every change above dmax: all cells fall back
+    for q_d in ((0.999, 10.0), (10.0, 1e-9)):
+        lim = rng.copy()
+        lim[8], lim[9] = q_d
+        out, fb, _, _ = oracle.surrogate_apply(st, dt, th, _unit_network(), lim)
+        assert fb.all() and np.array_equal(out.U, plain.U)
+
+
+def test_surrogate_network_rounds_h1_and_w2_to_bf16():
+    """The network of the surrogate step is the FP64 forward pass (pinned above) with the
+    operands of the 64 x 64 layer, h1 and W2, rounded to BF16: against oracle.mlp_forward on
+    BF16-rounded W2 it differs by the rounding of h1 alone, at most
+    sum_j |w3_j| sum_k |W2b_jk| 2^-8 |h1_k| (tanh is 1-Lipschitz), and not by nothing."""
+    th = inputs.DISC_THERMAL
+    st = inputs.disc(16, 16, 8)
+    dt = 2e-7
+    P = _params(12, scale=0.8)
+    flat = np.concatenate([P[k].ravel() for k in ("W1", "b1", "W2", "b2", "w3", "b3")])
+    _, _, feat, _ = oracle.surrogate_apply(st, dt, th, flat, _wide_range(st, th, dt))
+    X = feat[..., :4].reshape(-1, 4)
+    Pb = dict(P, W2=oracle.bf16_round(P["W2"].ravel()).reshape(P["W2"].shape))
+    y = oracle.mlp_forward(X, Pb)
+    h1 = np.tanh(X @ P["W1"].T + P["b1"])
+    bound = (np.abs(h1) * 2.0 ** -8) @ np.abs(Pb["W2"]).T @ np.abs(P["w3"])
+    diff = np.abs(feat[..., 4].ravel() - y)
+    assert np.all(diff <= bound + 1e-14) and diff.max() > 0
