@@ -51,22 +51,23 @@ FP32_LANES_PER_SM = 128
 KCLASS = {
     # recovery: three face sums, |m|^2 and |B|^2 (3 + 3), Newton step of 1/rho (2), p (4)
     "recovery": dict(fp64=15, fp32=30, bytes=64 + 8 * 4, unit="padded cell"),
-    "flux1_x": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "flux1_y": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "flux1_z": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "flux2_x": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "flux2_y": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "flux2_z": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 8 * 4, unit="face"),
-    "emf": dict(fp64=0, fp32=60, bytes=(12 + 3 + 3) * 4, unit="edge point"),
+    "flux1_x": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    "flux1_y": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    "flux1_z": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    "flux2_x": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    "flux2_y": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    "flux2_z": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    "emf": dict(fp64=0, fp32=60, bytes=(8 + 3 + 3) * 4, unit="edge point"),
     # update fused with the recovery of the new state: FP64 = 14 adds (cell, six faces, three
     # face sums) + |m|^2 and |B|^2 (3 + 3) + Newton step of 1/rho (2) + p (4); bytes = F (60) +
     # E (12) + base U (64) + new U (64) + new W and cell EMF (44)
     "update": dict(fp64=26, fp32=140, bytes=15 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="point"),
     "ghost": dict(fp64=0, fp32=0, bytes=11 * 4 * 2, unit="ghost point"),
     # corner EMFs fused with the update (three active axes): FP64 = 5 cell adds + 3 face
-    # updates + 3 face sums + 12 recovery; bytes = F of three directions (96) + cell EMFs of
-    # the input state (12) + base U (64) + new U (64) + new W and cell EMF (44)
-    "emf_update": dict(fp64=23, fp32=200, bytes=24 * 4 + 3 * 4 + 64 + 64 + 11 * 4, unit="cell"),
+    # updates + 3 face sums + 12 recovery; bytes = F of three directions (84) + cell EMFs of
+    # the input state (12) + base U (64) + new U (64; the predictor of a periodic box without
+    # potential stores its 24 B of faces only) + new W and cell EMF (44)
+    "emf_update": dict(fp64=23, fp32=200, bytes=21 * 4 + 3 * 4 + 64 + (64 + 24) / 2 + 11 * 4, unit="cell"),
 }
 # FP64 pipe operations per clock per SM: the nominal 1.25 TFLOP/s of the part is
 # 152 SMs x 2 FMAs x 2 flops x ~2.06 GHz.  (A DFMA probe measured 1.0 TFLOP/s.)

@@ -11,9 +11,10 @@
 //                   share the index i + PX (j + PY k).  No ghost cells: boundary
 //                   conditions are index maps applied on every load.
 //   scratch W, F, E : R, padded by 2 cells on active axes (QX = nx + 4 ...), holding
-//                   primitives W (8), face fluxes F_d (8 per direction: rho, mx, my, mz,
-//                   E, B_t1, B_t2 with (d, t1, t2) cyclic, and the face's mass-flux scale
-//                   sigma used by the corner-EMF upwinding) and edge EMFs (3).
+//                   primitives W (8), face fluxes F_d (7 per direction: rho, mx, my, mz,
+//                   E, B_t1, B_t2 with (d, t1, t2) cyclic; the lowest bit of the stored
+//                   mass flux marks a face without contact motion for the corner-EMF
+//                   upwinding) and edge EMFs (3).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,7 +26,7 @@ enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BXF = 5, BYF = 6, BZF = 7 };
 enum { WR = 0, WVX = 1, WVY = 2, WVZ = 3, WP = 4, WBX = 5, WBY = 6, WBZ = 7 };
 // stored with W: the cell EMF -(v x B), components x, y, z (read by the corner EMFs)
 enum { WEX = 8, WEY = 9, WEZ = 10, NWQ = 11 };
-enum { NFLUX = 8 };  // rho, mx, my, mz, E, B_t1, B_t2, mass-flux scale
+enum { NFLUX = 7 };  // rho (with the no-motion bit), mx, my, mz, E, B_t1, B_t2
 enum : int { ERR_NONFINITE = 1, ERR_NEGATIVE = 2, ERR_TIMEOUT = 4 };
 enum { POT_NONE = 0, POT_GAUSS_X = 1, POT_LOG_DISC = 2 };
 // Riemann solvers of Section 2.1: HLLD (MHD), HLLC and HLL (pure gas dynamics)
@@ -178,9 +179,18 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  // the no-motion mark of a stored mass flux: its lowest significand bit (a change of at
+  // most one ulp of the flux); its sign bit gives the direction of the motion
+  static __device__ __forceinline__ double mark(double x, bool band) {
+    return __longlong_as_double((__double_as_longlong(x) & ~1LL) | (long long)band);
+  }
+  static __device__ __forceinline__ bool marked(double x) { return __double_as_longlong(x) & 1LL; }
+  static __device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
   // explicitly rounded operations (never contracted into an FMA)
   static __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
   static constexpr double degen = 1e-8;
 };
 template <> struct Ar<float> {
@@ -207,8 +217,15 @@ template <> struct Ar<float> {
   }
   static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static __device__ __forceinline__ float mark(float x, bool band) {
+    return __uint_as_float((__float_as_uint(x) & ~1u) | (unsigned)band);
+  }
+  static __device__ __forceinline__ bool marked(float x) { return __float_as_uint(x) & 1u; }
+  static __device__ __forceinline__ bool negative(float x) { return (int)__float_as_uint(x) < 0; }
   static __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
   static constexpr float degen = 1e-8f;
 };
 
@@ -254,6 +271,18 @@ template <> __device__ __forceinline__ double inv_density<float>(double rho) {
   double r = f2d_alu(__frcp_rn(d2f_alu(rho)));
   double e = fma(-rho, r, 1.0);
   return fma(r, e, r);
+}
+
+// The same with every operation explicitly rounded, for the CFL limit of the recovery: the
+// update kernel's fused recovery and the standalone recovery must give the same limit bit for
+// bit (the CFL step of a continued run equals that of a restart), whatever FMA contraction
+// the compiler chooses in each kernel.
+template <class R> __device__ __forceinline__ R fast_speed_rn(R rho, R p, R bb, R bn2, R gam) {
+  const R gp = Ar<R>::mul_rn(gam, p);
+  const R s = Ar<R>::add_rn(gp, bb);
+  R disc = Ar<R>::fma_rn(s, s, Ar<R>::mul_rn(Ar<R>::mul_rn(R(-4), gp), bn2));
+  disc = disc > R(0) ? disc : R(0);
+  return Ar<R>::sqrt_(Ar<R>::mul_rn(Ar<R>::add_rn(s, Ar<R>::sqrt_(disc)), Ar<R>::rcp(Ar<R>::mul_rn(R(2), rho))));
 }
 
 template <class R> __device__ __forceinline__ R fast_speed(R rho, R p, R bb, R bn2, R gam) {
@@ -571,7 +600,11 @@ template <class R> __device__ __forceinline__ R centre(const PatchDev& P, int a,
 
 // ---------------------------------------------------------- phase: recovery --
 // cell EMF -(v x B)_C (Eq. 9) from the velocity and field components A = C+1, B = C+2
-template <class R> __device__ __forceinline__ R cell_emf(R vA, R vB, R bA, R bB) { return -(vA * bB - vB * bA); }
+// (explicitly rounded: the recovery fused into the update and the standalone recovery must
+// store the same bits, whatever FMA contraction the compiler applies in each kernel)
+template <class R> __device__ __forceinline__ R cell_emf(R vA, R vB, R bA, R bB) {
+  return -Ar<R>::sub_rn(Ar<R>::mul_rn(vA, bB), Ar<R>::mul_rn(vB, bA));
+}
 
 // exponent test of a double on the integer pipe (not inf, not NaN)
 __device__ __forceinline__ bool finite_d(double x) {
@@ -587,17 +620,21 @@ __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx,
                                             double e, double sbx, double sby, double sbz, R* __restrict__ W,
                                             long long q, bool store, bool interior) {
   if (P.floors && rho < P.rho_floor) rho = P.rho_floor;
+  // Every operation below is explicitly rounded (intrinsics are never contracted or
+  // reordered): the recovery fused into the update kernel and the standalone recovery store
+  // the same W and CFL limit bit for bit, whichever kernel inlines them.
   const double irho = inv_density<R>(rho);
-  const double m2 = mx * mx + my * my + mz * mz;
-  const double b2 = sbx * sbx + sby * sby + sbz * sbz;  // 4 |B_cc|^2
+  const double m2 = __fma_rn(mz, mz, __fma_rn(my, my, __dmul_rn(mx, mx)));
+  const double b2 = __fma_rn(sbz, sbz, __fma_rn(sby, sby, __dmul_rn(sbx, sbx)));  // 4 |B_cc|^2
   // p = (gamma-1) (E - |m|^2/(2 rho) - |B_cc|^2/2), in FP64, clamped when floors are on
-  double p = P.gm1 * e - P.hgm1 * (m2 * irho) - P.egm1 * b2;
+  double p = __fma_rn(-P.egm1, b2, __fma_rn(-P.hgm1, __dmul_rn(m2, irho), __dmul_rn(P.gm1, e)));
   if (P.floors) {
     const double lo = rho * P.pr_floor, hi = rho * P.pr_ceil;
     p = p < lo ? lo : (p > hi ? hi : p);  // a NaN passes through to the finiteness check
   }
   const R rirho = Ar<R>::from_d(irho);
-  const R vx = Ar<R>::from_d(mx) * rirho, vy = Ar<R>::from_d(my) * rirho, vz = Ar<R>::from_d(mz) * rirho;
+  const R vx = Ar<R>::mul_rn(Ar<R>::from_d(mx), rirho), vy = Ar<R>::mul_rn(Ar<R>::from_d(my), rirho),
+          vz = Ar<R>::mul_rn(Ar<R>::from_d(mz), rirho);
   const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
   const R rr = Ar<R>::from_d(rho), pr = Ar<R>::from_d(p);
   if (store) {
@@ -624,14 +661,14 @@ __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx,
     }
     const R v[3] = {vx, vy, vz};
     const R b[3] = {bx, by, bz};
-    const R bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const R bb = Ar<R>::fma_rn(b[2], b[2], Ar<R>::fma_rn(b[1], b[1], Ar<R>::mul_rn(b[0], b[0])));
     const R gam = Gam<R>::get(P);
     R lr = R(INFINITY);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (!P.act[a]) continue;
-      const R cf = fast_speed<R>(rr, pr, bb, b[a] * b[a], gam);
-      const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::abs_(v[a]) + cf);
+      const R cf = fast_speed_rn<R>(rr, pr, bb, Ar<R>::mul_rn(b[a], b[a]), gam);
+      const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::add_rn(Ar<R>::abs_(v[a]), cf));
       lr = t < lr ? t : lr;
     }
     lim = lr;
@@ -762,6 +799,22 @@ __device__ __forceinline__ int floor_point(const PatchDev& P, double* __restrict
   return changed;
 }
 
+// ---------------------------------------------------- Eq. 11's no-motion band --
+// Eq. 11 averages the one-sided EMF derivatives of the corner formula where the contact does
+// not move (F_rho = 0).  That is read as zero to the precision of the data the flux was
+// computed from: |F_rho| <= eps_R sigma, sigma = max(rho_L, rho_R) max(|S_L|, |S_R|).  FP64
+// path: eps = 2^-32, two orders above the rounding of FP64 data after the pressure
+// recovery's cancellation (relative error ~2^-52 E / thermal energy, up to 1e3-1e4).  FP32
+// bulk of the mixed path: eps = 64 * 2^-23, the same reading for data rounded to FP32.  A
+// flux that is zero in exact arithmetic comes out as rounding of sigma, of either sign.  The
+// flux kernels store the decision in the lowest bit of the mass flux (Ar::mark).
+template <class R> struct UpwindEps;
+template <> struct UpwindEps<double> { static constexpr double v = 1.0 / 4294967296.0; };
+template <> struct UpwindEps<float> { static constexpr float v = 64.0f * 1.1920928955078125e-7f; };
+template <class R> __device__ __forceinline__ bool no_motion_band(R fr, R sigma) {
+  return !(Ar<R>::abs_(fr) > UpwindEps<R>::v * sigma);
+}
+
 // ------------------------------------------------------------- phase: flux ----
 // HLLD flux through a D-face with donor-cell (ORDER 1) or kappa-scheme (ORDER 2)
 // interface states; the normal field is the face value; a face whose reconstructed rho
@@ -828,44 +881,34 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
   Gam<R>::kappa(P, kap[0], kap[1], kap[2]);
   flux_core<R, D, ORDER>([&](int m, int o) { return W[m * QS + q + o * st]; }, face_bn<R, D>(P, Ub, i, j, k),
                          Gam<R>::get(P), solver, kap, f);
-  F[q] = f[0];
+  F[q] = Ar<R>::mark(f[0], no_motion_band<R>(f[0], f[7]));
   F[(1 + D) * QS + q] = f[1];
   F[(1 + T1) * QS + q] = f[2];
   F[(1 + T2) * QS + q] = f[3];
   F[4 * QS + q] = f[4];
   F[5 * QS + q] = f[5];
   F[6 * QS + q] = f[6];
-  F[7 * QS + q] = f[7];
 }
 
 // -------------------------------------------------------------- phase: EMF ----
 // Corner EMF E_C at edge (A-1/2, B-1/2), (A, B, C) cyclic (Eq. 9-11): mean of the four
 // face EMFs plus upwinded one-sided corrections, the upwind side given by the sign of
-// the Riemann mass flux F_rho.  Eq. 11's "otherwise" (F_rho = 0) is read as zero to the
-// precision of the data the flux was computed from: |F_rho| <= eps_R sigma.  FP64 path:
-// eps = 2^-32, two orders above the rounding of FP64 data after the pressure recovery's
-// cancellation (relative error ~2^-52 E / thermal energy, up to 1e3-1e4).  FP32 bulk of
-// the mixed path: eps = 64 * 2^-23, the same reading for data rounded to FP32.  A flux that
-// is zero in exact arithmetic comes out as rounding of sigma, of either sign; (db/8) * 2/db
-// = 1/4.
-template <class R> struct UpwindEps;
-template <> struct UpwindEps<double> { static constexpr double v = 1.0 / 4294967296.0; };
-template <> struct UpwindEps<float> { static constexpr float v = 64.0f * 1.1920928955078125e-7f; };
-template <class R> __device__ __forceinline__ R upwind(R fr, R sigma, R left, R right) {
-  const R t = UpwindEps<R>::v * sigma;
-  return fr > t ? left : (fr < -t ? right : R(0.5) * (left + right));
+// the Riemann mass flux F_rho through the face, and their mean at a face that the flux
+// kernel marked as without contact motion (no_motion_band); (db/8) * 2/db = 1/4.
+template <class R> __device__ __forceinline__ R upwind(R fr, R left, R right) {
+  return Ar<R>::marked(fr) ? R(0.5) * (left + right) : (Ar<R>::negative(fr) ? right : left);
 }
 
 // Face EMFs around the edge: Ea_b, Ea_bm = -F_A(B_B) on the A-faces at b and b-1;
 // Eb_a, Eb_am = F_B(B_A) on the B-faces at a and a-1.  Cell EMFs ec0..ec3 at (a, b),
-// (a-1, b), (a, b-1), (a-1, b-1).  Mass fluxes and sigmas of the same four faces.
+// (a-1, b), (a, b-1), (a-1, b-1).  Marked mass fluxes of the same four faces.
 template <class R>
 __device__ __forceinline__ R corner_core(R Ea_b, R Ea_bm, R Eb_a, R Eb_am, R ec0, R ec1, R ec2, R ec3, R frA_b,
-                                         R sA_b, R frA_bm, R sA_bm, R frB_a, R sB_a, R frB_am, R sB_am) {
-  const R d_bq = upwind<R>(frA_b, sA_b, ec1 - Eb_am, ec0 - Eb_a);
-  const R d_b3q = upwind<R>(frA_bm, sA_bm, Eb_am - ec3, Eb_a - ec2);
-  const R d_aq = upwind<R>(frB_a, sB_a, ec2 - Ea_bm, ec0 - Ea_b);
-  const R d_a3q = upwind<R>(frB_am, sB_am, Ea_bm - ec3, Ea_b - ec1);
+                                         R frA_bm, R frB_a, R frB_am) {
+  const R d_bq = upwind<R>(frA_b, ec1 - Eb_am, ec0 - Eb_a);
+  const R d_b3q = upwind<R>(frA_bm, Eb_am - ec3, Eb_a - ec2);
+  const R d_aq = upwind<R>(frB_a, ec2 - Ea_bm, ec0 - Ea_b);
+  const R d_a3q = upwind<R>(frB_am, Ea_bm - ec3, Ea_b - ec1);
   return R(0.25) * (Ea_b + Ea_bm + Eb_a + Eb_am) + R(0.25) * (d_b3q - d_bq) + R(0.25) * (d_a3q - d_aq);
 }
 
@@ -883,8 +926,7 @@ __device__ __forceinline__ R corner_value(const PatchDev& P, const R* __restrict
   const long long oa = q - sa, ob = q - sb, oab = q - sa - sb;
   const R* ec = W + (WEX + C) * QS;  // cell EMFs stored by the recovery
   return corner_core<R>(-FA[5 * QS + q], -FA[5 * QS + ob], FB[6 * QS + q], FB[6 * QS + oa], ec[q], ec[oa], ec[ob],
-                        ec[oab], FA[q], FA[7 * QS + q], FA[ob], FA[7 * QS + ob], FB[q], FB[7 * QS + q], FB[oa],
-                        FB[7 * QS + oa]);
+                        ec[oab], FA[q], FA[ob], FB[q], FB[oa]);
 }
 
 template <class R, int C>

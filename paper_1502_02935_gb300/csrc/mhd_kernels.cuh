@@ -177,7 +177,7 @@ template <class R>
 __global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* __restrict__ Win,
                                                        R* __restrict__ Wout, const double* __restrict__ Ub,
                                                        const double* __restrict__ Us, double* __restrict__ Uo,
-                                                       StageArgs a, int lz, int images) {
+                                                       StageArgs a, int lz, int images, int cells_out) {
   constexpr int SX = kTX + 1;  // row pitch of the arrays with an x halo
   __shared__ R sEz[(kTY + 1) * SX];
   __shared__ R sEx[2][(kTY + 1) * kTX];
@@ -291,10 +291,12 @@ __global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* _
       const double bhi[3] = {sBx[tj * SX + ti + 1], sBy[(tj + 1) * kTX + ti], sBz[nxt][tj * kTX + ti]};
       if (last && P.floors)
         nfl += floor_core(P, u[0], u[1], u[2], u[3], u[4], blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2]);
-      Uo[s] = u[0];
+      if (cells_out) {
+        Uo[s] = u[0];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Uo[(MX + c) * FS + s] = u[1 + c];
-      Uo[EN * FS + s] = u[4];
+        for (int c = 0; c < 3; ++c) Uo[(MX + c) * FS + s] = u[1 + c];
+        Uo[EN * FS + s] = u[4];
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) Uo[(BXF + c) * FS + s] = blo[c];
       const R l = prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2],
@@ -506,7 +508,10 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     int lz = 8;
     while (lz > 2 && (long long)ntx * nty * ((P.n[2] + lz - 1) / lz) < 2LL * 5 * sm_count()) lz >>= 1;
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((P.n[2] + lz - 1) / lz), 1);
-    k_emf_update<R><<<grid, kBlock, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz, images);
+    // the predictor's cell fields of U^n+1/2 are read by nobody when the corrector's source
+    // term, the ghost fill and the passive scalars do not need them: only its faces are stored
+    const int cells_out = !(a.stage == 0 && images && a.src.potential == POT_NONE && P.ns == 0);
+    k_emf_update<R><<<grid, kBlock, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz, images, cells_out);
     ++nl;
   } else {
     const Range er = edge_range(P);
