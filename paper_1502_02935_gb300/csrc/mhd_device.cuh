@@ -870,6 +870,20 @@ __device__ __forceinline__ R face_bn(const PatchDev& P, const double* __restrict
   return Ar<R>::from_d(Ub[(BXF + D) * P.FS + sidx(P, s3[0], s3[1], s3[2])]);
 }
 
+// F_D at scratch index q from the solver's output f[0..7]: the mass flux (marked with Eq.
+// 11's no-motion decision), the momentum components in x, y, z order, E and B_T1, B_T2
+template <class R, int D>
+__device__ __forceinline__ void store_flux(R* __restrict__ F, long long QS, long long q, const R* f) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  F[q] = Ar<R>::mark(f[0], no_motion_band<R>(f[0], f[7]));
+  F[(1 + D) * QS + q] = f[1];
+  F[(1 + T1) * QS + q] = f[2];
+  F[(1 + T2) * QS + q] = f[3];
+  F[4 * QS + q] = f[4];
+  F[5 * QS + q] = f[5];
+  F[6 * QS + q] = f[6];
+}
+
 // the flux through the D-face at (i, j, k) (face index i-1/2 along D) from the stored W
 template <class R, int D, int ORDER>
 __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restrict__ W,
@@ -881,13 +895,7 @@ __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restric
   Gam<R>::kappa(P, kap[0], kap[1], kap[2]);
   flux_core<R, D, ORDER>([&](int m, int o) { return W[m * QS + q + o * st]; }, face_bn<R, D>(P, Ub, i, j, k),
                          Gam<R>::get(P), solver, kap, f);
-  F[q] = Ar<R>::mark(f[0], no_motion_band<R>(f[0], f[7]));
-  F[(1 + D) * QS + q] = f[1];
-  F[(1 + T1) * QS + q] = f[2];
-  F[(1 + T2) * QS + q] = f[3];
-  F[4 * QS + q] = f[4];
-  F[5 * QS + q] = f[5];
-  F[6 * QS + q] = f[6];
+  store_flux<R, D>(F, QS, q, f);
 }
 
 // -------------------------------------------------------------- phase: EMF ----

@@ -67,6 +67,99 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 1) k_flux(PatchDe
 }
 
 
+// Fluxes through the D-faces (D = y or z) marching along D: each thread takes one position
+// (x, the other transverse axis) of the flux range and a segment of kMarch consecutive faces,
+// and loads one new cell of W per face (coalesced along x).  The kappa-scheme reconstructs
+// each cell once: from its two one-sided differences dl, dr, the two limited slopes
+// m1 = minmod(dl, b dr), m2 = minmod(dr, b dl) give its value at the upper face,
+// w + K1 m1 + K2 m2 (w_L there), and at the lower face, w - K1 m2 - K2 m1 (w_R there) -- the
+// expressions of kappa_face, where the per-face kernel evaluates both neighbours of every face.
+// The donor-cell stage carries the previous cell.  Results equal those of flux_point.
+// Segments of 16 faces; FP32 kernels at four (donor cell) and three (kappa-scheme) resident
+// CTAs per SM: the fastest of 8, 16, 32, 64 faces and three or four CTAs (measured at 256^3:
+// the kappa kernels spill at four).
+constexpr int kMarch = 16;
+
+template <class R, int D, int ORDER, int S>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ORDER == 1 ? 4 : 3) : 1) k_flux_march(PatchDev P,
+                                                                             const double* __restrict__ Ub,
+                                                                             Range rg) {
+  static_assert(D == 1 || D == 2, "marching along y or z");
+  constexpr int T = D == 1 ? 2 : 1;  // the transverse axis other than x
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  const unsigned e0 = (unsigned)rg.ext[0];
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= e0 * (unsigned)rg.ext[T]) return;
+  const unsigned qt = r / e0;
+  int c3[3];
+  c3[0] = rg.lo[0] + (int)(r - qt * e0);
+  c3[T] = rg.lo[T] + (int)qt;
+  const int f0 = rg.lo[D] + (int)blockIdx.y * kMarch;
+  const int f1 = min(f0 + kMarch, rg.lo[D] + rg.ext[D]);
+  const R* __restrict__ W = (const R*)P.W;
+  R* __restrict__ F = (R*)P.F[D];
+  const long long QS = P.QS, st = qstride(P, D);
+  c3[D] = f0;
+  long long q = qidx(P, c3[0], c3[1], c3[2]);  // cell of face f0 (its lower face)
+  const R gam = Gam<R>::get(P);
+  const int comp[7] = {WR, WVX + D, WVX + T1, WVX + T2, WP, WBX + T1, WBX + T2};
+  R out[8];
+  if (ORDER == 1) {
+    R wm[7], w0[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) wm[m] = W[comp[m] * QS + q - st];
+#pragma unroll 1
+    for (int f = f0; f < f1; ++f, q += st) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) w0[m] = W[comp[m] * QS + q];
+      c3[D] = f;
+      riemann<R>(S, wm, w0, face_bn<R, D>(P, Ub, c3[0], c3[1], c3[2]), gam, out);
+      store_flux<R, D>(F, QS, q, out);
+#pragma unroll
+      for (int m = 0; m < 7; ++m) wm[m] = w0[m];
+    }
+  } else {
+    R K1, K2, kb;
+    Gam<R>::kappa(P, K1, K2, kb);
+    R b[7], c[7], up[7];  // W of cells f-1 and f; value of cell f-1 at face f (w_L there)
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      const R a = W[comp[m] * QS + q - 2 * st];
+      b[m] = W[comp[m] * QS + q - st];
+      c[m] = W[comp[m] * QS + q];
+      const R dl = b[m] - a, dr = c[m] - b[m];
+      up[m] = b[m] + K1 * minmod<R>(dl, kb * dr) + K2 * minmod<R>(dr, kb * dl);
+    }
+#pragma unroll 1
+    for (int f = f0; f < f1; ++f, q += st) {
+      R wl[7], wr[7];
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        const R d = W[comp[m] * QS + q + st];
+        const R dl = c[m] - b[m], dr = d - c[m];
+        const R m1 = minmod<R>(dl, kb * dr), m2 = minmod<R>(dr, kb * dl);
+        wl[m] = up[m];
+        wr[m] = c[m] - K1 * m2 - K2 * m1;
+        up[m] = c[m] + K1 * m1 + K2 * m2;
+        b[m] = c[m];
+        c[m] = d;
+      }
+      // a face whose reconstructed rho or p is not positive takes the donor-cell states:
+      // cells f - 1 (loaded again) and f (now in b)
+      if (!(wl[0] > R(0)) || !(wr[0] > R(0)) || !(wl[4] > R(0)) || !(wr[4] > R(0))) {
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+          wl[m] = W[comp[m] * QS + q - st];
+          wr[m] = b[m];
+        }
+      }
+      c3[D] = f;
+      riemann<R>(S, wl, wr, face_bn<R, D>(P, Ub, c3[0], c3[1], c3[2]), gam, out);
+      store_flux<R, D>(F, QS, q, out);
+    }
+  }
+}
+
 // corner EMFs: memory-latency bound; eight resident blocks per SM (measured)
 template <class R>
 __global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
@@ -112,9 +205,10 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
 }
 
 // Corner EMFs and the stage update in one kernel, for patches with three active axes.
-// Five resident CTAs per SM (48 registers): four, five and six time the same on 256^3,
-// five is best on 128^3 (measured).  A
-// CTA owns a kTX x kTY column of cells over lz consecutive z-planes and marches up in z.
+// Five resident CTAs per SM (48 registers, 72 B spilled): five is the fastest of four, five
+// and six on 128^3 and 256^3, and 32 x 8 tiles are faster than 32 x 16 at two or three CTAs
+// per SM (measured at 256^3: 1.26 ms against 1.37 at four CTAs, 1.39 and 1.69 with 32 x 16).
+// A CTA owns a kTX x kTY column of cells over lz consecutive z-planes and marches up in z.
 // For plane k:
 //  (A) the edge EMFs the plane's faces need -- E_z at plane k, E_x and E_y at plane k + 1
 //      (at the first plane also at k) -- over the tile and its upper halo row and column,
@@ -132,7 +226,8 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
 // read from Win, the W of the stage's input, while CTAs of neighbouring tiles write the W
 // of the new state: that goes to the other buffer, Wout.
 constexpr int kTX = 32, kTY = 8;
-static_assert(kTX * kTY == kBlock, "one thread per cell of a tile plane");
+constexpr int kEB = kTX * kTY;  // one thread per cell of a tile plane
+constexpr int kEMinBlocks = 5;
 
 // Periodic images of the W of interior cell (i, j, k) (scratch index q) in the ghost shell
 // of width 2: every combination of shifts by 0 or +-n per axis that lands in [-2, n + 1],
@@ -174,7 +269,7 @@ __device__ __forceinline__ R emf_at(const PatchDev& P, const R* __restrict__ W, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* __restrict__ Win,
+__global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, const R* __restrict__ Win,
                                                        R* __restrict__ Wout, const double* __restrict__ Ub,
                                                        const double* __restrict__ Us, double* __restrict__ Uo,
                                                        StageArgs a, int lz, int images, int cells_out) {
@@ -217,6 +312,14 @@ __global__ void __launch_bounds__(kBlock, 5) k_emf_update(PatchDev P, const R* _
     else if (c == 0) sEx[buf][jj * kTX + ii] = e;
     else sEy[buf][jj * SX + ii] = e;
   };
+  const long long SZ = (long long)P.QX * P.QY, QS = P.QS;
+  const R* __restrict__ Fx = (const R*)P.F[0];
+  const R* __restrict__ Fy = (const R*)P.F[1];
+  const R* __restrict__ Fz = (const R*)P.F[2];
+  const R* __restrict__ ecx = Win + WEX * QS;
+  const R* __restrict__ ecy = Win + WEY * QS;
+  const R* __restrict__ ecz = Win + WEZ * QS;
+  R cFx0 = R(0), cFx6 = R(0), cFy0 = R(0), cFy5 = R(0), cex0 = R(0), cex1 = R(0), cey0 = R(0), cey1 = R(0);
   for (int k = kz0; k < kz1; ++k) {
     const int cur = (k - kz0) & 1, nxt = cur ^ 1;
     const bool first = k == kz0;
@@ -434,6 +537,17 @@ static inline Range edge_range(const PatchDev& P) {
 // one direction's flux kernel for the patch's Riemann solver
 template <class R, int D, int ORDER>
 static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cudaStream_t s) {
+  if constexpr (D > 0) {
+    // y and z faces: the marching kernel, one thread per (x, other transverse) position and
+    // segment of kMarch faces
+    constexpr int T = D == 1 ? 2 : 1;
+    const long long plane = (long long)fr.ext[0] * fr.ext[T];
+    const dim3 g((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)((fr.ext[D] + kMarch - 1) / kMarch), 1);
+    if (P.riemann == RIEMANN_HLLC) k_flux_march<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr);
+    else if (P.riemann == RIEMANN_HLL) k_flux_march<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr);
+    else k_flux_march<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr);
+    return;
+  }
   const dim3 g = grid_of(fr);
   if (P.riemann == RIEMANN_HLLC) k_flux<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr);
   else if (P.riemann == RIEMANN_HLL) k_flux<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr);
@@ -503,15 +617,15 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
   if (fused) {
     ProfScope ps(prof, KC_EMF_UPDATE, s);
     // planes per CTA: 8, halved (down to 2) while the grid would be under two waves of
-    // five resident CTAs per SM
+    // resident CTAs
     const int ntx = (P.n[0] + kTX - 1) / kTX, nty = (P.n[1] + kTY - 1) / kTY;
     int lz = 8;
-    while (lz > 2 && (long long)ntx * nty * ((P.n[2] + lz - 1) / lz) < 2LL * 5 * sm_count()) lz >>= 1;
+    while (lz > 2 && (long long)ntx * nty * ((P.n[2] + lz - 1) / lz) < 2LL * kEMinBlocks * sm_count()) lz >>= 1;
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((P.n[2] + lz - 1) / lz), 1);
     // the predictor's cell fields of U^n+1/2 are read by nobody when the corrector's source
     // term, the ghost fill and the passive scalars do not need them: only its faces are stored
     const int cells_out = !(a.stage == 0 && images && a.src.potential == POT_NONE && P.ns == 0);
-    k_emf_update<R><<<grid, kBlock, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz, images, cells_out);
+    k_emf_update<R><<<grid, kEB, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz, images, cells_out);
     ++nl;
   } else {
     const Range er = edge_range(P);
