@@ -302,13 +302,25 @@ int mhd_set_profiling(mhd_ctx* ctx, int on);
  * class c, for c < n (n >= 16).  Synchronises. */
 int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
 
-/* Autotuner of the persistent batched step (context made with MHD_FLAG_PERSISTENT): times
- * the step for each candidate tile shape (TX x TY points of one z-plane per CTA) and CTA
- * count per SM, keeps the fastest, and records it in a JSON cache file at cache_path,
- * keyed by GPU name, precision and patch sizes (NULL: no cache).  force = 0 uses a cached
- * entry without timing.  The state is restored after the timing runs.  tile_out (may be
- * NULL) receives TX, TY.  MHD_ERR_STATE without MHD_FLAG_PERSISTENT. */
+/* Autotuner of the batched step (context made with MHD_FLAG_PERSISTENT).  It times the
+ * persistent step for each candidate tile shape (TX x TY points of one z-plane per CTA) and
+ * CTA count per SM and keeps the fastest; then it times that persistent step against the
+ * per-phase scheme (each patch's kernels as one chain on one of up to eight streams) over
+ * three whole steps from the same state, and the context runs its steps with the faster
+ * scheme from then on (mhd_step_scheme tells which; passive scalars only run per phase).
+ * The result is recorded in a JSON cache file at cache_path, keyed by GPU name, precision
+ * and patch sizes (NULL: no cache); force = 0 uses a cached entry without timing.  The state
+ * is restored after the timing runs and captured graphs are dropped.  tile_out (may be NULL)
+ * receives TX, TY.  MHD_ERR_STATE without MHD_FLAG_PERSISTENT. */
 int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out);
+
+/* The scheme the context's steps run with: *persistent_out = 1 for one persistent launch per
+ * step (MHD_FLAG_PERSISTENT, until mhd_autotune picks the per-phase scheme), 0 for per-phase
+ * launches.  mhd_set_step_scheme chooses it: 1 needs MHD_FLAG_PERSISTENT and no passive
+ * scalars (MHD_ERR_STATE otherwise); switching drops the captured graphs and the next step
+ * starts with the recovery.  Both schemes advance the same state. */
+int mhd_step_scheme(mhd_ctx* ctx, int* persistent_out);
+int mhd_set_step_scheme(mhd_ctx* ctx, int persistent);
 
 /* Bounded waits of the persistent step.  limit_ms: the longest a CTA waits at a grid
  * barrier before it sets the device error word to MHD_ERR_TIMEOUT and the launch ends

@@ -570,6 +570,32 @@ static int issue_step(mhd_ctx* ctx, double dt) {
   return MHD_OK;
 }
 
+// The per-phase scheme of a batch: each patch's step is one chain on one of up to eight
+// streams (cells balanced, largest patches first), forked from and joined back into the
+// context's stream.  Nothing to do for one patch or when the streams exist.
+static int make_aux_streams(mhd_ctx* ctx) {
+  if (ctx->np < 2 || !ctx->aux.empty()) return 0;
+  const int ns = ctx->np < 8 ? ctx->np : 8;
+  ctx->aux.assign(ns, nullptr);
+  ctx->ev_join.assign(ns, nullptr);
+  for (int q = 0; q < ns; ++q)
+    if (cudaStreamCreateWithFlags(&ctx->aux[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join[q], cudaEventDisableTiming) != cudaSuccess)
+      return -1;
+  if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return -1;
+  std::vector<int> order(ctx->np);
+  for (int p = 0; p < ctx->np; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ctx->P[x].ncell > ctx->P[y].ncell; });
+  std::vector<long long> load(ns, 0);
+  ctx->aux_of.assign(ctx->np, 0);
+  for (int p : order) {
+    const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    ctx->aux_of[p] = q;
+    load[q] += ctx->P[p].ncell;
+  }
+  return 0;
+}
+
 extern "C" {
 
 int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0,
@@ -700,26 +726,8 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
   if (g->flags & MHD_FLAG_PERSISTENT) {
     ctx->persistent = true;
     if (build_tables(ctx, 32, 8, 1.0)) return bail(MHD_ERR_CUDA);
-  } else if (ctx->np > 1) {
-    const int ns = ctx->np < 8 ? ctx->np : 8;
-    ctx->aux.assign(ns, nullptr);
-    ctx->ev_join.assign(ns, nullptr);
-    for (int q = 0; q < ns; ++q)
-      if (cudaStreamCreateWithFlags(&ctx->aux[q], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ctx->ev_join[q], cudaEventDisableTiming) != cudaSuccess)
-        return bail(MHD_ERR_CUDA);
-    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MHD_ERR_CUDA);
-    // balance cells over the streams, largest patches first
-    std::vector<int> order(ctx->np);
-    for (int p = 0; p < ctx->np; ++p) order[p] = p;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ctx->P[x].ncell > ctx->P[y].ncell; });
-    std::vector<long long> load(ns, 0);
-    ctx->aux_of.assign(ctx->np, 0);
-    for (int p : order) {
-      const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      ctx->aux_of[p] = q;
-      load[q] += ctx->P[p].ncell;
-    }
+  } else if (make_aux_streams(ctx)) {
+    return bail(MHD_ERR_CUDA);
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(MHD_ERR_CUDA);
   *out = ctx;
@@ -1296,6 +1304,7 @@ namespace {
 struct TuneEntry {
   int TX, TY;
   double occ, ms;
+  int persistent;  // the faster scheme: 1 one persistent launch, 0 per-phase launches
 };
 
 std::map<std::string, TuneEntry> read_cache(const char* path) {
@@ -1310,9 +1319,13 @@ std::map<std::string, TuneEntry> read_cache(const char* path) {
     const size_t c = line.find("\"TX\":", b);
     if (b == std::string::npos || c == std::string::npos) continue;
     TuneEntry e{};
+    e.persistent = 1;
     if (sscanf(line.c_str() + c, "\"TX\": %d, \"TY\": %d, \"occ\": %lf, \"ms\": %lf", &e.TX, &e.TY, &e.occ,
-               &e.ms) == 4)
+               &e.ms) == 4) {
+      const size_t d = line.find("\"persistent\":", c);
+      if (d != std::string::npos) sscanf(line.c_str() + d, "\"persistent\": %d", &e.persistent);
       m[line.substr(a + 1, b - a - 1)] = e;
+    }
   }
   return m;
 }
@@ -1324,8 +1337,8 @@ void write_cache(const char* path, const std::map<std::string, TuneEntry>& m) {
   size_t i = 0;
   for (const auto& kv : m) {
     char buf[256];
-    snprintf(buf, sizeof buf, "{\"TX\": %d, \"TY\": %d, \"occ\": %.3f, \"ms\": %.6f}", kv.second.TX,
-             kv.second.TY, kv.second.occ, kv.second.ms);
+    snprintf(buf, sizeof buf, "{\"TX\": %d, \"TY\": %d, \"occ\": %.3f, \"ms\": %.6f, \"persistent\": %d}",
+             kv.second.TX, kv.second.TY, kv.second.occ, kv.second.ms, kv.second.persistent);
     f << "\"" << kv.first << "\": " << buf << (++i < m.size() ? ",\n" : "\n");
   }
   f << "}\n";
@@ -1334,7 +1347,7 @@ void write_cache(const char* path, const std::map<std::string, TuneEntry>& m) {
 
 int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out) {
   if (!ctx) return MHD_ERR_ARG;
-  if (!ctx->persistent) return fail(ctx, MHD_ERR_STATE, "autotune needs MHD_FLAG_PERSISTENT");
+  if (!(ctx->flags & MHD_FLAG_PERSISTENT)) return fail(ctx, MHD_ERR_STATE, "autotune needs MHD_FLAG_PERSISTENT");
   int dev = 0;
   CK(cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -1343,10 +1356,19 @@ int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out)
   key << prop.name << "|" << (ctx->precision == MHD_PREC_FP64 ? "fp64" : "mixed") << "|";
   for (auto& p : ctx->P) key << p.desc.nx << "x" << p.desc.ny << "x" << p.desc.nz << ",";
   std::string k = key.str();
+  // the scheme that runs the steps from now on; the graphs captured for the other go
+  auto use_scheme = [&](int persistent) -> int {
+    if (!persistent && make_aux_streams(ctx)) return fail(ctx, MHD_ERR_CUDA, "per-phase streams");
+    ctx->persistent = persistent != 0;
+    ctx->w_valid = false;
+    drop_graph(ctx);
+    return MHD_OK;
+  };
   auto cache = read_cache(cache_path);
   auto it = cache.find(k);
   if (!force && it != cache.end()) {
     int rc = build_tables(ctx, it->second.TX, it->second.TY, it->second.occ);
+    if (rc == MHD_OK) rc = use_scheme(it->second.persistent && ctx->P[0].dev.ns == 0 ? 1 : 0);
     if (tile_out) {
       tile_out[0] = ctx->TX;
       tile_out[1] = ctx->TY;
@@ -1368,15 +1390,18 @@ int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out)
     for (int p = 0; p < ctx->np; ++p)
       cudaMemcpyAsync(ctx->P[p].dev.Un, backup[p], sizeof(double) * 8 * (size_t)ctx->P[p].dev.FS,
                       cudaMemcpyDeviceToDevice, ctx->stream);
+    ctx->w_valid = false;
   };
   const int cand[][2] = {{32, 4}, {32, 8}, {64, 4}, {16, 16}, {32, 16}, {64, 8}, {128, 2}, {128, 4}};
   const double occs[] = {1.0, 0.5};
-  TuneEntry best{32, 8, 1.0, 1e300};
+  TuneEntry best{32, 8, 1.0, 1e300, 1};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const bool was_prof = ctx->profiling;
   ctx->profiling = false;
+  ctx->persistent = true;
+  drop_graph(ctx);
   for (auto& c : cand) {
     for (double oc : occs) {
       if (build_tables(ctx, c[0], c[1], oc)) continue;
@@ -1391,8 +1416,26 @@ int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out)
       int h = 0;
       CK(cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost));
       if (h) break;
-      if (ms / 3.0 < best.ms) best = TuneEntry{c[0], c[1], oc, ms / 3.0};
+      if (ms / 3.0 < best.ms) best = TuneEntry{c[0], c[1], oc, ms / 3.0, 1};
     }
+  }
+  int rc = build_tables(ctx, best.TX, best.TY, best.occ);
+  // then the two schemes against each other from the same state, three whole steps each
+  // (one untimed first): the persistent launch with the tiles found, and the per-phase
+  // launches on the patch streams.  Passive scalars only run per phase.
+  float ms_scheme[2] = {1e30f, 1e30f};
+  for (int persistent = 1; rc == MHD_OK && persistent >= 0; --persistent) {
+    if (persistent && ctx->P[0].dev.ns > 0) continue;
+    rc = use_scheme(persistent);
+    if (rc) break;
+    restore();
+    rc = issue_step(ctx, -1.0);
+    if (rc) break;
+    CK(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < 3 && rc == MHD_OK; ++r) rc = issue_step(ctx, -1.0);
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms_scheme[persistent], e0, e1));
   }
   ctx->profiling = was_prof;
   cudaEventDestroy(e0);
@@ -1400,16 +1443,39 @@ int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out)
   restore();
   CK(cudaStreamSynchronize(ctx->stream));
   for (auto b : backup) cudaFree(b);
+  if (rc) return rc;
   int h = 0;
   CK(cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) return read_error_word(ctx);
-  int rc = build_tables(ctx, best.TX, best.TY, best.occ);
+  best.persistent = ms_scheme[1] <= ms_scheme[0] ? 1 : 0;
+  best.ms = (best.persistent ? ms_scheme[1] : ms_scheme[0]) / 3.0;
+  rc = use_scheme(best.persistent);
   if (rc) return rc;
   cache[k] = best;
   write_cache(cache_path, cache);
   if (tile_out) {
     tile_out[0] = ctx->TX;
     tile_out[1] = ctx->TY;
+  }
+  return MHD_OK;
+}
+
+int mhd_step_scheme(mhd_ctx* ctx, int* persistent_out) {
+  if (!ctx || !persistent_out) return MHD_ERR_ARG;
+  *persistent_out = ctx->persistent ? 1 : 0;
+  return MHD_OK;
+}
+
+int mhd_set_step_scheme(mhd_ctx* ctx, int persistent) {
+  if (!ctx || (persistent != 0 && persistent != 1)) return MHD_ERR_ARG;
+  if (persistent && !(ctx->flags & MHD_FLAG_PERSISTENT))
+    return fail(ctx, MHD_ERR_STATE, "the persistent scheme needs MHD_FLAG_PERSISTENT");
+  if (persistent && ctx->P[0].dev.ns > 0) return fail(ctx, MHD_ERR_STATE, "the persistent step carries no scalars");
+  if (!persistent && make_aux_streams(ctx)) return fail(ctx, MHD_ERR_CUDA, "per-phase streams");
+  if ((persistent != 0) != ctx->persistent) {
+    ctx->persistent = persistent != 0;
+    ctx->w_valid = false;
+    drop_graph(ctx);
   }
   return MHD_OK;
 }

@@ -889,7 +889,6 @@ template <class R, int D, int ORDER>
 __device__ __forceinline__ void flux_point(const PatchDev& P, const R* __restrict__ W,
                                            const double* __restrict__ Ub, R* __restrict__ F,
                                            int i, int j, int k, int solver) {
-  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long q = qidx(P, i, j, k), QS = P.QS, st = qstride(P, D);
   R f[8], kap[3];
   Gam<R>::kappa(P, kap[0], kap[1], kap[2]);

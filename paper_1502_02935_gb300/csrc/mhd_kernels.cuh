@@ -312,14 +312,6 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
     else if (c == 0) sEx[buf][jj * kTX + ii] = e;
     else sEy[buf][jj * SX + ii] = e;
   };
-  const long long SZ = (long long)P.QX * P.QY, QS = P.QS;
-  const R* __restrict__ Fx = (const R*)P.F[0];
-  const R* __restrict__ Fy = (const R*)P.F[1];
-  const R* __restrict__ Fz = (const R*)P.F[2];
-  const R* __restrict__ ecx = Win + WEX * QS;
-  const R* __restrict__ ecy = Win + WEY * QS;
-  const R* __restrict__ ecz = Win + WEZ * QS;
-  R cFx0 = R(0), cFx6 = R(0), cFy0 = R(0), cFy5 = R(0), cex0 = R(0), cex1 = R(0), cey0 = R(0), cey1 = R(0);
   for (int k = kz0; k < kz1; ++k) {
     const int cur = (k - kz0) & 1, nxt = cur ^ 1;
     const bool first = k == kz0;

@@ -73,7 +73,8 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_surrogate_params", "mhd_surrogate_rows", "mhd_mlp_forward", "mhd_mlp_grad",
            "mhd_mlp_forward_tc", "mhd_mlp_grad_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
            "mhd_set_inflow", "mhd_set_scalars", "mhd_set_scalar_state", "mhd_get_scalar_state",
-           "mhd_set_inflow_scalars", "mhd_surrogate_fallback_cells"]
+           "mhd_set_inflow_scalars", "mhd_surrogate_fallback_cells", "mhd_step_scheme",
+           "mhd_set_step_scheme"]
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics
 RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
@@ -119,6 +120,8 @@ def lib():
     L.mhd_get_profile.argtypes = [vp, dp, C.POINTER(C.c_longlong), ip]
     L.mhd_cfl_dt_noalloc.argtypes = [C.POINTER(PatchDesc), C.c_double, vp, vp, vp, vp]
     L.mhd_autotune.argtypes = [vp, C.c_char_p, ip, C.POINTER(C.c_int)]
+    L.mhd_step_scheme.argtypes = [vp, C.POINTER(C.c_int)]
+    L.mhd_set_step_scheme.argtypes = [vp, ip]
     L.mhd_set_wait_limit.argtypes = [vp, C.c_double, ip]
     L.mhd_set_thermal.argtypes = [vp, C.POINTER(ThermalDesc)]
     L.mhd_thermal_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
@@ -327,6 +330,16 @@ class Grid:
         path = cache_path.encode() if cache_path else None
         self._check(self.L.mhd_autotune(self.h, path, int(force), tile), "mhd_autotune")
         return int(tile[0]), int(tile[1])
+
+    def step_scheme(self) -> str:
+        """'persistent' (one launch per step) or 'per_phase' (the autotuner's choice on a
+        context made with FLAG_PERSISTENT)."""
+        v = C.c_int()
+        self._check(self.L.mhd_step_scheme(self.h, C.byref(v)), "mhd_step_scheme")
+        return "persistent" if v.value else "per_phase"
+
+    def set_step_scheme(self, scheme: str):
+        self._check(self.L.mhd_set_step_scheme(self.h, 1 if scheme == "persistent" else 0), "mhd_set_step_scheme")
 
     def set_wait_limit(self, limit_ms: float, phantom_blocks: int = 0):
         self._check(self.L.mhd_set_wait_limit(self.h, float(limit_ms), int(phantom_blocks)), "mhd_set_wait_limit")

@@ -69,13 +69,41 @@ def test_autotune_keeps_state_and_caches(tmp_path):
     cache = str(tmp_path / "tune.json")
     tx, ty = g.autotune(cache)
     assert tx * ty in (128, 256, 512)
+    scheme = g.step_scheme()
+    assert scheme in ("persistent", "per_phase")
     after = _all_states(g, len(sts))
     for sa, sb in zip(before, after):
         assert np.array_equal(sa.U, sb.U)
     assert g.autotune(cache) == (tx, ty)  # served from the cache
+    assert g.step_scheme() == scheme
+    assert '"persistent": %d' % (scheme == "persistent") in open(cache).read()
     g.step(-1.0)
     g.sync()
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_switching_schemes_on_one_context(precision):
+    """A context made with FLAG_PERSISTENT steps with either scheme: two steps per phase after
+    two persistent steps equal the same four steps on a per-phase context (within the step's
+    tolerance: the two schemes order some sums differently), and the persistent scheme is
+    refused on a context made without the flag."""
+    sts = batch()[:3]
+    a = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_PERSISTENT | mhd.FLAG_GRAPH)
+    b = mhd.Grid(sts, precision=precision, cfl=0.4, flags=mhd.FLAG_GRAPH)
+    for s in range(4):
+        if s == 2:
+            a.set_step_scheme("per_phase")
+            assert a.step_scheme() == "per_phase"
+        a.step(-1.0)
+        b.step(-1.0)
+    tol = 3 * FP64_TOL if precision == "fp64" else 1e-6
+    for p in range(len(sts)):
+        assert_close(a.get_state(p), b.get_state(p), 4 * tol, f"patch {p}", normalized=(precision == "mixed"))
+    with pytest.raises(mhd.MHDError):
+        b.set_step_scheme("persistent")
+    a.close()
+    b.close()
 
 
 def test_barrier_timeout_is_reported():
