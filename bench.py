@@ -74,12 +74,13 @@ KCLASS = {
 FP64_OPS_PER_SM_CLK = 2
 # The step's algorithmic HBM bytes per cell: read the 8 FP64 fields of U^n, write U^n+1.
 ALG_BYTES_PER_CELL = 128.0
-# DRAM bytes (read + write) per item of the dominant kernel, from one ncu capture of the
-# EMF + update kernel on turbulence 192^3 (2.195 GB per launch over 192^3 cells, planes
-# marched as on 256^3); scaled by the items of a launch.  Retake it when the kernel changes.
-MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 2.195e9 / 192 ** 3}
-MEASURED_DRAM_NOTE = {"emf_update": "ncu dram__bytes_read.sum + dram__bytes_write.sum at turbulence 192^3, "
-                                    "per cell, scaled to this launch"}
+# DRAM bytes (read + write) per item of the dominant kernel, from one ncu capture of each
+# stage of the EMF + update kernel on turbulence 192^3 (corrector 2.048 GB, predictor 1.747 GB
+# per launch over 192^3 cells, planes marched as on 256^3), their mean scaled by the items of a
+# launch.  Retake it when the kernel changes.
+MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 0.5 * (2.048e9 + 1.747e9) / 192 ** 3}
+MEASURED_DRAM_NOTE = {"emf_update": "ncu dram bytes (read + write) at turbulence 192^3, mean of the predictor "
+                                    "and corrector launches, per cell, scaled to this launch"}
 
 
 def units_per_launch(cls: str, n: int) -> int:
@@ -263,11 +264,11 @@ def run_batched(args, stream, world=1, rank=0, pg=None):
     beside the same batch stepped with one launch per phase per patch."""
     import torch
     from paper_1502_02935_gb300 import inputs, mhd, sharding
-    allst = inputs.blast_batch(64, seed=SEED)
+    allst = inputs.blast_batch(64, seed=SEED)[:args.batch]
     mine = sharding.partition([s.geom.ncell for s in allst], world)[rank]
     sts = [allst[i] for i in mine]  # this rank's share; no data crosses ranks
     cells = sum(s.geom.ncell for s in allst)
-    out = {"workload": "64 periodic blast patches, edges from {32,48,64,96,128} (seed 1502), gamma=5/3, "
+    out = {"workload": f"{args.batch} periodic blast patches, edges from {{32,48,64,96,128}} (seed 1502), gamma=5/3, "
                        "rho=1, p=0.1 / 10 inside r<0.1, |B|=1/sqrt2 along a seeded direction; mixed path",
            "cells": cells, "unit": "zone-updates/s"}
     # one context: the autotuner picks the tiles of the persistent step and then the faster
@@ -749,6 +750,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_CELLS, help="cells per axis (default 256)")
+    ap.add_argument("--batch", type=int, default=64, help="patches of the batched workload (the first of the "
+                    "64-patch seeded batch; default 64)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-patch batched workload")
     ap.add_argument("--disc", type=int, nargs=3, default=[512, 512, 128],
