@@ -521,7 +521,7 @@ def run_table(args):
     stream = torch.cuda.Stream()
 
     def gpu_rate(states, precision, steps, flags=mhd.FLAG_GRAPH, src=None, thermal=None, riemann=None,
-                 recon=None, inflow=None):
+                 recon=None, inflow=None, scheme=None):
         sts = states if isinstance(states, list) else [states]
         g = mhd.Grid(sts if len(sts) > 1 else sts[0], precision=precision, cfl=CFL, flags=flags,
                      stream=stream.cuda_stream)
@@ -537,6 +537,8 @@ def run_table(args):
             g.set_thermal(mhd.THERMAL_PLAIN, **thermal)
         if flags & mhd.FLAG_PERSISTENT:
             g.autotune(None)
+            if scheme:
+                g.set_step_scheme(scheme)
         for _ in range(3):
             g.step(-1.0)
         torch.cuda.synchronize()
@@ -635,7 +637,9 @@ def run_table(args):
         table["C4 64 blast patches"] = {
             "gpu_fp64_per_phase": gpu_rate(sts, "fp64", 3),
             "gpu_mixed_per_phase": gpu_rate(sts, "mixed", 10),
-            "gpu_mixed_persistent": gpu_rate(sts, "mixed", 10, flags=mhd.FLAG_GRAPH | mhd.FLAG_PERSISTENT),
+            "gpu_mixed_persistent": gpu_rate(sts, "mixed", 10, flags=mhd.FLAG_GRAPH | mhd.FLAG_PERSISTENT,
+                                             scheme="persistent"),
+            "gpu_mixed_autotuned": gpu_rate(sts, "mixed", 10, flags=mhd.FLAG_GRAPH | mhd.FLAG_PERSISTENT),
             "oracle_1core": r1, "oracle_1core_sample": "first 4 patches, 1 step", "oracle_all": rn,
             "oracle_all_sample": "all 64 patches, 1 step"}
     if want("C5"):
