@@ -302,7 +302,8 @@ int mhd_set_profiling(mhd_ctx* ctx, int on);
  * class c, for c < n (n >= 16).  Synchronises. */
 int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
 
-/* Autotuner of the batched step (context made with MHD_FLAG_PERSISTENT).  It times the
+/* Autotuner of the batched step (context made with MHD_FLAG_PERSISTENT; a schedule, not part
+ * of the paper's method).  It times the
  * persistent step for each candidate tile shape (TX x TY points of one z-plane per CTA) and
  * CTA count per SM and keeps the fastest; then it times that persistent step against the
  * per-phase scheme (each patch's kernels as one chain on one of up to eight streams) over
@@ -314,8 +315,10 @@ int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
  * receives TX, TY.  MHD_ERR_STATE without MHD_FLAG_PERSISTENT. */
 int mhd_autotune(mhd_ctx* ctx, const char* cache_path, int force, int* tile_out);
 
-/* The scheme the context's steps run with: *persistent_out = 1 for one persistent launch per
- * step (MHD_FLAG_PERSISTENT, until mhd_autotune picks the per-phase scheme), 0 for per-phase
+/* The scheme the context's steps run with (the schedule of the same step, Eq. 7-8, over a
+ * batch of independent patches; the paper runs one grid per MPI rank and has no
+ * counterpart): *persistent_out = 1 for one persistent launch per step
+ * (MHD_FLAG_PERSISTENT, until mhd_autotune picks the per-phase scheme), 0 for per-phase
  * launches.  mhd_set_step_scheme chooses it: 1 needs MHD_FLAG_PERSISTENT and no passive
  * scalars (MHD_ERR_STATE otherwise); switching drops the captured graphs and the next step
  * starts with the recovery.  Both schemes advance the same state. */
