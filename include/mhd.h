@@ -161,6 +161,15 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* src);
  * all three.  MHD_ERR_ARG for another value. */
 int mhd_set_riemann(mhd_ctx* ctx, int solver);
 
+/* Which kernel computes the fluxes through y and z faces (the same fluxes, Eq. 3 with the
+ * interface states of Eq. 12-14; a choice of schedule): MHD_FLUX_MARCH, threads marching
+ * along the flux direction over segments of 16 faces (8, 4 or 2 on thinner boxes), each cell
+ * loaded and reconstructed once; MHD_FLUX_PER_FACE, one thread per face; MHD_FLUX_AUTO (the
+ * default), marching where the box gives at least two waves of threads, per face on thinner
+ * ones (2D planes, small patches).  x faces are always per face.  Drops captured graphs. */
+enum { MHD_FLUX_AUTO = 0, MHD_FLUX_MARCH = 1, MHD_FLUX_PER_FACE = 2 };
+int mhd_set_flux_scheme(mhd_ctx* ctx, int scheme);
+
 /* Reconstruction of every patch for the following steps, MHD_RECON_* (the minmod
  * kappa-scheme with K1 = (1 - kappa)/4, K2 = (1 + kappa)/4, b = (3 - kappa)/(1 - kappa)).
  * MHD_ERR_ARG for another value. */
@@ -373,6 +382,15 @@ int mhd_mlp_grad(long long n, const float* rows, const float* params, float* gra
  * mhd_surrogate_train uses.  MHD_ERR_TIMEOUT if a bounded wait for the MMAs ran out. */
 int mhd_mlp_grad_tc(long long n, const float* rows, const float* params, float* grad, float* loss_sum,
                     void* stream);
+
+/* Unit-level entry for a parity test of the mixed path's FP64 <-> FP32 conversions (the
+ * precision split's plumbing; the paper has none), which run on the integer pipe: for n
+ * elements of device arrays, d2f_out = d_in rounded to FP32 (nearest, ties to even; a
+ * result below the smallest normal float becomes a signed zero; overflow gives inf; NaN a
+ * quiet NaN) and f2d_out = f_in widened exactly (subnormal floats become a signed zero).
+ * Synchronises stream. */
+int mhd_convert_fp(long long n, const double* d_in, const float* f_in, float* d2f_out, double* f2d_out,
+                   void* stream);
 
 /* Largest patch (nx*ny*nz cells) that mhd_cfl_dt_noalloc accepts. */
 #define MHD_NOALLOC_MAX_CELLS 8388608

@@ -711,6 +711,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     D.err = ctx->err;
     D.index = p;
     D.riemann = RIEMANN_HLLD;
+    D.flux_scheme = FLUX_AUTO;
     set_kappa(D, 1.0 / 3.0);
     D.floors = 0;
     D.rho_floor = D.pr_floor = 0.0;
@@ -883,6 +884,14 @@ int mhd_set_reconstruction(mhd_ctx* ctx, int recon) {
   for (auto& p : ctx->P) set_kappa(p.dev, kappa);
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   drop_graph(ctx);  // the coefficients are part of the captured launches' arguments
+  return MHD_OK;
+}
+
+int mhd_set_flux_scheme(mhd_ctx* ctx, int scheme) {
+  if (!ctx) return MHD_ERR_ARG;
+  if (scheme < MHD_FLUX_AUTO || scheme > MHD_FLUX_PER_FACE) return fail(ctx, MHD_ERR_ARG, "unknown flux scheme");
+  for (auto& p : ctx->P) p.dev.flux_scheme = scheme;
+  drop_graph(ctx);
   return MHD_OK;
 }
 
@@ -1627,6 +1636,29 @@ int mhd_riemann_hlld(int n, const double* wl, const double* wr, const double* bn
   cudaStream_t s = (cudaStream_t)stream;
   if (be.riemann(MHD_RIEMANN_HLLD, n, wl, wr, bn, gamma, flux, s)) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  return MHD_OK;
+}
+
+namespace {
+// the mixed path's FP64 <-> FP32 conversions (integer pipe), element by element
+__global__ void k_convert(long long n, const double* __restrict__ d_in, const float* __restrict__ f_in,
+                          float* __restrict__ d2f_out, double* __restrict__ f2d_out) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    d2f_out[q] = d2f_alu(d_in[q]);
+    f2d_out[q] = f2d_alu(f_in[q]);
+  }
+}
+}  // namespace
+
+int mhd_convert_fp(long long n, const double* d_in, const float* f_in, float* d2f_out, double* f2d_out,
+                   void* stream) {
+  if (n < 0 || (n > 0 && (!d_in || !f_in || !d2f_out || !f2d_out))) return MHD_ERR_ARG;
+  if (n == 0) return MHD_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  k_convert<<<(unsigned)blocks, 256, 0, s>>>(n, d_in, f_in, d2f_out, f2d_out);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
   return MHD_OK;
 }
 

@@ -29,6 +29,7 @@ enum { WEX = 8, WEY = 9, WEZ = 10, NWQ = 11 };
 enum { NFLUX = 7 };  // rho (with the no-motion bit), mx, my, mz, E, B_t1, B_t2
 enum : int { ERR_NONFINITE = 1, ERR_NEGATIVE = 2, ERR_TIMEOUT = 4 };
 enum { POT_NONE = 0, POT_GAUSS_X = 1, POT_LOG_DISC = 2 };
+enum { FLUX_AUTO = 0, FLUX_MARCH = 1, FLUX_PER_FACE = 2 };
 // Riemann solvers of Section 2.1: HLLD (MHD), HLLC and HLL (pure gas dynamics)
 enum { RIEMANN_HLLD = 0, RIEMANN_HLLC = 1, RIEMANN_HLL = 2 };
 
@@ -61,6 +62,7 @@ struct PatchDev {
   double rho_floor, pr_floor, pr_ceil;
   unsigned long long* floored;  // count of cells changed by the end-of-step floors
   int riemann;                  // RIEMANN_*
+  int flux_scheme;              // FLUX_* (host side: which kernel computes the y and z fluxes)
   // kappa-scheme coefficients K1 = (1 - kappa)/4, K2 = (1 + kappa)/4, b = (3 - kappa)/(1 - kappa)
   double rK1, rK2, rb;
   float rK1_f, rK2_f, rb_f;

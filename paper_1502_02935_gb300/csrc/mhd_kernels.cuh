@@ -75,15 +75,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 1) k_flux(PatchDe
 // w + K1 m1 + K2 m2 (w_L there), and at the lower face, w - K1 m2 - K2 m1 (w_R there) -- the
 // expressions of kappa_face, where the per-face kernel evaluates both neighbours of every face.
 // The donor-cell stage carries the previous cell.  Results equal those of flux_point.
-// Segments of 16 faces; FP32 kernels at four (donor cell) and three (kappa-scheme) resident
-// CTAs per SM: the fastest of 8, 16, 32, 64 faces and three or four CTAs (measured at 256^3:
-// the kappa kernels spill at four).
+// Segments of seg faces (16 where the box gives enough columns, fewer on thinner boxes, see
+// launch_flux); FP32 kernels at four (donor cell) and three (kappa-scheme) resident CTAs per
+// SM: the fastest of 8, 16, 32, 64 faces and three or four CTAs at 256^3 (the kappa kernels
+// spill at four).
 constexpr int kMarch = 16;
 
 template <class R, int D, int ORDER, int S>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ORDER == 1 ? 4 : 3) : 1) k_flux_march(PatchDev P,
                                                                              const double* __restrict__ Ub,
-                                                                             Range rg) {
+                                                                             Range rg, int seg) {
   static_assert(D == 1 || D == 2, "marching along y or z");
   constexpr int T = D == 1 ? 2 : 1;  // the transverse axis other than x
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
@@ -94,8 +95,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ORDER == 1 ? 4 : 3) 
   int c3[3];
   c3[0] = rg.lo[0] + (int)(r - qt * e0);
   c3[T] = rg.lo[T] + (int)qt;
-  const int f0 = rg.lo[D] + (int)blockIdx.y * kMarch;
-  const int f1 = min(f0 + kMarch, rg.lo[D] + rg.ext[D]);
+  const int f0 = rg.lo[D] + (int)blockIdx.y * seg;
+  const int f1 = min(f0 + seg, rg.lo[D] + rg.ext[D]);
   const R* __restrict__ W = (const R*)P.W;
   R* __restrict__ F = (R*)P.F[D];
   const long long QS = P.QS, st = qstride(P, D);
@@ -531,14 +532,22 @@ template <class R, int D, int ORDER>
 static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cudaStream_t s) {
   if constexpr (D > 0) {
     // y and z faces: the marching kernel, one thread per (x, other transverse) position and
-    // segment of kMarch faces
+    // segment of seg faces.  seg = 16, 8, 4 or 2, the longest that still gives two waves of
+    // three resident CTAs of kBlock threads per SM; a box too thin even for seg = 2 (a 2D
+    // plane, a small patch) takes the per-face kernel, which has one thread per face
     constexpr int T = D == 1 ? 2 : 1;
     const long long plane = (long long)fr.ext[0] * fr.ext[T];
-    const dim3 g((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)((fr.ext[D] + kMarch - 1) / kMarch), 1);
-    if (P.riemann == RIEMANN_HLLC) k_flux_march<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr);
-    else if (P.riemann == RIEMANN_HLL) k_flux_march<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr);
-    else k_flux_march<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr);
-    return;
+    const long long want = 2LL * 3 * kBlock * sm_count();
+    int seg = kMarch;
+    while (P.flux_scheme == FLUX_AUTO && seg > 2 && plane * ((fr.ext[D] + seg - 1) / seg) < want) seg >>= 1;
+    if (P.flux_scheme == FLUX_MARCH ||
+        (P.flux_scheme == FLUX_AUTO && plane * ((fr.ext[D] + seg - 1) / seg) >= want)) {
+      const dim3 g((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)((fr.ext[D] + seg - 1) / seg), 1);
+      if (P.riemann == RIEMANN_HLLC) k_flux_march<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
+      else if (P.riemann == RIEMANN_HLL) k_flux_march<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
+      else k_flux_march<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
+      return;
+    }
   }
   const dim3 g = grid_of(fr);
   if (P.riemann == RIEMANN_HLLC) k_flux<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr);

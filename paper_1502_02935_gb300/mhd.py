@@ -74,10 +74,12 @@ EXPORTS = ["mhd_init_grid", "mhd_set_sources", "mhd_step", "mhd_cfl_dt", "mhd_cf
            "mhd_mlp_forward_tc", "mhd_mlp_grad_tc", "mhd_set_riemann", "mhd_riemann_flux", "mhd_set_reconstruction",
            "mhd_set_inflow", "mhd_set_scalars", "mhd_set_scalar_state", "mhd_get_scalar_state",
            "mhd_set_inflow_scalars", "mhd_surrogate_fallback_cells", "mhd_step_scheme",
-           "mhd_set_step_scheme"]
+           "mhd_set_step_scheme", "mhd_convert_fp", "mhd_set_flux_scheme"]
 
 # Riemann solvers (Section 2.1): HLLD for MHD; HLLC and HLL for pure gas dynamics
 RIEMANN = {"hlld": 0, "hllc": 1, "hll": 2}
+# kernels of the y and z fluxes (mhd_set_flux_scheme)
+FLUX_SCHEMES = {"auto": 0, "march": 1, "per_face": 2}
 # corrector reconstructions of Eq. 12-14 (kappa = 1/3, 0, -1)
 RECON = {"kappa_third": 0, "kappa_zero": 1, "kappa_upwind": 2}
 
@@ -122,6 +124,8 @@ def lib():
     L.mhd_autotune.argtypes = [vp, C.c_char_p, ip, C.POINTER(C.c_int)]
     L.mhd_step_scheme.argtypes = [vp, C.POINTER(C.c_int)]
     L.mhd_set_step_scheme.argtypes = [vp, ip]
+    L.mhd_set_flux_scheme.argtypes = [vp, ip]
+    L.mhd_convert_fp.argtypes = [C.c_longlong, vp, vp, vp, vp, vp]
     L.mhd_set_wait_limit.argtypes = [vp, C.c_double, ip]
     L.mhd_set_thermal.argtypes = [vp, C.POINTER(ThermalDesc)]
     L.mhd_thermal_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
@@ -338,6 +342,10 @@ class Grid:
         self._check(self.L.mhd_step_scheme(self.h, C.byref(v)), "mhd_step_scheme")
         return "persistent" if v.value else "per_phase"
 
+    def set_flux_scheme(self, scheme: str):
+        """'auto', 'march' or 'per_face': the kernel of the y and z fluxes."""
+        self._check(self.L.mhd_set_flux_scheme(self.h, FLUX_SCHEMES[scheme]), "mhd_set_flux_scheme")
+
     def set_step_scheme(self, scheme: str):
         self._check(self.L.mhd_set_step_scheme(self.h, 1 if scheme == "persistent" else 0), "mhd_set_step_scheme")
 
@@ -473,3 +481,20 @@ def mlp_grad(xs, targets, params, tcgen05: bool = False):
     if rc != 0:
         raise MHDError(rc, "mhd_mlp_grad")
     return float(loss.item()), g.cpu().numpy()
+
+
+def convert_fp(d, f):
+    """The mixed path's FP64 -> FP32 and FP32 -> FP64 device conversions of d and f (numpy
+    arrays of one length); returns (float32 array, float64 array)."""
+    import torch
+    d_t = torch.as_tensor(np.ascontiguousarray(d, dtype=np.float64)).cuda()
+    f_t = torch.as_tensor(np.ascontiguousarray(f, dtype=np.float32)).cuda()
+    o_f = torch.empty(d_t.numel(), dtype=torch.float32, device="cuda")
+    o_d = torch.empty(f_t.numel(), dtype=torch.float64, device="cuda")
+    if d_t.numel() != f_t.numel():
+        raise ValueError("d and f must have the same length")
+    rc = lib().mhd_convert_fp(d_t.numel(), d_t.data_ptr(), f_t.data_ptr(), o_f.data_ptr(), o_d.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise MHDError(rc, "mhd_convert_fp")
+    return o_f.cpu().numpy(), o_d.cpu().numpy()

@@ -61,9 +61,11 @@ MHD_CASES = {
 }
 
 
-def _run(st, precision, solver, nsteps, cfl=0.4):
+def _run(st, precision, solver, nsteps, cfl=0.4, flux=None):
     g = mhd.Grid(st, precision=precision, cfl=cfl)
     g.set_riemann(solver)
+    if flux:
+        g.set_flux_scheme(flux)
     ref = st
     for _ in range(nsteps):
         dt = oracle.cfl_dt(ref, cfl)
@@ -74,18 +76,20 @@ def _run(st, precision, solver, nsteps, cfl=0.4):
     return got, ref
 
 
+@pytest.mark.parametrize("flux", ["auto", "march"])
 @pytest.mark.parametrize("solver", ["hllc", "hll"])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_fp64_hydro_steps_match_oracle(solver, case):
-    got, ref = _run(CASES[case](), "fp64", solver, 3)
-    assert_close(got, ref, FP64_TOL, f"{case} {solver}")
+def test_fp64_hydro_steps_match_oracle(solver, case, flux):
+    got, ref = _run(CASES[case](), "fp64", solver, 3, flux=flux)
+    assert_close(got, ref, FP64_TOL, f"{case} {solver} {flux}")
 
 
+@pytest.mark.parametrize("flux", ["auto", "march"])
 @pytest.mark.parametrize("solver", ["hllc", "hll"])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_mixed_hydro_step_matches_oracle(solver, case):
-    got, ref = _run(CASES[case](), "mixed", solver, 1)
-    assert_close(got, ref, MIXED_TOL, f"{case} {solver}", normalized=True)
+def test_mixed_hydro_step_matches_oracle(solver, case, flux):
+    got, ref = _run(CASES[case](), "mixed", solver, 1, flux=flux)
+    assert_close(got, ref, MIXED_TOL, f"{case} {solver} {flux}", normalized=True)
 
 
 @pytest.mark.parametrize("case", sorted(MHD_CASES))

@@ -19,9 +19,11 @@ CASES = {
 }
 
 
-def _run(st, precision, recon, nsteps, cfl=0.4):
+def _run(st, precision, recon, nsteps, cfl=0.4, flux=None):
     g = mhd.Grid(st, precision=precision, cfl=cfl)
     g.set_reconstruction(recon)
+    if flux:
+        g.set_flux_scheme(flux)
     ref = st
     for _ in range(nsteps):
         dt = oracle.cfl_dt(ref, cfl)
@@ -32,18 +34,20 @@ def _run(st, precision, recon, nsteps, cfl=0.4):
     return got, ref
 
 
+@pytest.mark.parametrize("flux", ["auto", "march"])
 @pytest.mark.parametrize("recon", ["kappa_zero", "kappa_upwind"])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_fp64_kappa_variant_matches_oracle(recon, case):
-    got, ref = _run(CASES[case](), "fp64", recon, 3)
-    assert_close(got, ref, FP64_TOL, f"{case} {recon}")
+def test_fp64_kappa_variant_matches_oracle(recon, case, flux):
+    got, ref = _run(CASES[case](), "fp64", recon, 3, flux=flux)
+    assert_close(got, ref, FP64_TOL, f"{case} {recon} {flux}")
 
 
+@pytest.mark.parametrize("flux", ["auto", "march"])
 @pytest.mark.parametrize("recon", ["kappa_zero", "kappa_upwind"])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_mixed_kappa_variant_matches_oracle(recon, case):
-    got, ref = _run(CASES[case](), "mixed", recon, 1)
-    assert_close(got, ref, MIXED_TOL, f"{case} {recon}", normalized=True)
+def test_mixed_kappa_variant_matches_oracle(recon, case, flux):
+    got, ref = _run(CASES[case](), "mixed", recon, 1, flux=flux)
+    assert_close(got, ref, MIXED_TOL, f"{case} {recon} {flux}", normalized=True)
 
 
 # Rotor error scale.  By and the rotational momenta grow from zero by cancellation of
