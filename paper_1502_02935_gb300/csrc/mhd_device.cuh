@@ -347,39 +347,11 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   const R sm = (dr * rr * ur - dl * rl * ul - ptr + ptl) * iden;
   const R pts = (dr * rr * ptl - dl * rl * ptr + rl * rr * dr * dl * (ur - ul)) * iden;
 
-  // single-star states on both sides
-  R rs[2], vs[2], zs[2], bys[2], bzs[2], es[2];
-  {
-    const R S[2] = {sl, sr};
-    const R rho[2] = {rl, rr}, un[2] = {ul, ur}, v1[2] = {vl, vr}, v2[2] = {zl, zr};
-    const R b1[2] = {byl, byr}, b2[2] = {bzl, bzr}, ee[2] = {el, er}, pt[2] = {ptl, ptr};
-    const R vb[2] = {vbl, vbr};
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const R ds = S[s] - un[s];
-      const R ism = Ar<R>::rcp(S[s] - sm);
-      rs[s] = rho[s] * ds * ism;
-      const R t1 = rho[s] * ds * (S[s] - sm);
-      const R den = t1 - bn2;
-      if (Ar<R>::abs_(den) < Ar<R>::degen * (Ar<R>::abs_(t1) + bn2)) {
-        vs[s] = v1[s];
-        zs[s] = v2[s];
-        bys[s] = b1[s];
-        bzs[s] = b2[s];
-      } else {
-        const R iden2 = Ar<R>::rcp(den);
-        const R fv = bn * (sm - un[s]) * iden2;
-        const R fb = (rho[s] * ds * ds - bn2) * iden2;
-        vs[s] = v1[s] - b1[s] * fv;
-        zs[s] = v2[s] - b2[s] * fv;
-        bys[s] = b1[s] * fb;
-        bzs[s] = b2[s] * fb;
-      }
-      const R vbs = sm * bn + vs[s] * bys[s] + zs[s] * bzs[s];
-      es[s] = (ds * ee[s] - pt[s] * un[s] + pts * sm + bn * (vb[s] - vbs)) * ism;
-    }
-  }
-  const R sqrl = Ar<R>::sqrt_(rs[0]), sqrr = Ar<R>::sqrt_(rs[1]);
+  // single-star densities on both sides; with them the rotational speeds, which fix the
+  // region of the fan the face lies in
+  const R isml = Ar<R>::rcp(sl - sm), ismr = Ar<R>::rcp(sr - sm);
+  const R rsl = rl * dl * isml, rsr = rr * dr * ismr;
+  const R sqrl = Ar<R>::sqrt_(rsl), sqrr = Ar<R>::sqrt_(rsr);
   const R abn = Ar<R>::abs_(bn);
   const R ssl = sm - abn * Ar<R>::rcp(sqrl);
   const R ssr = sm + abn * Ar<R>::rcp(sqrr);
@@ -387,7 +359,6 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   // choose the side and whether the double-star state is needed
   int side;  // 0: left, 1: right
   bool dbl;
-  R S, Ss;
   if (ssl >= R(0)) {
     side = 0; dbl = false;
   } else if (sm >= R(0)) {
@@ -397,8 +368,33 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   } else {
     side = 1; dbl = false;
   }
-  S = side ? sr : sl;
-  Ss = side ? ssr : ssl;
+  // the remaining single-star state of side s (v*, B*, E*; M&K Eq. 44-48): the outer star
+  // regions need one side's, the double-star region both
+  auto star = [&](int s, R& vs, R& zs, R& bys, R& bzs, R& es) {
+    const R S_ = s ? sr : sl, rho_ = s ? rr : rl, un_ = s ? ur : ul, v1_ = s ? vr : vl, v2_ = s ? zr : zl;
+    const R b1_ = s ? byr : byl, b2_ = s ? bzr : bzl, ee_ = s ? er : el, pt_ = s ? ptr : ptl;
+    const R vb_ = s ? vbr : vbl, ds = s ? dr : dl, ism = s ? ismr : isml;
+    const R t1 = rho_ * ds * (S_ - sm);
+    const R den = t1 - bn2;
+    if (Ar<R>::abs_(den) < Ar<R>::degen * (Ar<R>::abs_(t1) + bn2)) {
+      vs = v1_;
+      zs = v2_;
+      bys = b1_;
+      bzs = b2_;
+    } else {
+      const R iden2 = Ar<R>::rcp(den);
+      const R fv = bn * (sm - un_) * iden2;
+      const R fb = (rho_ * ds * ds - bn2) * iden2;
+      vs = v1_ - b1_ * fv;
+      zs = v2_ - b2_ * fv;
+      bys = b1_ * fb;
+      bzs = b2_ * fb;
+    }
+    const R vbs = sm * bn + vs * bys + zs * bzs;
+    es = (ds * ee_ - pt_ * un_ + pts * sm + bn * (vb_ - vbs)) * ism;
+  };
+  const R S = side ? sr : sl;
+  const R Ss = side ? ssr : ssl;
   const R rho = side ? rr : rl, un = side ? ur : ul, v1 = side ? vr : vl, v2 = side ? zr : zl;
   const R b1 = side ? byr : byl, b2 = side ? bzr : bzl, ee = side ? er : el, pt = side ? ptr : ptl;
   const R vb = side ? vbr : vbl;
@@ -411,9 +407,9 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   R F5 = b1 * un - bn * v1;
   R F6 = b2 * un - bn * v2;
   // F*_a = F_a + S_a (U*_a - U_a)
-  const R rsa = side ? rs[1] : rs[0], vsa = side ? vs[1] : vs[0], zsa = side ? zs[1] : zs[0];
-  const R bysa = side ? bys[1] : bys[0], bzsa = side ? bzs[1] : bzs[0];
-  const R esa = side ? es[1] : es[0];
+  const R rsa = side ? rsr : rsl;
+  R vsa, zsa, bysa, bzsa, esa;
+  star(side, vsa, zsa, bysa, bzsa, esa);
   F0 += S * (rsa - rho);
   F1 += S * (rsa * sm - rho * un);
   F2 += S * (rsa * vsa - rho * v1);
@@ -422,13 +418,19 @@ __device__ __forceinline__ void hlld(const R* wl, const R* wr, R bn, R gam, R* f
   F5 += S * (bysa - b1);
   F6 += S * (bzsa - b2);
   if (dbl) {
-    // double-star states (sqrt(rho*)-weighted, M&K Eq. 59-63); F** = F* + S*(U** - U*)
+    // the other side's single-star state, then the double-star states (sqrt(rho*)-weighted,
+    // M&K Eq. 59-63); F** = F* + S*(U** - U*)
+    R vso, zso, byso, bzso, eso;
+    star(1 - side, vso, zso, byso, bzso, eso);
+    const R vs0 = side ? vso : vsa, vs1 = side ? vsa : vso, zs0 = side ? zso : zsa, zs1 = side ? zsa : zso;
+    const R bys0 = side ? byso : bysa, bys1 = side ? bysa : byso, bzs0 = side ? bzso : bzsa,
+            bzs1 = side ? bzsa : bzso;
     const R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
     const R isum = Ar<R>::rcp(sqrl + sqrr);
-    const R vss = (sqrl * vs[0] + sqrr * vs[1] + (bys[1] - bys[0]) * sgn) * isum;
-    const R zss = (sqrl * zs[0] + sqrr * zs[1] + (bzs[1] - bzs[0]) * sgn) * isum;
-    const R byss = (sqrl * bys[1] + sqrr * bys[0] + sqrl * sqrr * (vs[1] - vs[0]) * sgn) * isum;
-    const R bzss = (sqrl * bzs[1] + sqrr * bzs[0] + sqrl * sqrr * (zs[1] - zs[0]) * sgn) * isum;
+    const R vss = (sqrl * vs0 + sqrr * vs1 + (bys1 - bys0) * sgn) * isum;
+    const R zss = (sqrl * zs0 + sqrr * zs1 + (bzs1 - bzs0) * sgn) * isum;
+    const R byss = (sqrl * bys1 + sqrr * bys0 + sqrl * sqrr * (vs1 - vs0) * sgn) * isum;
+    const R bzss = (sqrl * bzs1 + sqrr * bzs0 + sqrl * sqrr * (zs1 - zs0) * sgn) * isum;
     const R vbsa = sm * bn + vsa * bysa + zsa * bzsa;
     const R vbss = sm * bn + vss * byss + zss * bzss;
     const R sq = side ? sqrr : sqrl;
