@@ -680,6 +680,83 @@ __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx,
   return lim;
 }
 
+// The second half of prim_core for floor_prim_core: W at scratch index q and the CFL limit
+// from the recovered density, its reciprocal and the pressure (the same arithmetic as
+// prim_core's, which keeps its own copy: inlined into the update kernel without floors,
+// a shared tail cost that kernel registers and 6% of its time).
+template <class R>
+__device__ __forceinline__ R prim_tail(const PatchDev& P, double rho, double irho, double mx, double my, double mz,
+                                       double e, double sbx, double sby, double sbz, double p,
+                                       R* __restrict__ W, long long q, bool store, bool interior) {
+  const R rirho = Ar<R>::from_d(irho);
+  const R vx = Ar<R>::mul_rn(Ar<R>::from_d(mx), rirho), vy = Ar<R>::mul_rn(Ar<R>::from_d(my), rirho),
+          vz = Ar<R>::mul_rn(Ar<R>::from_d(mz), rirho);
+  const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
+  const R rr = Ar<R>::from_d(rho), pr = Ar<R>::from_d(p);
+  if (store) {
+    const long long QS = P.QS;
+    W[q] = rr;
+    W[WVX * QS + q] = vx;
+    W[WVY * QS + q] = vy;
+    W[WVZ * QS + q] = vz;
+    W[WP * QS + q] = pr;
+    W[WBX * QS + q] = bx;
+    W[WBY * QS + q] = by;
+    W[WBZ * QS + q] = bz;
+    W[WEX * QS + q] = cell_emf<R>(vy, vz, by, bz);
+    W[WEY * QS + q] = cell_emf<R>(vz, vx, bz, bx);
+    W[WEZ * QS + q] = cell_emf<R>(vx, vy, bx, by);
+  }
+  R lim = R(INFINITY);
+  if (interior) {
+    // positivity / finiteness on the bulk-type values; CFL arithmetic in the bulk type
+    if (!(isfinite(rr) && isfinite(pr) && finite_d(e))) {
+      atomicOr(P.err, ERR_NONFINITE);
+    } else if (!(rr > R(0)) || !(pr > R(0))) {
+      atomicOr(P.err, ERR_NEGATIVE);
+    }
+    const R v[3] = {vx, vy, vz};
+    const R b[3] = {bx, by, bz};
+    const R bb = Ar<R>::fma_rn(b[2], b[2], Ar<R>::fma_rn(b[1], b[1], Ar<R>::mul_rn(b[0], b[0])));
+    const R gam = Gam<R>::get(P);
+    R lr = R(INFINITY);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!P.act[a]) continue;
+      const R cf = fast_speed_rn<R>(rr, pr, bb, Ar<R>::mul_rn(b[a], b[a]), gam);
+      const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::add_rn(Ar<R>::abs_(v[a]), cf));
+      lr = t < lr ? t : lr;
+    }
+    lim = lr;
+  }
+  return lim;
+}
+
+
+// The end-of-step floors and the recovery of the new state in one pass, sharing their FP64
+// arithmetic (floors on): with rho_f = max(rho, rho_floor), the recovery's pressure with rho_f
+// is clamped to [rho_f pr_floor, rho_f pr_ceil].  An unchanged cell keeps its state and takes
+// W from that pressure, as prim_core would.  A changed cell gets rho_f and E rebuilt by the
+// energy closure from the clamped pressure (momentum kept), counted in *nfl, and is
+// recovered again from those stored values (so a standalone recovery gives the same W).
+template <class R>
+__device__ __forceinline__ R floor_prim_core(const PatchDev& P, double& rho, double mx, double my, double mz,
+                                             double& e, double sbx, double sby, double sbz,
+                                             R* __restrict__ W, long long q, int* nfl) {
+  const double rf = rho < P.rho_floor ? P.rho_floor : rho;
+  const double irho = inv_density<R>(rf);
+  const double m2 = __fma_rn(mz, mz, __fma_rn(my, my, __dmul_rn(mx, mx)));
+  const double b2 = __fma_rn(sbz, sbz, __fma_rn(sby, sby, __dmul_rn(sbx, sbx)));
+  const double p = __fma_rn(-P.egm1, b2, __fma_rn(-P.hgm1, __dmul_rn(m2, irho), __dmul_rn(P.gm1, e)));
+  const double lo = rf * P.pr_floor, hi = rf * P.pr_ceil;
+  const double pf = p < lo ? lo : (p > hi ? hi : p);
+  if (rf == rho && pf == p) return prim_tail<R>(P, rho, irho, mx, my, mz, e, sbx, sby, sbz, p, W, q, true, true);
+  rho = rf;
+  e = pf / P.gm1 + 0.5 * m2 * irho + 0.125 * b2;  // p/(gamma-1) + |m|^2/(2 rho) + |B_cc|^2/2
+  ++*nfl;
+  return prim_core<R>(P, rho, mx, my, mz, e, sbx, sby, sbz, W, q, true, true);
+}
+
 // W at a (possibly ghost) cell from U via the boundary index maps.
 template <class R>
 __device__ __forceinline__ R prim_point(const PatchDev& P, const double* __restrict__ U,
