@@ -680,19 +680,10 @@ __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx,
   return lim;
 }
 
-// The second half of prim_core for floor_prim_core: W at scratch index q and the CFL limit
-// from the recovered density, its reciprocal and the pressure (the same arithmetic as
-// prim_core's, which keeps its own copy: inlined into the update kernel without floors,
-// a shared tail cost that kernel registers and 6% of its time).
+// The W stores and the CFL limit of prim_core from the bulk-type values (efin: E finite).
 template <class R>
-__device__ __forceinline__ R prim_tail(const PatchDev& P, double rho, double irho, double mx, double my, double mz,
-                                       double e, double sbx, double sby, double sbz, double p,
-                                       R* __restrict__ W, long long q, bool store, bool interior) {
-  const R rirho = Ar<R>::from_d(irho);
-  const R vx = Ar<R>::mul_rn(Ar<R>::from_d(mx), rirho), vy = Ar<R>::mul_rn(Ar<R>::from_d(my), rirho),
-          vz = Ar<R>::mul_rn(Ar<R>::from_d(mz), rirho);
-  const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
-  const R rr = Ar<R>::from_d(rho), pr = Ar<R>::from_d(p);
+__device__ __forceinline__ R prim_store(const PatchDev& P, R rr, R vx, R vy, R vz, R bx, R by, R bz, R pr,
+                                        bool efin, R* __restrict__ W, long long q, bool store, bool interior) {
   if (store) {
     const long long QS = P.QS;
     W[q] = rr;
@@ -710,7 +701,7 @@ __device__ __forceinline__ R prim_tail(const PatchDev& P, double rho, double irh
   R lim = R(INFINITY);
   if (interior) {
     // positivity / finiteness on the bulk-type values; CFL arithmetic in the bulk type
-    if (!(isfinite(rr) && isfinite(pr) && finite_d(e))) {
+    if (!(isfinite(rr) && isfinite(pr) && efin)) {
       atomicOr(P.err, ERR_NONFINITE);
     } else if (!(rr > R(0)) || !(pr > R(0))) {
       atomicOr(P.err, ERR_NEGATIVE);
@@ -732,6 +723,41 @@ __device__ __forceinline__ R prim_tail(const PatchDev& P, double rho, double irh
   return lim;
 }
 
+// The second half of prim_core for floor_prim_core: W at scratch index q and the CFL limit
+// from the recovered density, its reciprocal and the pressure (the same arithmetic as
+// prim_core's, which keeps its own copy: inlined into the update kernel without floors,
+// a shared tail cost that kernel registers and 6% of its time).
+template <class R>
+__device__ __forceinline__ R prim_tail(const PatchDev& P, double rho, double irho, double mx, double my, double mz,
+                                       double e, double sbx, double sby, double sbz, double p,
+                                       R* __restrict__ W, long long q, bool store, bool interior) {
+  const R rirho = Ar<R>::from_d(irho);
+  const R vx = Ar<R>::mul_rn(Ar<R>::from_d(mx), rirho), vy = Ar<R>::mul_rn(Ar<R>::from_d(my), rirho),
+          vz = Ar<R>::mul_rn(Ar<R>::from_d(mz), rirho);
+  const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
+  return prim_store<R>(P, Ar<R>::from_d(rho), vx, vy, vz, bx, by, bz, Ar<R>::from_d(p), finite_d(e), W, q, store,
+                       interior);
+}
+
+// The terms of the recovery's pressure that do not depend on E (prim_core's arithmetic and
+// rounding, without the density floor): 1/rho, |m|^2/rho and 4|B_cc|^2.  A change of E alone
+// (the thermal source) recovers the new pressure from them with recovery_pressure, bit for
+// bit as prim_core would from the changed state.
+struct RecoveryTerms {
+  double irho, kin, b2;
+};
+template <class R>
+__device__ __forceinline__ RecoveryTerms recovery_terms(double rho, double mx, double my, double mz, double sbx,
+                                                        double sby, double sbz) {
+  const double irho = inv_density<R>(rho);
+  const double m2 = __fma_rn(mz, mz, __fma_rn(my, my, __dmul_rn(mx, mx)));
+  const double b2 = __fma_rn(sbz, sbz, __fma_rn(sby, sby, __dmul_rn(sbx, sbx)));
+  return {irho, __dmul_rn(m2, irho), b2};
+}
+// p = (gamma-1) (E - |m|^2/(2 rho) - |B_cc|^2/2), unclamped
+__device__ __forceinline__ double recovery_pressure(const PatchDev& P, const RecoveryTerms& t, double e) {
+  return __fma_rn(-P.egm1, t.b2, __fma_rn(-P.hgm1, t.kin, __dmul_rn(P.gm1, e)));
+}
 
 // The end-of-step floors and the recovery of the new state in one pass, sharing their FP64
 // arithmetic (floors on): with rho_f = max(rho, rho_floor), the recovery's pressure with rho_f

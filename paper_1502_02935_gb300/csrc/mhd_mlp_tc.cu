@@ -224,19 +224,38 @@ __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, The
   const float zf = (float)th.z;
   const float kLn10 = 2.302585093f;
   float lim = INFINITY;
+  const long long FS = P.FS;
   for (long long base = (long long)blockIdx.x * kTcRows; base < nc; base += (long long)gridDim.x * kTcRows) {
     const long long c = base + threadIdx.x;
     int i = 0, j = 0, k = 0;
     bool inrange = false;
     float tf = 0.f, rf = 0.f;
     float x[4] = {0.f, 0.f, 0.f, 0.f}, dl = 0.f;
+    long long cs = 0;
+    // The recovery's terms that the isochoric change of E leaves alone, computed once: the
+    // FP64 ones for T here and for the new pressure below, the bulk-type velocity and field
+    // for the new W (prim_core's arithmetic, so W is what a recovery pass would store).
+    double rho = 1.0, e0 = 0.0;
+    RecoveryTerms rt{1.0, 0.0, 0.0};
+    float vx = 0.f, vy = 0.f, vz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
     if (c < nc) {
       i = (int)(c % P.n[0]);
       const long long r = c / P.n[0];
       j = (int)(r % P.n[1]);
       k = (int)(r / P.n[1]);
-      double rho, irho;
-      const double p = th_pressure(P, P.Un, i, j, k, rho, irho);
+      cs = sidx(P, i, j, k);
+      rho = P.Un[cs];
+      const double mx = P.Un[MX * FS + cs], my = P.Un[MY * FS + cs], mz = P.Un[MZ * FS + cs];
+      e0 = P.Un[EN * FS + cs];
+      const double sbx = P.Un[BXF * FS + cs] + P.Un[BXF * FS + sidx(P, fmap(P, 0, i + 1), j, k)];
+      const double sby = P.Un[BYF * FS + cs] + P.Un[BYF * FS + sidx(P, i, fmap(P, 1, j + 1), k)];
+      const double sbz = P.Un[BZF * FS + cs] + P.Un[BZF * FS + sidx(P, i, j, fmap(P, 2, k + 1))];
+      rt = recovery_terms<float>(rho, mx, my, mz, sbx, sby, sbz);
+      const double p = recovery_pressure(P, rt, e0);
+      const double irho = rt.irho;
+      const float rirho = d2f_alu(irho);
+      vx = __fmul_rn(d2f_alu(mx), rirho), vy = __fmul_rn(d2f_alu(my), rirho), vz = __fmul_rn(d2f_alu(mz), rirho);
+      bx = d2f_alu(sbx) * 0.5f, by = d2f_alu(sby) * 0.5f, bz = d2f_alu(sbz) * 0.5f;
       // T and n_H in FP32 (integer-pipe conversions); the clamp lets a NaN through to fall back
       rf = d2f_alu(rho);
       tf = tpp * d2f_alu(p) * d2f_alu(irho);
@@ -268,8 +287,22 @@ __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, The
         const float dT = (T0 != tf || !(T1 >= 10.0f && T1 <= 1e8f))
                              ? (T1 < 10.0f ? 10.0f : (T1 > 1e8f ? 1e8f : T1)) - tf
                              : T0 * expm1f(d * kLn10);
-        P.Un[EN * P.FS + sidx(P, i, j, k)] += f2d_alu(cef * rf * dT);
-        if (Wst) lim = fminf(lim, prim_point<float>(P, P.Un, Wst, i, j, k, true, true));
+        const double e1 = e0 + f2d_alu(cef * rf * dT);
+        P.Un[EN * FS + cs] = e1;
+        if (Wst) {
+          if (P.floors && rho < P.rho_floor) {
+            // the recovery floors the density (not after the step's own floors): in full
+            lim = fminf(lim, prim_point<float>(P, P.Un, Wst, i, j, k, true, true));
+          } else {
+            double p1 = recovery_pressure(P, rt, e1);
+            if (P.floors) {
+              const double lo = rho * P.pr_floor, hi = rho * P.pr_ceil;
+              p1 = p1 < lo ? lo : (p1 > hi ? hi : p1);
+            }
+            lim = fminf(lim, prim_store<float>(P, rf, vx, vy, vz, bx, by, bz, d2f_alu(p1), finite_d(e1), Wst,
+                                               qidx(P, i, j, k), true, true));
+          }
+        }
       } else {
         fb_list[atomicAdd(fb_count, 1ull)] = (int)c;
         fb = 1;
