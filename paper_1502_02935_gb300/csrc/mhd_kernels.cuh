@@ -205,15 +205,53 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
   }
 }
 
+constexpr int kTX = 32, kTY = 8;
+constexpr int kEB = kTX * kTY;  // one thread per cell of a tile plane
+
+template <class R>
+__device__ __forceinline__ R emf_at(const PatchDev& P, const R* __restrict__ W, int c, int i, int j, int k) {
+  const long long q = qidx(P, i, j, k);
+  return c == 0 ? corner_value<R, 0>(P, W, q) : (c == 1 ? corner_value<R, 1>(P, W, q) : corner_value<R, 2>(P, W, q));
+}
+
+// asynchronous global -> shared copy of one 4- or 8-byte value (completion: cp_async_wait)
+template <class R> __device__ __forceinline__ void cp_async(R* smem, const R* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(sizeof(R)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The twelve values per cell that the edge EMFs of a plane read (the mass flux and the two
+// transverse-field fluxes of each direction, and the three cell EMFs), staged in shared
+// memory over the tile and a halo of one cell below and above it in x and y:
+// (kTY + 2) x (kTX + 2) per array, point (ii, jj) of the tile at (jj + 1) * kSW + ii + 1.
+// Rolling pairs [2] hold planes k and k + 1 of the march, the others plane k (the x and y
+// faces) or the z faces at k + 1/2.
+// Used by the FP32 update with the end-of-step floors (24.5 KB per CTA): there it is 3%
+// faster per launch on the disc than reading the inputs from global memory (2.96 against
+// 3.06 ms at 512 x 512 x 128), while without the floors it is 3% slower (1.30 against 1.26 ms
+// at 256^3).  The FP64 arrays would take a CTA past 48 KB of static shared memory.
+constexpr int kSW = kTX + 2, kSH = kTY + 2, kSP = kSW * kSH;
+template <class R, bool ON> struct EdgeStage {
+  static constexpr int N = ON ? kSP : 1;
+  R x0[2][N], x6[2][N], x5[N];  // F_x: mass (marked), B_z flux, B_y flux
+  R y0[2][N], y5[2][N], y6[N];  // F_y: mass (marked), B_z flux, B_x flux
+  R z0[N], z5[N], z6[N];        // F_z at k + 1/2: mass (marked), B_x flux, B_y flux
+  R ecx[2][N], ecy[2][N], ecz[N];
+};
+
 // Corner EMFs and the stage update in one kernel, for patches with three active axes.
-// Five resident CTAs per SM (48 registers, 72 B spilled): five is the fastest of four, five
-// and six on 128^3 and 256^3, and 32 x 8 tiles are faster than 32 x 16 at two or three CTAs
-// per SM (measured at 256^3: 1.26 ms against 1.37 at four CTAs, 1.39 and 1.69 with 32 x 16).
+// Five resident CTAs per SM (48 registers): five is the fastest of four, five and six on
+// 128^3 and 256^3, and 32 x 8 tiles are faster than 32 x 16 at two or three CTAs per SM
+// (measured at 256^3: 1.26 ms against 1.37 at four CTAs, 1.39 and 1.69 with 32 x 16).
 // A CTA owns a kTX x kTY column of cells over lz consecutive z-planes and marches up in z.
 // For plane k:
+//  (S) with the floors (FP32, see EdgeStage): the edge EMFs' inputs of plane k + 1 are
+//      copied to shared memory asynchronously while (B) and (C) run; plane k's arrived
+//      during the previous plane;
 //  (A) the edge EMFs the plane's faces need -- E_z at plane k, E_x and E_y at plane k + 1
-//      (at the first plane also at k) -- over the tile and its upper halo row and column,
-//      into shared memory;
+//      (at the first plane also at k, from global memory) -- over the tile and its upper
+//      halo row and column, into shared memory;
 //  (B) from them, the new face values -- x and y faces at plane k, z faces at k + 1 (at the
 //      first plane also at k) -- over the tile and its upper halo, into shared memory;
 //      faces of the extra layer of an outflow axis, which no cell owns, are stored here;
@@ -221,13 +259,13 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
 //      when asked, the recovery of the new state (W, cell EMFs) and its CFL limit.
 // E_x, E_y and the z faces roll between two plane buffers.  Each face is
 // computed about once (about 3.3 FP64 face updates per cell against 6 when every cell
-// recomputes its upper faces), and the edge EMFs do not go through HBM.  Edges and faces
+// recomputes its upper faces), the edge EMFs do not go through HBM, and when staged the
+// twelve edge inputs of a cell are read from global memory once instead of three times
+// (without staging the second and third reads hit L1 or L2).  Edges and faces
 // of the halo are computed by both CTAs that need them; both get the same bits
-// (corner_value and face_from are insensitive to FMA contraction).  The cell EMFs are
+// (corner_core and face_from are insensitive to FMA contraction).  The cell EMFs are
 // read from Win, the W of the stage's input, while CTAs of neighbouring tiles write the W
 // of the new state: that goes to the other buffer, Wout.
-constexpr int kTX = 32, kTY = 8;
-constexpr int kEB = kTX * kTY;  // one thread per cell of a tile plane
 constexpr int kEMinBlocks = 5;
 
 // Periodic images of the W of interior cell (i, j, k) (scratch index q) in the ghost shell
@@ -263,12 +301,6 @@ __device__ __forceinline__ void periodic_images(const PatchDev& P, R* __restrict
   }
 }
 
-template <class R>
-__device__ __forceinline__ R emf_at(const PatchDev& P, const R* __restrict__ W, int c, int i, int j, int k) {
-  const long long q = qidx(P, i, j, k);
-  return c == 0 ? corner_value<R, 0>(P, W, q) : (c == 1 ? corner_value<R, 1>(P, W, q) : corner_value<R, 2>(P, W, q));
-}
-
 template <class R, bool FLOORS>
 __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, const R* __restrict__ Win,
                                                        R* __restrict__ Wout, const double* __restrict__ Ub,
@@ -281,6 +313,8 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
   __shared__ double sBx[kTY * SX];
   __shared__ double sBy[(kTY + 1) * kTX];
   __shared__ double sBz[2][kTY * kTX];
+  constexpr bool STAGED = sizeof(R) == 4 && FLOORS;
+  __shared__ EdgeStage<R, STAGED> G;
   __shared__ R sh;
   if (threadIdx.x == 0) {
     double dt;
@@ -292,8 +326,8 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
     }
     sh = Ar<R>::from_d(a.stage == 0 ? 0.5 * dt : dt);
   }
-  __syncthreads();
-  const R h = sh;
+  // (staged: this barrier comes after the first plane's copies)
+  if constexpr (!STAGED) __syncthreads();
   const int ntx = (P.n[0] + kTX - 1) / kTX;
   const int i0 = (int)(blockIdx.x % ntx) * kTX, j0 = (int)(blockIdx.x / ntx) * kTY;
   const int kz0 = (int)blockIdx.y * lz;
@@ -303,10 +337,69 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
   const bool own = ti < ni && tj < nj;
   const R ix = Gam<R>::inv(P, 0), iy = Gam<R>::inv(P, 1), iz = Gam<R>::inv(P, 2);
   const long long FS = P.FS, QX = P.QX, PX = P.PX;
+  const long long QS = P.QS, QP = (long long)P.QX * P.QY;
+  const R* __restrict__ Fx = (const R*)P.F[0];
+  const R* __restrict__ Fy = (const R*)P.F[1];
+  const R* __restrict__ Fz = (const R*)P.F[2];
+  // (S) for plane kk: the x and y faces and cell E_z at kk, the rolling arrays at kk + 1
+  // into buffer nb (and at kk into the other buffer when first), the z faces at kk + 1/2.
+  // The points of the (ni + 2) x (nj + 2) box lie in the scratch arrays' padding of 2.
+  auto stage = [&](int kk, int nb, bool first) {
+    const int w = ni + 2, npts = w * (nj + 2);
+    for (int t = (int)threadIdx.x; t < npts; t += kEB) {
+      const int jj = t / w - 1, ii = t - (jj + 1) * w - 1;
+      const int o = (jj + 1) * kSW + ii + 1;
+      const long long q0 = qidx(P, i0 + ii, j0 + jj, kk), q1 = q0 + QP;
+      cp_async(&G.x5[o], Fx + 5 * QS + q0);
+      cp_async(&G.y6[o], Fy + 6 * QS + q0);
+      cp_async(&G.ecz[o], Win + WEZ * QS + q0);
+      cp_async(&G.x0[nb][o], Fx + q1);
+      cp_async(&G.x6[nb][o], Fx + 6 * QS + q1);
+      cp_async(&G.y0[nb][o], Fy + q1);
+      cp_async(&G.y5[nb][o], Fy + 5 * QS + q1);
+      cp_async(&G.ecx[nb][o], Win + WEX * QS + q1);
+      cp_async(&G.ecy[nb][o], Win + WEY * QS + q1);
+      cp_async(&G.z0[o], Fz + q1);
+      cp_async(&G.z5[o], Fz + 5 * QS + q1);
+      cp_async(&G.z6[o], Fz + 6 * QS + q1);
+      if (first) {
+        const int ob = nb ^ 1;
+        cp_async(&G.x0[ob][o], Fx + q0);
+        cp_async(&G.x6[ob][o], Fx + 6 * QS + q0);
+        cp_async(&G.y0[ob][o], Fy + q0);
+        cp_async(&G.y5[ob][o], Fy + 5 * QS + q0);
+        cp_async(&G.ecx[ob][o], Win + WEX * QS + q0);
+        cp_async(&G.ecy[ob][o], Win + WEY * QS + q0);
+      }
+    }
+  };
+  if constexpr (STAGED) {
+    stage(kz0, 1, true);
+    cp_async_wait();
+    __syncthreads();
+  }
+  const R h = sh;
   const bool last = a.stage == 1;
   R lim = R(INFINITY);
   int nfl = 0;
-  // edge EMF c at tile offset (ii, jj) of plane kk into its shared array
+  // edge EMFs at tile offset (ii, jj) from the staged inputs (corner_core's arguments as
+  // corner_value takes them from global memory): E_z at plane k, E_x and E_y at k + 1/2
+  auto ez_at = [&](int ii, int jj, int cur) {
+    const int o = (jj + 1) * kSW + ii + 1;
+    return corner_core<R>(-G.x5[o], -G.x5[o - kSW], G.y6[o], G.y6[o - 1], G.ecz[o], G.ecz[o - 1], G.ecz[o - kSW],
+                          G.ecz[o - kSW - 1], G.x0[cur][o], G.x0[cur][o - kSW], G.y0[cur][o], G.y0[cur][o - 1]);
+  };
+  auto ex_at = [&](int ii, int jj, int cur) {
+    const int o = (jj + 1) * kSW + ii + 1, nx = cur ^ 1;
+    return corner_core<R>(-G.y5[nx][o], -G.y5[cur][o], G.z6[o], G.z6[o - kSW], G.ecx[nx][o], G.ecx[nx][o - kSW],
+                          G.ecx[cur][o], G.ecx[cur][o - kSW], G.y0[nx][o], G.y0[cur][o], G.z0[o], G.z0[o - kSW]);
+  };
+  auto ey_at = [&](int ii, int jj, int cur) {
+    const int o = (jj + 1) * kSW + ii + 1, nx = cur ^ 1;
+    return corner_core<R>(-G.z5[o], -G.z5[o - 1], G.x6[nx][o], G.x6[cur][o], G.ecy[nx][o], G.ecy[cur][o],
+                          G.ecy[nx][o - 1], G.ecy[cur][o - 1], G.z0[o], G.z0[o - 1], G.x0[nx][o], G.x0[cur][o]);
+  };
+  // unstaged: edge EMF c at tile offset (ii, jj) of plane kk into its shared array
   auto put_e = [&](int c, int ii, int jj, int kk, int buf) {
     const R e = emf_at<R>(P, Win, c, i0 + ii, j0 + jj, kk);
     if (c == 2) sEz[jj * SX + ii] = e;
@@ -319,16 +412,38 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
     // (A) edge EMFs.  Each thread: E_z(k), E_x(k+1), E_y(k+1) at its own (ti, tj) (and
     // E_x(k), E_y(k) at the first plane); warps 0-2 (3-4 at the first plane) add the
     // upper halo row (jj = nj) and column (ii = ni).
-    if (own) {
-      put_e(2, ti, tj, k, 0);
-      put_e(0, ti, tj, k + 1, nxt);
-      put_e(1, ti, tj, k + 1, nxt);
-      if (first) {
-        put_e(0, ti, tj, k, cur);
-        put_e(1, ti, tj, k, cur);
+    if constexpr (STAGED) {
+      if (own) {
+        sEz[tj * SX + ti] = ez_at(ti, tj, cur);
+        sEx[nxt][tj * kTX + ti] = ex_at(ti, tj, cur);
+        sEy[nxt][tj * SX + ti] = ey_at(ti, tj, cur);
+        if (first) {
+          sEx[cur][tj * kTX + ti] = emf_at<R>(P, Win, 0, i0 + ti, j0 + tj, k);
+          sEy[cur][tj * SX + ti] = emf_at<R>(P, Win, 1, i0 + ti, j0 + tj, k);
+        }
       }
-    }
-    {
+      const int w = tj, l = ti;
+      if (w == 0 && l < ni) sEz[nj * SX + l] = ez_at(l, nj, cur);
+      if (w == 1 && l < ni) sEx[nxt][nj * kTX + l] = ex_at(l, nj, cur);
+      if (w == 2) {
+        if (l <= nj) sEz[l * SX + ni] = ez_at(ni, l, cur);
+        else if (l >= 16 && l - 16 < nj) sEy[nxt][(l - 16) * SX + ni] = ey_at(ni, l - 16, cur);
+      }
+      if (first) {
+        if (w == 3 && l < ni) sEx[cur][nj * kTX + l] = emf_at<R>(P, Win, 0, i0 + l, j0 + nj, k);
+        if (w == 4 && l < nj) sEy[cur][l * SX + ni] = emf_at<R>(P, Win, 1, i0 + ni, j0 + l, k);
+      }
+    } else {
+      // the same edges from global memory (corner_value)
+      if (own) {
+        put_e(2, ti, tj, k, 0);
+        put_e(0, ti, tj, k + 1, nxt);
+        put_e(1, ti, tj, k + 1, nxt);
+        if (first) {
+          put_e(0, ti, tj, k, cur);
+          put_e(1, ti, tj, k, cur);
+        }
+      }
       const int w = tj, l = ti;
       if (w == 0 && l < ni) put_e(2, l, nj, k, 0);
       if (w == 1 && l < ni) put_e(0, l, nj, k + 1, nxt);
@@ -342,6 +457,10 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
       }
     }
     __syncthreads();
+    // (S) the next plane's edge inputs, in flight during (B) and (C): its rolling arrays go
+    // to buffer cur, whose plane k (A) has just read
+    if constexpr (STAGED)
+      if (k + 1 < kz1) stage(k + 1, cur, false);
     // (B) new faces.  Each thread: the x and y faces of its cell at plane k and the z face
     // above it (and the z face below it at the first plane); warps 0-1 add the halo x-face
     // column (ii = ni) and y-face row (jj = nj).
@@ -415,7 +534,14 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
       lim = l < lim ? l : lim;
       if (images) periodic_images<R>(P, Wout, i0 + ti, j0 + tj, k, q);
     }
-    // C(k) and A(k + 1) touch different shared arrays and share one barrier interval
+    if constexpr (STAGED) {
+      // the next plane's edge inputs have landed (each thread waits for its own copies; the
+      // barrier makes all of them visible)
+      cp_async_wait();
+      __syncthreads();
+    }
+    // (unstaged: C(k) and A(k + 1) touch different shared arrays and share one barrier
+    // interval)
   }
   if (a.stage == 1) {
     if (P.floors) {

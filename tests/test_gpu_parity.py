@@ -387,11 +387,15 @@ def test_floors_parity_disc():
     assert counts[1] > 0 and abs(counts[0] - counts[1]) <= 0.05 * counts[1] + 2, counts
 
 
-def test_floors_off_leave_the_step_unchanged():
-    """Floors that no cell reaches leave the device step bit for bit as without them."""
-    st = inputs.turbulence((20, 16, 12), seed=7)
-    a = mhd.Grid(st, precision="fp64", cfl=0.4)
-    b = mhd.Grid(st, precision="fp64", cfl=0.4)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_floors_off_leave_the_step_unchanged(precision):
+    """Floors that no cell reaches leave the device step bit for bit as without them.  On the
+    mixed path the update kernel with floors stages the edge EMFs' inputs in shared memory
+    and the one without reads them from global memory: the same bits over ragged tiles
+    (40 x 20 cells: x tiles of 32 and 8, y tiles of 8, 8 and 4) and several planes."""
+    st = inputs.turbulence((40, 20, 12), seed=7)
+    a = mhd.Grid(st, precision=precision, cfl=0.4)
+    b = mhd.Grid(st, precision=precision, cfl=0.4)
     b.set_sources(rho_floor=1e-12, pr_floor=1e-12, pr_ceil=1e12)
     for _ in range(3):
         a.step(-1.0)
