@@ -161,12 +161,15 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* src);
  * all three.  MHD_ERR_ARG for another value. */
 int mhd_set_riemann(mhd_ctx* ctx, int solver);
 
-/* Which kernel computes the fluxes through y and z faces (the same fluxes, Eq. 3 with the
- * interface states of Eq. 12-14; a choice of schedule): MHD_FLUX_MARCH, threads marching
+/* Which kernels compute the fluxes (the same fluxes, Eq. 3 with the interface states of
+ * Eq. 12-14; a choice of schedule).  MHD_FLUX_MARCH: through y and z faces, threads marching
  * along the flux direction over segments of 16 faces (8, 4 or 2 on thinner boxes), each cell
- * loaded and reconstructed once; MHD_FLUX_PER_FACE, one thread per face; MHD_FLUX_AUTO (the
- * default), marching where the box gives at least two waves of threads, per face on thinner
- * ones (2D planes, small patches).  x faces are always per face.  Drops captured graphs. */
+ * loaded and reconstructed once; through x faces of the kappa-scheme stage, warps of 32
+ * consecutive cells that pass each cell's upper-face value to the next lane by a shuffle.
+ * MHD_FLUX_PER_FACE: one thread per face in every direction.  MHD_FLUX_AUTO (the default): as
+ * MARCH, except that y and z go per face where the box gives fewer than two waves of marching
+ * threads (2D planes, small patches).  The donor-cell stage's x faces are always per face.
+ * Drops captured graphs. */
 enum { MHD_FLUX_AUTO = 0, MHD_FLUX_MARCH = 1, MHD_FLUX_PER_FACE = 2 };
 int mhd_set_flux_scheme(mhd_ctx* ctx, int scheme);
 

@@ -161,6 +161,64 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ORDER == 1 ? 4 : 3) 
   }
 }
 
+// kappa-scheme fluxes through the x faces with each cell reconstructed once: a warp takes 32
+// consecutive cells of the scratch rows of one plane of the flux range (rows run on through
+// their padding, so a warp may span two rows).  Each lane reconstructs its cell's values at
+// its lower and upper faces (w - K1 m2 - K2 m1 and w + K1 m1 + K2 m2, the expressions of
+// kappa_face), and the face below lane l takes lane l - 1's upper value by a shuffle.  Windows
+// overlap by one cell (lane 0 only passes its value on), so a warp computes 31 faces; faces in
+// the x padding are computed and not stored.  Loads are clamped into the arrays (lanes past
+// the last row read stored values and store nothing).  Measured at 256^3: 0.345 ms per launch
+// against 0.362 for the per-face kernel (512 x 512 x 128: 0.566 against 0.609); the same
+// scheme for the donor-cell stage, which has no reconstruction to share, was slower than its
+// per-face kernel (0.302 against 0.284 ms), as was this kernel at four CTAs per SM (0.375 ms).
+template <class R, int S>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 1) k_flux_xs(PatchDev P,
+                                                                          const double* __restrict__ Ub,
+                                                                          Range rg, unsigned nwin) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned win = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+  if (win >= nwin) return;  // whole warps
+  const int k = rg.lo[2] + (int)blockIdx.y;
+  const long long QS = P.QS;
+  const long long q0 = qidx(P, -2, rg.lo[1], k);    // first cell of the plane's rows
+  const long long len = (long long)rg.ext[1] * P.QX;  // cells of those rows
+  const long long off = 31LL * win - 1 + lane;        // this lane's cell, from q0
+  const long long q = q0 + off;
+  const long long ql = q < 1 ? 1 : (q > QS - 2 ? QS - 2 : q);
+  const R* __restrict__ W = (const R*)P.W;
+  constexpr int comp[7] = {WR, WVX, WVY, WVZ, WP, WBY, WBZ};
+  R K1, K2, kb;
+  Gam<R>::kappa(P, K1, K2, kb);
+  R wl[7], wr[7];
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    const R* Wm = W + comp[m] * QS;
+    const R a = Wm[ql - 1], c = Wm[ql], e = Wm[ql + 1];
+    const R dl = c - a, dr = e - c;
+    const R m1 = minmod<R>(dl, kb * dr), m2 = minmod<R>(dr, kb * dl);
+    const R up = c + K1 * m1 + K2 * m2;
+    wr[m] = c - K1 * m2 - K2 * m1;
+    wl[m] = __shfl_up_sync(0xffffffffu, up, 1);
+  }
+  // the face below this lane's cell: stored when its cell is a flux-range face
+  if (lane == 0 || off < 0 || off >= len) return;
+  const unsigned row = (unsigned)off / (unsigned)P.QX;
+  const int i = (int)((unsigned)off - row * (unsigned)P.QX) - 2;
+  if (i < 0 || i > P.n[0]) return;
+  if (!(wl[0] > R(0)) || !(wr[0] > R(0)) || !(wl[4] > R(0)) || !(wr[4] > R(0))) {
+    // a face whose reconstructed rho or p is not positive takes the donor-cell states
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      wl[m] = W[comp[m] * QS + q - 1];
+      wr[m] = W[comp[m] * QS + q];
+    }
+  }
+  R out[8];
+  riemann<R>(S, wl, wr, face_bn<R, 0>(P, Ub, i, rg.lo[1] + (int)row, k), Gam<R>::get(P), out);
+  store_flux<R, 0>((R*)P.F[0], QS, q, out);
+}
+
 // corner EMFs: memory-latency bound; eight resident blocks per SM (measured)
 template <class R>
 __global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
@@ -687,6 +745,19 @@ static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cu
       if (P.riemann == RIEMANN_HLLC) k_flux_march<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
       else if (P.riemann == RIEMANN_HLL) k_flux_march<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
       else k_flux_march<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
+      return;
+    }
+  }
+  if constexpr (D == 0 && ORDER == 2) {
+    // kappa-scheme x faces: the shuffle kernel (each cell reconstructed once), unless the
+    // per-face kernel is asked for
+    if (P.flux_scheme != FLUX_PER_FACE) {
+      const long long len = (long long)fr.ext[1] * P.QX;
+      const unsigned nwin = (unsigned)((len + 30) / 31);  // window w: the faces below cells 31w .. 31w + 30
+      const dim3 g((nwin + kBlock / 32 - 1) / (kBlock / 32), (unsigned)fr.ext[2], 1);
+      if (P.riemann == RIEMANN_HLLC) k_flux_xs<R, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr, nwin);
+      else if (P.riemann == RIEMANN_HLL) k_flux_xs<R, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr, nwin);
+      else k_flux_xs<R, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr, nwin);
       return;
     }
   }
