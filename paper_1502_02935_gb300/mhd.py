@@ -422,7 +422,8 @@ def cfl_dt_noalloc(geom: Geom, cfl: float, U_ptr: int, B_ptr: int, dt_ptr: int, 
 def thermal_cells(T0, nh, ce, dt, th: dict):
     """Plain FP64 thermal integrator on the GPU for independent cells; returns (T, status)."""
     import torch
-    arr = [torch.as_tensor(np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), np.shape(T0)))).cuda()
+    # (a broadcast view is read-only: copy it into a writable array first)
+    arr = [torch.from_numpy(np.array(np.broadcast_to(np.asarray(a, dtype=np.float64), np.shape(T0)))).cuda()
            for a in (T0, nh, ce, dt)]
     out = torch.empty_like(arr[0])
     st = torch.zeros(arr[0].shape, dtype=torch.int32, device="cuda")
