@@ -34,10 +34,21 @@ struct ProfScope {
   }
 };
 
+// Two side streams and their events for one issuing stream: a stage issues the y and z flux
+// kernels on the side streams, beside the x kernel on its own stream, and joins them before
+// the update (in a captured graph: three parallel branches).
+struct ForkSet {
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[2] = {nullptr, nullptr};
+};
+
 struct Backend {
   size_t scratch_elem;  // bytes per scratch value (8 for FP64, 4 for the mixed path)
   // one stage (0 predictor, 1 corrector) of a van Leer step of one patch; both write Uh
-  int (*stage)(const PatchDev&, const StageArgs&, cudaStream_t, long long* launches, ProfRec* prof);
+  // (fk: side streams for the flux kernels, or null to issue everything on the stream)
+  int (*stage)(const PatchDev&, const StageArgs&, cudaStream_t, long long* launches, ProfRec* prof,
+               const ForkSet* fk);
   // W and CFL limit of the current state Un (the recovery that starts a step)
   int (*prim)(const PatchDev&, cudaStream_t, long long* launches, ProfRec* prof);
   // CFL limit of the current state into the patch's cfl_min slot

@@ -767,13 +767,27 @@ static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cu
   else k_flux<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr);
 }
 
-// per-direction flux kernels of one stage, and the corner-EMF kernel when asked
+// per-direction flux kernels of one stage, and the corner-EMF kernel when asked.  With a
+// fork set (and no per-class profiling, whose events time one stream) the directions after
+// the first active one run on the side streams, in parallel with it: each kernel fills the
+// GPU, and the overlap fills the others' last partial waves (256^3: 4.299 -> 4.267 ms per
+// step on the same box).
 template <class R>
-static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s, ProfRec* prof,
-                        bool emf) {
+static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s0, ProfRec* prof,
+                        bool emf, const ForkSet* fk) {
   int nl = 0;
+  const bool par = fk && !prof && P.act[0] + P.act[1] + P.act[2] >= 2;
+  if (par) {
+    if (cudaEventRecord(fk->fork, s0) != cudaSuccess) return -1;
+    for (int q = 0; q < 2; ++q)
+      if (cudaStreamWaitEvent(fk->side[q], fk->fork, 0) != cudaSuccess) return -1;
+  }
+  int side = 0;
+  bool first = true;
   for (int d = 0; d < 3; ++d) {
     if (!P.act[d]) continue;
+    const cudaStream_t s = (par && !first) ? fk->side[side++] : s0;
+    first = false;
     const Range fr = flux_range(P, d);
     ProfScope ps(prof, (a.stage == 0 ? KC_FLUX1 : KC_FLUX2) + d, s);
     if (a.stage == 0) {
@@ -787,10 +801,16 @@ static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usr
     }
     ++nl;
   }
+  if (par) {
+    for (int q = 0; q < side; ++q)
+      if (cudaEventRecord(fk->join[q], fk->side[q]) != cudaSuccess ||
+          cudaStreamWaitEvent(s0, fk->join[q], 0) != cudaSuccess)
+        return -1;
+  }
   if (!emf) return nl;
   const Range er = edge_range(P);
-  ProfScope ps(prof, KC_EMF, s);
-  k_emf<R><<<grid_of(er), kBlock, 0, s>>>(P, er);
+  ProfScope ps(prof, KC_EMF, s0);
+  k_emf<R><<<grid_of(er), kBlock, 0, s0>>>(P, er);
   return nl + 1;
 }
 
@@ -806,7 +826,7 @@ static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usr
 // every step.  Other patches use the corner-EMF kernel and the fused update, in place.
 template <class R>
 static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, long long* launches,
-                       ProfRec* prof) {
+                       ProfRec* prof, const ForkSet* fk) {
   const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
   const bool fused = P.act[0] && P.act[1] && P.act[2] && P.W2;
   // all axes periodic: the fused kernel writes W's ghost images itself
@@ -817,7 +837,8 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     Q.W = a.stage == 0 ? P.W : P.W2;
     G.W = a.stage == 0 ? P.W2 : P.W;
   }
-  int nl = issue_fluxes<R>(Q, a, Usrc, s, prof, !fused);
+  int nl = issue_fluxes<R>(Q, a, Usrc, s, prof, !fused, fk);
+  if (nl < 0) return -1;
   if (P.ns > 0) {
     // passive scalars, before the update overwrites the corrector's input state in Uh
     ProfScope ps(prof, KC_SCALARS, s);
