@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 1) k_flux(PatchDe
 // m1 = minmod(dl, b dr), m2 = minmod(dr, b dl) give its value at the upper face,
 // w + K1 m1 + K2 m2 (w_L there), and at the lower face, w - K1 m2 - K2 m1 (w_R there) -- the
 // expressions of kappa_face, where the per-face kernel evaluates both neighbours of every face.
-// The donor-cell stage carries the previous cell.  Results equal those of flux_point.
+// The donor-cell stage carries the previous cell.  The arithmetic is flux_point's (the
+// compiler may contract its multiply-adds differently, so the bits can differ in the last
+// place).
 // Segments of seg faces (16 where the box gives enough columns, fewer on thinner boxes, see
 // launch_flux); FP32 kernels at four (donor cell) and three (kappa-scheme) resident CTAs per
 // SM: the fastest of 8, 16, 32, 64 faces and three or four CTAs at 256^3 (the kappa kernels
