@@ -54,6 +54,8 @@ KCLASS = {
     "flux1_x": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
     "flux1_y": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
     "flux1_z": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
+    # the three donor-cell directions in one kernel (three active axes): per face
+    "flux1_xyz": dict(fp64=0, fp32=343, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
     "flux2_x": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
     "flux2_y": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
     "flux2_z": dict(fp64=0, fp32=553, bytes=7 * 4 + 8 + 7 * 4, unit="face"),
@@ -88,6 +90,8 @@ def units_per_launch(cls: str, n: int) -> int:
         return (n + 4) ** 3
     if cls == "ghost":
         return (n + 4) ** 3 - n ** 3
+    if cls == "flux1_xyz":
+        return 3 * (n + 1) * (n + 2) * (n + 2)
     if cls.startswith("flux"):
         return (n + 1) * (n + 2) * (n + 2)
     if cls == "emf_update":

@@ -165,11 +165,12 @@ int mhd_set_riemann(mhd_ctx* ctx, int solver);
  * Eq. 12-14; a choice of schedule).  MHD_FLUX_MARCH: through y and z faces, threads marching
  * along the flux direction over segments of 16 faces (8, 4 or 2 on thinner boxes), each cell
  * loaded and reconstructed once; through x faces of the kappa-scheme stage, warps of 32
- * consecutive cells that pass each cell's upper-face value to the next lane by a shuffle.
- * MHD_FLUX_PER_FACE: one thread per face in every direction.  MHD_FLUX_AUTO (the default): as
- * MARCH, except that y and z go per face where the box gives fewer than two waves of marching
- * threads (2D planes, small patches).  The donor-cell stage's x faces are always per face.
- * Drops captured graphs. */
+ * consecutive cells that pass each cell's upper-face value to the next lane by a shuffle;
+ * the donor-cell stage's x faces one thread per face.  MHD_FLUX_PER_FACE: one thread per face
+ * in every direction.  MHD_FLUX_AUTO (the default): as MARCH, except that y and z go per face
+ * where the box gives fewer than two waves of marching threads (2D planes, small patches),
+ * and that on patches with three active axes and enough columns the donor-cell stage
+ * computes all three directions in one kernel marching in z.  Drops captured graphs. */
 enum { MHD_FLUX_AUTO = 0, MHD_FLUX_MARCH = 1, MHD_FLUX_PER_FACE = 2 };
 int mhd_set_flux_scheme(mhd_ctx* ctx, int scheme);
 
@@ -311,7 +312,7 @@ int mhd_surrogate_fallback_cells(mhd_ctx* ctx, int* cells_out, long long max_cel
 int mhd_set_profiling(mhd_ctx* ctx, int on);
 
 /* Totals since profiling was switched on: ms[c] milliseconds and launches[c] launches of
- * class c, for c < n (n >= 16).  Synchronises. */
+ * class c, for c < n (n >= 17).  Synchronises. */
 int mhd_get_profile(mhd_ctx* ctx, double* ms, long long* launches, int n);
 
 /* Autotuner of the batched step (context made with MHD_FLAG_PERSISTENT; a schedule, not part

@@ -10,7 +10,8 @@ struct PersistentArgs;
 
 // Optional per-launch CUDA-event pairs recorded on the launching stream.
 enum { KC_PRIM = 0, KC_FLUX1 = 1, KC_FLUX2 = 4, KC_EMF = 7, KC_UPDATE = 8, KC_CFL = 9, KC_PERSISTENT = 10,
-       KC_THERMAL = 11, KC_FLOOR = 12, KC_GHOST = 13, KC_EMF_UPDATE = 14, KC_SCALARS = 15, KC_COUNT = 16 };
+       KC_THERMAL = 11, KC_FLOOR = 12, KC_GHOST = 13, KC_EMF_UPDATE = 14, KC_SCALARS = 15, KC_FLUX1_XYZ = 16,
+       KC_COUNT = 17 };
 struct ProfRec {
   static constexpr int kMax = 64;
   cudaEvent_t a[kMax], b[kMax];

@@ -221,6 +221,75 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 1) k_flux_xs(Patc
   store_flux<R, 0>((R*)P.F[0], QS, q, out);
 }
 
+// Donor-cell fluxes of the predictor through the faces of all three directions in one
+// kernel, for patches with three active axes: a thread takes one (x, y) column of
+// [-1, n0] x [-1, n1] and a segment of seg planes of [-1, n2], marching up in z.  At each cell c
+// it loads W(c) once and computes the x face between c - x and c, the y face between c - y and
+// c, and the z face between c - z (carried from the previous plane) and c: 22 loads per cell
+// for three faces, where the three separate kernels take 28 (the per-face x kernel loads both
+// of its cells).  Each (i, j, k) computes exactly the faces the three flux ranges hold there.
+// Measured at 256^3: step 4.266 -> 4.210 ms (disc 512 x 512 x 128: 9.24 -> 9.10 ms).
+template <class R, int S>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_flux_d3(PatchDev P, const double* __restrict__ Ub,
+                                                                          int seg) {
+  const unsigned ex = (unsigned)P.n[0] + 2u, ey = (unsigned)P.n[1] + 2u;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ex * ey) return;
+  const unsigned qy = r / ex;
+  const int i = -1 + (int)(r - qy * ex), j = -1 + (int)qy;
+  const int k0 = -1 + (int)blockIdx.y * seg;
+  const int k1 = min(k0 + seg, P.n[2] + 1);
+  const R* __restrict__ W = (const R*)P.W;
+  const long long QS = P.QS, QX = P.QX, QP = (long long)P.QX * P.QY;
+  const R gam = Gam<R>::get(P);
+  long long q = qidx(P, i, j, k0);
+  R wz[8];  // W of the cell below
+#pragma unroll
+  for (int m = 0; m < 8; ++m) wz[m] = W[m * QS + q - QP];
+  R out[8];
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k, q += QP) {
+    R w[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) w[m] = W[m * QS + q];
+    if (i >= 0) {  // x face: [rho, vx, vy, vz, p, By, Bz]
+      R wl[7], wr[7];
+      const int cp[7] = {WR, WVX, WVY, WVZ, WP, WBY, WBZ};
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        wl[m] = W[cp[m] * QS + q - 1];
+        wr[m] = w[cp[m]];
+      }
+      riemann<R>(S, wl, wr, face_bn<R, 0>(P, Ub, i, j, k), gam, out);
+      store_flux<R, 0>((R*)P.F[0], QS, q, out);
+    }
+    if (j >= 0) {  // y face: [rho, vy, vz, vx, p, Bz, Bx]
+      R wl[7], wr[7];
+      const int cp[7] = {WR, WVY, WVZ, WVX, WP, WBZ, WBX};
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        wl[m] = W[cp[m] * QS + q - QX];
+        wr[m] = w[cp[m]];
+      }
+      riemann<R>(S, wl, wr, face_bn<R, 1>(P, Ub, i, j, k), gam, out);
+      store_flux<R, 1>((R*)P.F[1], QS, q, out);
+    }
+    if (k >= 0) {  // z face: [rho, vz, vx, vy, p, Bx, By]
+      R wl[7], wr[7];
+      const int cp[7] = {WR, WVZ, WVX, WVY, WP, WBX, WBY};
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        wl[m] = wz[cp[m]];
+        wr[m] = w[cp[m]];
+      }
+      riemann<R>(S, wl, wr, face_bn<R, 2>(P, Ub, i, j, k), gam, out);
+      store_flux<R, 2>((R*)P.F[2], QS, q, out);
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) wz[m] = w[m];
+  }
+}
+
 // corner EMFs: memory-latency bound; eight resident blocks per SM (measured)
 template <class R>
 __global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
@@ -777,6 +846,23 @@ static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cu
 template <class R>
 static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s0, ProfRec* prof,
                         bool emf, const ForkSet* fk) {
+  if (a.stage == 0 && P.act[0] && P.act[1] && P.act[2] && P.flux_scheme == FLUX_AUTO) {
+    // the predictor's three directions in one marching kernel: segments of 16 planes, 8, 4 or
+    // 2 while the box gives fewer than two waves of four resident CTAs per SM; thinner boxes
+    // keep the per-direction kernels
+    const long long cols = (long long)(P.n[0] + 2) * (P.n[1] + 2), planes = P.n[2] + 2;
+    const long long want = 2LL * 4 * kBlock * sm_count();
+    int seg = kMarch;
+    while (seg > 2 && cols * ((planes + seg - 1) / seg) < want) seg >>= 1;
+    if (cols * ((planes + seg - 1) / seg) >= want) {
+      ProfScope ps(prof, KC_FLUX1_XYZ, s0);
+      const dim3 g((unsigned)((cols + kBlock - 1) / kBlock), (unsigned)((planes + seg - 1) / seg), 1);
+      if (P.riemann == RIEMANN_HLLC) k_flux_d3<R, RIEMANN_HLLC><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
+      else if (P.riemann == RIEMANN_HLL) k_flux_d3<R, RIEMANN_HLL><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
+      else k_flux_d3<R, RIEMANN_HLLD><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
+      return 1;
+    }
+  }
   int nl = 0;
   const bool par = fk && !prof && P.act[0] + P.act[1] + P.act[2] >= 2;
   if (par) {

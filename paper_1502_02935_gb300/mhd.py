@@ -283,7 +283,8 @@ class Grid:
                 "floored": int(m.floored)}
 
     KERNEL_CLASSES = ["recovery", "flux1_x", "flux1_y", "flux1_z", "flux2_x", "flux2_y", "flux2_z",
-                      "emf", "update", "cfl", "persistent", "thermal", "floor", "ghost", "emf_update", "scalars"]
+                      "emf", "update", "cfl", "persistent", "thermal", "floor", "ghost", "emf_update", "scalars",
+                      "flux1_xyz"]
 
     def set_thermal(self, mode, gamma_heat=2e-26, z=0.02, rate_unit=7.13e-31, cap=0.1, nh_per_rho=0.76,
                     t_per_pr=72.7):
