@@ -41,6 +41,10 @@ struct PatchHost {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// FP32 copy of a floor parameter for the device's conservative pre-checks: the nearest float
+// (a bound the pre-check cannot use, below the normal range, makes it defer to FP64)
+float d2f_host(double x) { return (float)x; }
+
 // kappa-scheme coefficients of Eq. 13-14 and their FP32 copies
 void set_kappa(PatchDev& D, double kappa) {
   D.rK1 = (1.0 - kappa) / 4.0;
@@ -738,6 +742,8 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
     D.floors = 0;
     D.rho_floor = D.pr_floor = 0.0;
     D.pr_ceil = INFINITY;
+    D.rho_floor_f = D.pr_floor_f = 0.0f;
+    D.pr_ceil_f = INFINITY;
     D.floored = ctx->floored;
   }
   if (cudaMalloc(&ctx->staging, sizeof(double) * (size_t)max_dense) != cudaSuccess)
@@ -783,6 +789,9 @@ int mhd_set_sources(mhd_ctx* ctx, const mhd_source_desc* s) {
     p.dev.rho_floor = s->rho_floor > 0.0 ? s->rho_floor : 0.0;
     p.dev.pr_floor = s->rho_floor > 0.0 && s->pr_floor > 0.0 ? s->pr_floor : 0.0;
     p.dev.pr_ceil = s->rho_floor > 0.0 && s->pr_ceil > 0.0 ? s->pr_ceil : INFINITY;
+    p.dev.rho_floor_f = d2f_host(p.dev.rho_floor);
+    p.dev.pr_floor_f = d2f_host(p.dev.pr_floor);
+    p.dev.pr_ceil_f = d2f_host(p.dev.pr_ceil);
   }
   if (ctx->dP && build_tables(ctx, ctx->TX, ctx->TY, ctx->occ)) return MHD_ERR_CUDA;
   drop_graph(ctx);  // sources are baked into captured launches

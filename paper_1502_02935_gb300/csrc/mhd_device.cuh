@@ -60,6 +60,7 @@ struct PatchDev {
   // floors (off unless floors != 0): rho >= rho_floor, rho pr_floor <= p <= rho pr_ceil
   int floors;
   double rho_floor, pr_floor, pr_ceil;
+  float rho_floor_f, pr_floor_f, pr_ceil_f;  // FP32 copies for the conservative pre-checks
   unsigned long long* floored;  // count of cells changed by the end-of-step floors
   int riemann;                  // RIEMANN_*
   int flux_scheme;              // FLUX_* (host side: which kernel computes the y and z fluxes)
@@ -727,16 +728,29 @@ __device__ __forceinline__ R prim_store(const PatchDev& P, R rr, R vx, R vy, R v
 // from the recovered density, its reciprocal and the pressure (the same arithmetic as
 // prim_core's, which keeps its own copy: inlined into the update kernel without floors,
 // a shared tail cost that kernel registers and 6% of its time).
+// (rr, pr: the density and pressure already in the bulk type)
 template <class R>
-__device__ __forceinline__ R prim_tail(const PatchDev& P, double rho, double irho, double mx, double my, double mz,
-                                       double e, double sbx, double sby, double sbz, double p,
+__device__ __forceinline__ R prim_tail(const PatchDev& P, R rr, double irho, double mx, double my, double mz,
+                                       double e, double sbx, double sby, double sbz, R pr,
                                        R* __restrict__ W, long long q, bool store, bool interior) {
   const R rirho = Ar<R>::from_d(irho);
   const R vx = Ar<R>::mul_rn(Ar<R>::from_d(mx), rirho), vy = Ar<R>::mul_rn(Ar<R>::from_d(my), rirho),
           vz = Ar<R>::mul_rn(Ar<R>::from_d(mz), rirho);
   const R bx = Ar<R>::from_d(sbx) * R(0.5), by = Ar<R>::from_d(sby) * R(0.5), bz = Ar<R>::from_d(sbz) * R(0.5);
-  return prim_store<R>(P, Ar<R>::from_d(rho), vx, vy, vz, bx, by, bz, Ar<R>::from_d(p), finite_d(e), W, q, store,
-                       interior);
+  return prim_store<R>(P, rr, vx, vy, vz, bx, by, bz, pr, finite_d(e), W, q, store, interior);
+}
+
+// Conservative FP32 pre-checks of the floors (FP32 copies x = d2f_alu of the FP64 values):
+// true only when the FP64 value certainly lies strictly inside the bound, so that the FP64
+// comparison (and its clamp) can be skipped with the same result.  The margin 2^-20 exceeds
+// the relative error of the roundings involved (at most 4 x 2^-24); NaN, zero and values
+// that d2f_alu flushes fail the check and take the FP64 path.
+constexpr float kFloorMargin = 1.0f + 1.0f / 1048576.0f;
+__device__ __forceinline__ bool surely_above(float x, float bound_f) {
+  return bound_f >= 1.17549435e-38f && x > bound_f * kFloorMargin;
+}
+__device__ __forceinline__ bool surely_inside(float x, float lo_f, float hi_f) {
+  return surely_above(x, lo_f) && x < hi_f * (2.0f - kFloorMargin);
 }
 
 // The terms of the recovery's pressure that do not depend on E (prim_core's arithmetic and
@@ -769,14 +783,20 @@ template <class R>
 __device__ __forceinline__ R floor_prim_core(const PatchDev& P, double& rho, double mx, double my, double mz,
                                              double& e, double sbx, double sby, double sbz,
                                              R* __restrict__ W, long long q, int* nfl) {
-  const double rf = rho < P.rho_floor ? P.rho_floor : rho;
+  // (FP32 path: the FP64 comparisons only where the FP32 pre-checks cannot decide them)
+  const R rr = Ar<R>::from_d(rho);
+  const bool rho_in = sizeof(R) == 4 && surely_above(float(rr), P.rho_floor_f);
+  const double rf = rho_in ? rho : (rho < P.rho_floor ? P.rho_floor : rho);
   const double irho = inv_density<R>(rf);
   const double m2 = __fma_rn(mz, mz, __fma_rn(my, my, __dmul_rn(mx, mx)));
   const double b2 = __fma_rn(sbz, sbz, __fma_rn(sby, sby, __dmul_rn(sbx, sbx)));
   const double p = __fma_rn(-P.egm1, b2, __fma_rn(-P.hgm1, __dmul_rn(m2, irho), __dmul_rn(P.gm1, e)));
+  const R pr = Ar<R>::from_d(p);
+  if (rho_in && surely_inside(float(pr), float(rr) * P.pr_floor_f, float(rr) * P.pr_ceil_f))
+    return prim_tail<R>(P, rr, irho, mx, my, mz, e, sbx, sby, sbz, pr, W, q, true, true);
   const double lo = rf * P.pr_floor, hi = rf * P.pr_ceil;
   const double pf = p < lo ? lo : (p > hi ? hi : p);
-  if (rf == rho && pf == p) return prim_tail<R>(P, rho, irho, mx, my, mz, e, sbx, sby, sbz, p, W, q, true, true);
+  if (rf == rho && pf == p) return prim_tail<R>(P, rr, irho, mx, my, mz, e, sbx, sby, sbz, pr, W, q, true, true);
   rho = rf;
   e = pf / P.gm1 + 0.5 * m2 * irho + 0.125 * b2;  // p/(gamma-1) + |m|^2/(2 rho) + |B_cc|^2/2
   ++*nfl;

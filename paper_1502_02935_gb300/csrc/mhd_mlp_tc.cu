@@ -290,16 +290,19 @@ __global__ void __launch_bounds__(128, 8) k_thermal_surrogate_tc(PatchDev P, The
         const double e1 = e0 + f2d_alu(cef * rf * dT);
         P.Un[EN * FS + cs] = e1;
         if (Wst) {
-          if (P.floors && rho < P.rho_floor) {
+          // (the floors' FP64 comparisons only where the FP32 pre-check cannot decide them)
+          if (P.floors && !surely_above(rf, P.rho_floor_f) && rho < P.rho_floor) {
             // the recovery floors the density (not after the step's own floors): in full
             lim = fminf(lim, prim_point<float>(P, P.Un, Wst, i, j, k, true, true));
           } else {
             double p1 = recovery_pressure(P, rt, e1);
-            if (P.floors) {
+            float pr = d2f_alu(p1);
+            if (P.floors && !surely_inside(pr, rf * P.pr_floor_f, rf * P.pr_ceil_f)) {
               const double lo = rho * P.pr_floor, hi = rho * P.pr_ceil;
               p1 = p1 < lo ? lo : (p1 > hi ? hi : p1);
+              pr = d2f_alu(p1);
             }
-            lim = fminf(lim, prim_store<float>(P, rf, vx, vy, vz, bx, by, bz, d2f_alu(p1), finite_d(e1), Wst,
+            lim = fminf(lim, prim_store<float>(P, rf, vx, vy, vz, bx, by, bz, pr, finite_d(e1), Wst,
                                                qidx(P, i, j, k), true, true));
           }
         }
