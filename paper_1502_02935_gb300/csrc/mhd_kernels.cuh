@@ -298,6 +298,39 @@ __global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
   emf_point<R>(P, (const R*)P.W, (R*)P.E, i, j, k);
 }
 
+// Periodic images of the W of interior cell (i, j, k) for a patch with fewer than three active
+// axes: the shifts by 0 or +-n that land in [-2, n + 1] along the active axes only (a trivial
+// axis has no ghost shell).
+template <class R>
+__device__ __forceinline__ void periodic_images_act(const PatchDev& P, R* __restrict__ W, int i, int j, int k,
+                                                    long long q) {
+  const int c[3] = {i, j, k};
+  bool near = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) near |= P.act[a] && (c[a] < 2 || c[a] >= P.n[a] - 2);
+  if (!near) return;
+  const long long QS = P.QS;
+  R v[NWQ];
+#pragma unroll
+  for (int m = 0; m < NWQ; ++m) v[m] = W[m * QS + q];
+  const int z0 = P.act[2] ? -1 : 0, y0 = P.act[1] ? -1 : 0, x0 = P.act[0] ? -1 : 0;
+  for (int sz = z0; sz <= -z0; ++sz) {
+    const int kk = k + sz * P.n[2];
+    if (kk < -2 || kk > P.n[2] + 1) continue;
+    for (int sy = y0; sy <= -y0; ++sy) {
+      const int jj = j + sy * P.n[1];
+      if (jj < -2 || jj > P.n[1] + 1) continue;
+      for (int sx = x0; sx <= -x0; ++sx) {
+        const int ii = i + sx * P.n[0];
+        if (ii < -2 || ii > P.n[0] + 1 || (sx == 0 && sy == 0 && sz == 0)) continue;
+        const long long t = qidx(P, ii, jj, kk);
+#pragma unroll
+        for (int m = 0; m < NWQ; ++m) W[m * QS + t] = v[m];
+      }
+    }
+  }
+}
+
 // Stage update fused with the recovery of the new state (see update_fused_point).  Its FP64
 // arithmetic is the bound; six resident blocks per SM (40 registers, a few spills to L1)
 // hide the memory latency better than fewer blocks without spills (measured).  The
@@ -306,7 +339,8 @@ __global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
 template <class R>
 __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const double* __restrict__ Ub,
                                                          const double* __restrict__ Us,
-                                                         double* __restrict__ Uo, Range rg, StageArgs a) {
+                                                         double* __restrict__ Uo, Range rg, StageArgs a,
+                                                         int images) {
   // dt and h once per block
   __shared__ R sh;
   if (threadIdx.x == 0) {
@@ -323,8 +357,11 @@ __global__ void __launch_bounds__(kBlock, 6) k_update_fused(PatchDev P, const do
   const R h = sh;
   int i, j, k, nfl = 0;
   R lim = R(INFINITY);
-  if (range_point(rg, i, j, k))
+  if (range_point(rg, i, j, k)) {
     lim = update_fused_point<R>(P, Ub, Us, Uo, (const R*)P.E, h, a.src, i, j, k, a.stage == 1, &nfl);
+    // (every axis periodic: the new cell's W also at its images in the ghost shell)
+    if (images && i < P.n[0] && j < P.n[1] && k < P.n[2]) periodic_images_act<R>(P, (R*)P.W, i, j, k, qidx(P, i, j, k));
+  }
   if (a.stage == 1) {
     if (P.floors) {
       const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nfl);
@@ -918,7 +955,9 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
   const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
   const bool fused = P.act[0] && P.act[1] && P.act[2] && P.W2;
   // all axes periodic: the fused kernel writes W's ghost images itself
-  const int images = fused && P.per[0] && P.per[1] && P.per[2];
+  // all axes periodic (a trivial axis counts as periodic): the update kernel writes W's ghost
+  // images itself
+  const int images = P.per[0] && P.per[1] && P.per[2];
   PatchDev Q = P;  // Q.W: the W the stage reads
   PatchDev G = P;  // G.W: the W the stage writes
   if (fused) {
@@ -956,7 +995,7 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
   } else {
     const Range er = edge_range(P);
     ProfScope ps(prof, KC_UPDATE, s);
-    k_update_fused<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, P.Uh, er, a);
+    k_update_fused<R><<<grid_of(er), kBlock, 0, s>>>(P, P.Un, Usrc, P.Uh, er, a, images);
     ++nl;
   }
   if (!images) {
