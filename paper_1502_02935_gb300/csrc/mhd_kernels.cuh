@@ -290,6 +290,46 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_flux_d3(Patc
   }
 }
 
+// The same for patches whose active axes are x and y (a 2D plane): a thread per cell of
+// [-1, n0] x [-1, n1] computes its lower x and y faces from W(c), W(c - x) and W(c - y).
+template <class R, int S>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_flux_d2(PatchDev P, const double* __restrict__ Ub) {
+  const unsigned ex = (unsigned)P.n[0] + 2u, ey = (unsigned)P.n[1] + 2u;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ex * ey) return;
+  const unsigned qy = r / ex;
+  const int i = -1 + (int)(r - qy * ex), j = -1 + (int)qy;
+  const R* __restrict__ W = (const R*)P.W;
+  const long long QS = P.QS, QX = P.QX;
+  const R gam = Gam<R>::get(P);
+  const long long q = qidx(P, i, j, 0);
+  R w[8], out[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) w[m] = W[m * QS + q];
+  if (i >= 0) {  // x face: [rho, vx, vy, vz, p, By, Bz]
+    R wl[7], wr[7];
+    const int cp[7] = {WR, WVX, WVY, WVZ, WP, WBY, WBZ};
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      wl[m] = W[cp[m] * QS + q - 1];
+      wr[m] = w[cp[m]];
+    }
+    riemann<R>(S, wl, wr, face_bn<R, 0>(P, Ub, i, j, 0), gam, out);
+    store_flux<R, 0>((R*)P.F[0], QS, q, out);
+  }
+  if (j >= 0) {  // y face: [rho, vy, vz, vx, p, Bz, Bx]
+    R wl[7], wr[7];
+    const int cp[7] = {WR, WVY, WVZ, WVX, WP, WBZ, WBX};
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      wl[m] = W[cp[m] * QS + q - QX];
+      wr[m] = w[cp[m]];
+    }
+    riemann<R>(S, wl, wr, face_bn<R, 1>(P, Ub, i, j, 0), gam, out);
+    store_flux<R, 1>((R*)P.F[1], QS, q, out);
+  }
+}
+
 // corner EMFs: memory-latency bound; eight resident blocks per SM (measured)
 template <class R>
 __global__ void __launch_bounds__(kBlock, 8) k_emf(PatchDev P, Range rg) {
@@ -892,13 +932,36 @@ static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usr
     int seg = kMarch;
     while (seg > 2 && cols * ((planes + seg - 1) / seg) < want) seg >>= 1;
     if (cols * ((planes + seg - 1) / seg) >= want) {
-      ProfScope ps(prof, KC_FLUX1_XYZ, s0);
-      const dim3 g((unsigned)((cols + kBlock - 1) / kBlock), (unsigned)((planes + seg - 1) / seg), 1);
-      if (P.riemann == RIEMANN_HLLC) k_flux_d3<R, RIEMANN_HLLC><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
-      else if (P.riemann == RIEMANN_HLL) k_flux_d3<R, RIEMANN_HLL><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
-      else k_flux_d3<R, RIEMANN_HLLD><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
-      return 1;
+      {
+        ProfScope ps(prof, KC_FLUX1_XYZ, s0);
+        const dim3 g((unsigned)((cols + kBlock - 1) / kBlock), (unsigned)((planes + seg - 1) / seg), 1);
+        if (P.riemann == RIEMANN_HLLC) k_flux_d3<R, RIEMANN_HLLC><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
+        else if (P.riemann == RIEMANN_HLL) k_flux_d3<R, RIEMANN_HLL><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
+        else k_flux_d3<R, RIEMANN_HLLD><<<g, kBlock, 0, s0>>>(P, Usrc, seg);
+      }
+      if (!emf) return 1;
+      const Range er = edge_range(P);
+      ProfScope ps(prof, KC_EMF, s0);
+      k_emf<R><<<grid_of(er), kBlock, 0, s0>>>(P, er);
+      return 2;
     }
+  }
+  if (a.stage == 0 && P.act[0] && P.act[1] && !P.act[2] && P.flux_scheme == FLUX_AUTO) {
+    // a 2D plane: the predictor's x and y faces in one kernel, a thread per cell; then the
+    // corner EMFs as below
+    {
+      ProfScope ps(prof, KC_FLUX1_XYZ, s0);
+      const long long cols = (long long)(P.n[0] + 2) * (P.n[1] + 2);
+      const dim3 g((unsigned)((cols + kBlock - 1) / kBlock), 1, 1);
+      if (P.riemann == RIEMANN_HLLC) k_flux_d2<R, RIEMANN_HLLC><<<g, kBlock, 0, s0>>>(P, Usrc);
+      else if (P.riemann == RIEMANN_HLL) k_flux_d2<R, RIEMANN_HLL><<<g, kBlock, 0, s0>>>(P, Usrc);
+      else k_flux_d2<R, RIEMANN_HLLD><<<g, kBlock, 0, s0>>>(P, Usrc);
+    }
+    if (!emf) return 1;
+    const Range er = edge_range(P);
+    ProfScope ps(prof, KC_EMF, s0);
+    k_emf<R><<<grid_of(er), kBlock, 0, s0>>>(P, er);
+    return 2;
   }
   int nl = 0;
   const bool par = fk && !prof && P.act[0] + P.act[1] + P.act[2] >= 2;
