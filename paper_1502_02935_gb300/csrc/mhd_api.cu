@@ -712,8 +712,9 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
               (long long)n[0] * n[1] * (n[2] + 1);
     if (H.dense > max_dense) max_dense = H.dense;
     const size_t sbytes = sizeof(double) * 16 * (size_t)D.FS;
-    // W, F (3 directions), E, and for a patch with three active axes a second W buffer
-    const bool w2 = D.act[0] && D.act[1] && D.act[2];
+    // W, F (3 directions), E, and for a patch with three active axes or an x-y plane a second
+    // W buffer (the fused EMF + update kernels read one W and write the other)
+    const bool w2 = D.act[0] && D.act[1];
     const size_t qbytes = ctx->be.scratch_elem * (size_t)(NWQ + 3 * NFLUX + 3 + (w2 ? NWQ : 0)) * (size_t)D.QS;
     if (cudaMalloc(&H.state, sbytes) != cudaSuccess) return bail(MHD_ERR_NOMEM);
     if (cudaMalloc(&H.scratch, qbytes) != cudaSuccess) return bail(MHD_ERR_NOMEM);

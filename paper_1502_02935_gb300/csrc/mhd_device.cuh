@@ -52,7 +52,7 @@ struct PatchDev {
   void* W;
   void* F[3];
   void* E;
-  void* W2;  // second W buffer of the fused EMF + update kernel (3D patches)
+  void* W2;  // second W buffer of the fused EMF + update kernels (3D patches, x-y planes)
   unsigned long long* cfl_min;  // per-patch ordered-bits minimum of the CFL limit
   double* dt_used;
   int* err;

@@ -758,6 +758,118 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
   }
 }
 
+// Corner EMFs and the stage update in one kernel for a 2D plane (x and y active, z trivial):
+// the single-plane form of k_emf_update.  A CTA owns a kTX x kTY tile of cells:
+//  (A) E_z at the tile's edges and its upper halo row and column (corner_value), into shared
+//      memory;
+//  (B) the new x and y faces of the tile and its upper halo (-curl E with E_z from shared
+//      memory), and each cell's z face, whose edge EMFs along x and y are the fluxes of B_z
+//      through the y and x faces (-F_y(B_z) and F_x(B_z), as corner_point takes them on a
+//      trivial axis); faces of the extra layer of an outflow axis are stored here;
+//  (C) each cell: flux divergence and source, its owned faces stored, the floors when asked,
+//      the recovery of the new state and its CFL limit, and its periodic images.
+// Every face takes face_from's operations in the order face_new gives them on a plane, so
+// the state is bit for bit that of the corner-EMF kernel followed by k_update_fused.  The
+// cell EMFs come from Win while neighbouring tiles write the new W to Wout.
+template <class R>
+__global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update2(PatchDev P, const R* __restrict__ Win,
+                                                        R* __restrict__ Wout, const double* __restrict__ Ub,
+                                                        const double* __restrict__ Us, double* __restrict__ Uo,
+                                                        StageArgs a, int images, int cells_out) {
+  constexpr int SX = kTX + 1;  // row pitch of the arrays with an x halo
+  __shared__ R sEz[(kTY + 1) * SX];
+  __shared__ double sBx[kTY * SX];
+  __shared__ double sBy[(kTY + 1) * kTX];
+  __shared__ R sh;
+  if (threadIdx.x == 0) {
+    double dt;
+    if (a.stage == 0) {
+      dt = a.dt_host > 0.0 ? a.dt_host : a.cfl * __longlong_as_double((long long)*P.cfl_min);
+      if (blockIdx.x == 0) *P.dt_used = dt;
+    } else {
+      dt = *P.dt_used;
+    }
+    sh = Ar<R>::from_d(a.stage == 0 ? 0.5 * dt : dt);
+  }
+  __syncthreads();
+  const R h = sh;
+  const int ntx = (P.n[0] + kTX - 1) / kTX;
+  const int i0 = (int)(blockIdx.x % ntx) * kTX, j0 = (int)(blockIdx.x / ntx) * kTY;
+  const int ni = min(kTX, P.n[0] - i0), nj = min(kTY, P.n[1] - j0);
+  const int ti = (int)threadIdx.x % kTX, tj = (int)threadIdx.x / kTX;
+  const bool own = ti < ni && tj < nj;
+  const R ix = Gam<R>::inv(P, 0), iy = Gam<R>::inv(P, 1), iz = Gam<R>::inv(P, 2);
+  const long long FS = P.FS, QS = P.QS, QX = P.QX;
+  const R zero = R(0);
+  // (A) E_z
+  auto put_ez = [&](int ii, int jj) { sEz[jj * SX + ii] = emf_at<R>(P, Win, 2, i0 + ii, j0 + jj, 0); };
+  if (own) put_ez(ti, tj);
+  if (tj == 0 && ti < ni) put_ez(ti, nj);
+  if (tj == 2 && ti <= nj) put_ez(ni, ti);
+  __syncthreads();
+  // (B) x and y faces (face_new on a plane: the x face has only the dE_z/dy term, the y face
+  // only -dE_z/dx)
+  if (own) {
+    const long long so = sidx(P, i0 + ti, j0 + tj, 0);
+    sBx[tj * SX + ti] = face_from<R>(Ub[BXF * FS + so], sEz[tj * SX + ti], sEz[(tj + 1) * SX + ti], zero, zero, iy,
+                                     iz, h);
+    sBy[tj * kTX + ti] = face_from<R>(Ub[BYF * FS + so], zero, zero, sEz[tj * SX + ti], sEz[tj * SX + ti + 1], iz,
+                                      ix, h);
+  }
+  if (tj == 0 && ti < nj) {  // x face at the halo column
+    const int jj = ti, i = i0 + ni, j = j0 + jj;
+    const double b = face_from<R>(Ub[BXF * FS + sidx(P, fmap(P, 0, i), j, 0)], sEz[jj * SX + ni],
+                                  sEz[(jj + 1) * SX + ni], zero, zero, iy, iz, h);
+    sBx[jj * SX + ni] = b;
+    if (i == P.n[0] && P.nface[0] > P.n[0]) Uo[BXF * FS + sidx(P, i, j, 0)] = b;
+  }
+  if (tj == 1 && ti < ni) {  // y face at the halo row
+    const int ii = ti, i = i0 + ii, j = j0 + nj;
+    const double b = face_from<R>(Ub[BYF * FS + sidx(P, i, fmap(P, 1, j), 0)], zero, zero, sEz[nj * SX + ii],
+                                  sEz[nj * SX + ii + 1], iz, ix, h);
+    sBy[nj * kTX + ii] = b;
+    if (j == P.n[1] && P.nface[1] > P.n[1]) Uo[BYF * FS + sidx(P, i, j, 0)] = b;
+  }
+  __syncthreads();
+  // (C) the cell
+  R lim = R(INFINITY);
+  int nfl = 0;
+  if (own) {
+    const int i = i0 + ti, j = j0 + tj;
+    const long long s = sidx(P, i, j, 0);
+    const long long q = qidx(P, i, j, 0);
+    // its z face: E_y = F_x(B_z) at the x faces, E_x = -F_y(B_z) at the y faces
+    const R* Fx = (const R*)P.F[0];
+    const R* Fy = (const R*)P.F[1];
+    const double bz = face_from<R>(Ub[BZF * FS + s], Fx[6 * QS + q], Fx[6 * QS + q + 1], -Fy[5 * QS + q],
+                                   -Fy[5 * QS + q + QX], ix, iy, h);
+    double u[5];
+    cell_update<R>(P, Ub, Us, h, a.src, i, j, 0, s, q, u);
+    const double blo[3] = {sBx[tj * SX + ti], sBy[tj * kTX + ti], bz};
+    const double bhi[3] = {sBx[tj * SX + ti + 1], sBy[(tj + 1) * kTX + ti], bz};
+    if (a.stage == 1 && P.floors)
+      nfl += floor_core(P, u[0], u[1], u[2], u[3], u[4], blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2]);
+    if (cells_out) {
+      Uo[s] = u[0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Uo[(MX + c) * FS + s] = u[1 + c];
+      Uo[EN * FS + s] = u[4];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Uo[(BXF + c) * FS + s] = blo[c];
+    lim = prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2], Wout, q,
+                       true, true);
+    if (images) periodic_images_act<R>(P, Wout, i, j, 0, q);
+  }
+  if (a.stage == 1) {
+    if (P.floors) {
+      const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)nfl);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.floored, (unsigned long long)tot);
+    }
+    block_min_atomic(lim, P.cfl_min);
+  }
+}
+
 // X of the passive scalars over the padded box, from the stage's input state
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_scalar_prim(PatchDev P, const double* __restrict__ U,
@@ -1017,17 +1129,18 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
                        ProfRec* prof, const ForkSet* fk) {
   const double* Usrc = a.stage == 0 ? P.Un : P.Uh;  // state the fluxes and S are built from
   const bool fused = P.act[0] && P.act[1] && P.act[2] && P.W2;
-  // all axes periodic: the fused kernel writes W's ghost images itself
+  // a 2D plane in x and y: the single-plane fused kernel
+  const bool fused2 = P.act[0] && P.act[1] && !P.act[2] && P.W2;
   // all axes periodic (a trivial axis counts as periodic): the update kernel writes W's ghost
   // images itself
   const int images = P.per[0] && P.per[1] && P.per[2];
   PatchDev Q = P;  // Q.W: the W the stage reads
   PatchDev G = P;  // G.W: the W the stage writes
-  if (fused) {
+  if (fused || fused2) {
     Q.W = a.stage == 0 ? P.W : P.W2;
     G.W = a.stage == 0 ? P.W2 : P.W;
   }
-  int nl = issue_fluxes<R>(Q, a, Usrc, s, prof, !fused, fk);
+  int nl = issue_fluxes<R>(Q, a, Usrc, s, prof, !(fused || fused2), fk);
   if (nl < 0) return -1;
   if (P.ns > 0) {
     // passive scalars, before the update overwrites the corrector's input state in Uh
@@ -1054,6 +1167,13 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
     else
       k_emf_update<R, false><<<grid, kEB, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, lz, images,
                                                   cells_out);
+    ++nl;
+  } else if (fused2) {
+    ProfScope ps(prof, KC_EMF_UPDATE, s);
+    const int ntx = (P.n[0] + kTX - 1) / kTX, nty = (P.n[1] + kTY - 1) / kTY;
+    const int cells_out = !(a.stage == 0 && images && a.src.potential == POT_NONE && P.ns == 0);
+    k_emf_update2<R><<<(unsigned)(ntx * nty), kEB, 0, s>>>(Q, (const R*)Q.W, (R*)G.W, P.Un, Usrc, P.Uh, a, images,
+                                                          cells_out);
     ++nl;
   } else {
     const Range er = edge_range(P);
