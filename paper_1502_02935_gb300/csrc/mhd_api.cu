@@ -534,6 +534,7 @@ static int issue_step(mhd_ctx* ctx, double dt) {
   a.cfl = ctx->cfl;
   a.src = ctx->src;
   if (!ctx->aux.empty() && !ctx->profiling) {
+    a.concurrent = 1;
     // one chain per patch: [recovery], predictor, reset of its CFL slot, corrector
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     for (auto q : ctx->aux) CK(cudaStreamWaitEvent(q, ctx->ev_fork, 0));

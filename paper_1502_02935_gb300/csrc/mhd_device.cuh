@@ -92,6 +92,7 @@ struct StageArgs {
   double dt_host;  // > 0: use it; <= 0: cfl * device CFL limit
   double cfl;
   SourceDev src;
+  int concurrent;  // host side: the patch's chain runs beside other patches' (a batch)
 };
 
 // ------------------------------------------------------------------ indexing --
