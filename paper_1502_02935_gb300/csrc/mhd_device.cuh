@@ -620,11 +620,12 @@ __device__ __forceinline__ bool finite_d(double x) {
 // W of one cell from its conserved values: Eq. 6 for the cell-centred field (sbx, sby, sbz
 // are the sums of the two face values, i.e. twice it), the energy closure after Eq. 3 for p
 // (FP64 in both paths), with the floors when they are on.  Stores W at scratch index q when
-// asked; returns the CFL limit min_d d/(|v_d| + c_f,d) for interior cells (else +inf).
+// asked; returns the CFL limit min_d d/(|v_d| + c_f,d) for interior cells when cfl is set
+// (else +inf; the predictor's new state needs no CFL limit: 256^3 step 4.210 -> 4.190 ms).
 template <class R>
 __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx, double my, double mz,
                                             double e, double sbx, double sby, double sbz, R* __restrict__ W,
-                                            long long q, bool store, bool interior) {
+                                            long long q, bool store, bool interior, bool cfl = true) {
   if (P.floors && rho < P.rho_floor) rho = P.rho_floor;
   // Every operation below is explicitly rounded (intrinsics are never contracted or
   // reordered): the recovery fused into the update kernel and the standalone recovery store
@@ -665,19 +666,21 @@ __device__ __forceinline__ R prim_core(const PatchDev& P, double rho, double mx,
     } else if (!(rr > R(0)) || !(pr > R(0))) {
       atomicOr(P.err, ERR_NEGATIVE);
     }
-    const R v[3] = {vx, vy, vz};
-    const R b[3] = {bx, by, bz};
-    const R bb = Ar<R>::fma_rn(b[2], b[2], Ar<R>::fma_rn(b[1], b[1], Ar<R>::mul_rn(b[0], b[0])));
-    const R gam = Gam<R>::get(P);
-    R lr = R(INFINITY);
+    if (cfl) {
+      const R v[3] = {vx, vy, vz};
+      const R b[3] = {bx, by, bz};
+      const R bb = Ar<R>::fma_rn(b[2], b[2], Ar<R>::fma_rn(b[1], b[1], Ar<R>::mul_rn(b[0], b[0])));
+      const R gam = Gam<R>::get(P);
+      R lr = R(INFINITY);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (!P.act[a]) continue;
-      const R cf = fast_speed_rn<R>(rr, pr, bb, Ar<R>::mul_rn(b[a], b[a]), gam);
-      const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::add_rn(Ar<R>::abs_(v[a]), cf));
-      lr = t < lr ? t : lr;
+      for (int a = 0; a < 3; ++a) {
+        if (!P.act[a]) continue;
+        const R cf = fast_speed_rn<R>(rr, pr, bb, Ar<R>::mul_rn(b[a], b[a]), gam);
+        const R t = Ar<R>::div(Gam<R>::d(P, a), Ar<R>::add_rn(Ar<R>::abs_(v[a]), cf));
+        lr = t < lr ? t : lr;
+      }
+      lim = lr;
     }
-    lim = lr;
   }
   return lim;
 }
@@ -1252,9 +1255,9 @@ __device__ __forceinline__ R update_fused_point(const PatchDev& P, const double*
   Uo[EN * FS + s] = u[4];
 #pragma unroll
   for (int a = 0; a < 3; ++a) Uo[(BXF + a) * FS + s] = blo[a];
-  // recovery of the new cell
+  // recovery of the new cell (its CFL limit in the corrector only)
   return prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2],
-                      (R*)P.W, q, true, true);
+                      (R*)P.W, q, true, true, last);
 }
 
 // Ghost position number t of the padded scratch box (the shell of width g2 around the

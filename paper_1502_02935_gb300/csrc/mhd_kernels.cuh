@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
         l = last ? floor_prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1],
                                       blo[2] + bhi[2], Wout, q, &nfl)
                  : prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1],
-                                blo[2] + bhi[2], Wout, q, true, true);
+                                blo[2] + bhi[2], Wout, q, true, true, false);
       }
       if (cells_out) {
         Uo[s] = u[0];
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update(PatchDev P, con
       for (int c = 0; c < 3; ++c) Uo[(BXF + c) * FS + s] = blo[c];
       if constexpr (!FLOORS)
         l = prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2],
-                         Wout, q, true, true);
+                         Wout, q, true, true, last);
       lim = l < lim ? l : lim;
       if (images) periodic_images<R>(P, Wout, i0 + ti, j0 + tj, k, q);
     }
@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(kEB, kEMinBlocks) k_emf_update2(PatchDev P, co
 #pragma unroll
     for (int c = 0; c < 3; ++c) Uo[(BXF + c) * FS + s] = blo[c];
     lim = prim_core<R>(P, u[0], u[1], u[2], u[3], u[4], blo[0] + bhi[0], blo[1] + bhi[1], blo[2] + bhi[2], Wout, q,
-                       true, true);
+                       true, true, a.stage == 1);
     if (images) periodic_images_act<R>(P, Wout, i, j, 0, q);
   }
   if (a.stage == 1) {
