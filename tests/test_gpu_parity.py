@@ -382,6 +382,20 @@ def test_floors_parity_negative_pressure_cell_mixed():
         ref = nxt
 
 
+def test_floors_parity_negative_pressure_cell_plane_fp64():
+    """The floors on an x-y plane (the single-plane EMF + update kernel): a 2D outflow box with
+    a 3 x 3 block of cells whose energy leaves p < 0, three steps, the FP64 bound and the same
+    floored cells (the oracle floors four of them in the first step)."""
+    st = inputs.smooth_random(_geom((40, 20, 1), (1, 1, 1, 1, 0, 0), d=(0.1, 0.1, 1.0)), 5)
+    U = st.U.copy()
+    U[4, 0, 6:9, 12:15] = 0.0
+    st, src = st.replace(U=U), {"rho_floor": 1e-3, "pr_floor": 1e-2}
+    counts = []
+    got, ref, _ = _run_pair(st, src, "fp64", 3, counts=counts)
+    assert_close(got, ref, 3 * FP64_TOL, "plane floors")
+    assert counts[0] == counts[1] and counts[1] >= 1, counts
+
+
 def test_floors_parity_disc():
     """Small disc (24 x 24 x 12) with its potential and floors, FP64, three steps.  Cells
     sitting exactly at the density floor may land either side of it by rounding, so the
