@@ -77,10 +77,10 @@ FP64_OPS_PER_SM_CLK = 2
 # The step's algorithmic HBM bytes per cell: read the 8 FP64 fields of U^n, write U^n+1.
 ALG_BYTES_PER_CELL = 128.0
 # DRAM bytes (read + write) per item of the dominant kernel, from one ncu capture of each
-# stage of the EMF + update kernel on turbulence 192^3 (corrector 2.048 GB, predictor 1.747 GB
-# per launch over 192^3 cells, planes marched as on 256^3), their mean scaled by the items of a
-# launch.  Retake it when the kernel changes.
-MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 0.5 * (2.048e9 + 1.747e9) / 192 ** 3}
+# stage of the EMF + update kernel on turbulence 192^3 (corrector 2.037 GB, predictor 1.734 GB
+# per launch over 192^3 cells, ten planes per CTA as on 256^3), their mean scaled by the items
+# of a launch.  Retake it when the kernel changes.
+MEASURED_DRAM_BYTES_PER_POINT = {"emf_update": 0.5 * (2.037e9 + 1.734e9) / 192 ** 3}
 MEASURED_DRAM_NOTE = {"emf_update": "ncu dram bytes (read + write) at turbulence 192^3, mean of the predictor "
                                     "and corrector launches, per cell, scaled to this launch"}
 

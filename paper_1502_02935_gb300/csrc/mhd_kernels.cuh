@@ -1154,10 +1154,12 @@ static int issue_stage(const PatchDev& P, const StageArgs& a, cudaStream_t s, lo
   }
   if (fused) {
     ProfScope ps(prof, KC_EMF_UPDATE, s);
-    // planes per CTA: 8, halved (down to 2) while the grid would be under two waves of
-    // resident CTAs
+    // planes per CTA: 10, halved (down to 2) while the grid would be under two waves of
+    // resident CTAs (10 against 8, 9, 12, 16 at 256^3: 1.238 ms per launch against 1.253,
+    // 1.242, 1.267, 1.29; also faster on the disc and the batch: each CTA's first plane
+    // recomputes its lower edges, and the grid's last partial wave idles)
     const int ntx = (P.n[0] + kTX - 1) / kTX, nty = (P.n[1] + kTY - 1) / kTY;
-    int lz = 8;
+    int lz = 10;
     while (lz > 2 && (long long)ntx * nty * ((P.n[2] + lz - 1) / lz) < 2LL * kEMinBlocks * sm_count()) lz >>= 1;
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((P.n[2] + lz - 1) / lz), 1);
     // the predictor's cell fields of U^n+1/2 are read by nobody when the corrector's source
