@@ -1036,13 +1036,14 @@ template <class R>
 static int issue_fluxes(const PatchDev& P, const StageArgs& a, const double* Usrc, cudaStream_t s0, ProfRec* prof,
                         bool emf, const ForkSet* fk) {
   if (a.stage == 0 && P.act[0] && P.act[1] && P.act[2] && P.flux_scheme == FLUX_AUTO) {
-    // the predictor's three directions in one marching kernel: segments of 16 planes, 8, 4 or
-    // 2 while the box gives fewer than two waves of four resident CTAs per SM; thinner boxes
-    // keep the per-direction kernels, unless the patch's chain runs beside other patches'
-    // (the 64-patch batch: 11.01 -> 10.92 ms per step with every 3D patch fused)
+    // the predictor's three directions in one marching kernel: segments of 8 planes (at 256^3
+    // 0.651 ms per launch against 0.661 with 16, 0.664 with 24, 0.694 with 32), 4 or 2 while
+    // the box gives fewer than two waves of four resident CTAs per SM; thinner boxes keep the
+    // per-direction kernels, unless the patch's chain runs beside other patches' (the 64-patch
+    // batch: 11.01 -> 10.92 ms per step with every 3D patch fused)
     const long long cols = (long long)(P.n[0] + 2) * (P.n[1] + 2), planes = P.n[2] + 2;
     const long long want = 2LL * 4 * kBlock * sm_count();
-    int seg = kMarch;
+    int seg = 8;
     while (seg > 2 && cols * ((planes + seg - 1) / seg) < want) seg >>= 1;
     if (a.concurrent || cols * ((planes + seg - 1) / seg) >= want) {
       {
