@@ -78,6 +78,16 @@ CASES = {
     "gauss_well_1d_200": lambda: (
         inputs.smooth_random(_geom((200, 1, 1), (1, 1, 0, 0, 0, 0), d=(0.005, 1.0, 1.0), lo=(-0.5, 0, 0)), 2, 0.0),
         dict(potential=1, psi0=5.0, xc=0.0, xw=0.1)),
+    # degenerate shapes: planes and lines off the x-y orientation (the per-direction kernels,
+    # the corner-EMF kernel and the update with periodic images of a trivial x or y axis),
+    # the smallest active axes (2 cells: each ghost is an image of an interior cell) and a
+    # slab two planes thick
+    "yz_plane_1x20x14": lambda: (inputs.smooth_random(_geom((1, 20, 14), (0, 0, 1, 1, 0, 0)), 21), None),
+    "xz_plane_18x1x12": lambda: (inputs.smooth_random(_geom((18, 1, 12), (1, 1, 0, 0, 0, 0)), 22), None),
+    "brio_wu_z_200": lambda: (inputs.brio_wu(200, axis=2), None),
+    "tiny_2x2x2": lambda: (inputs.smooth_random(_geom((2, 2, 2), (0,) * 6), 23), None),
+    "tiny_3x2x2_outflow": lambda: (inputs.smooth_random(_geom((3, 2, 2), (1,) * 6), 24), None),
+    "slab_33x9x2": lambda: (inputs.smooth_random(_geom((33, 9, 2), (0, 0, 1, 1, 0, 0)), 25), None),
 }
 
 

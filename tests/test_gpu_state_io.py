@@ -21,6 +21,8 @@ CASES = {
     "periodic_37x29x23": lambda: inputs.turbulence((37, 29, 23), seed=5),
     "outflow_17x9x5": lambda: inputs.smooth_random(_geom((17, 9, 5), (1,) * 6), 3),
     "orszag_tang_40x24": lambda: inputs.orszag_tang(40, 24),
+    "yz_plane_1x20x14": lambda: inputs.smooth_random(_geom((1, 20, 14), (0, 0, 1, 1, 0, 0)), 21),
+    "tiny_2x2x2": lambda: inputs.smooth_random(_geom((2, 2, 2), (0,) * 6), 23),
 }
 
 

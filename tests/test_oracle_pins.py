@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 from paper_1502_02935_gb300 import inputs
-from tests import textbook
+from tests import axes, textbook
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 RNG = np.random.default_rng(20150211)
@@ -593,6 +593,34 @@ def test_cyclic_axis_permutation_3d():
     assert np.max(np.abs(a.By - np.transpose(b.Bz, (2, 0, 1)))) <= 1e-13
     assert np.max(np.abs(a.Bz - np.transpose(b.Bx, (2, 0, 1)))) <= 1e-13
     assert np.max(np.abs(a.Bx - np.transpose(b.By, (2, 0, 1)))) <= 1e-13
+
+
+def _g01(n, bc):
+    return inputs.Geom(n[0], n[1], n[2], 0.0, 0.0, 0.0, 0.1, 0.11, 0.13, bc, 5.0 / 3.0)
+
+
+@pytest.mark.parametrize("case", ["outflow_10x8x6", "mixed_bc_9x7x5", "orszag_tang_16x12", "brio_wu_64"])
+def test_cyclic_axis_permutation_boundaries_planes_lines(case):
+    """As above, with outflow and mixed boundaries (whose sides move with their axis), a 2D
+    plane turned into a y-z and a z-x plane, and a 1D tube turned into a line along y and z.
+    Both relabellings, three steps at one dt: equal to 1e-13 of each field's scale (only the
+    order of the sums over components changes; the plane and the line come out bit for bit)."""
+    st = {"outflow_10x8x6": lambda: inputs.smooth_random(_g01((10, 8, 6), (1,) * 6), 3),
+          "mixed_bc_9x7x5": lambda: inputs.smooth_random(_g01((9, 7, 5), (1, 1, 0, 0, 1, 1)), 4),
+          "orszag_tang_16x12": lambda: inputs.orszag_tang(16, 12),
+          "brio_wu_64": lambda: inputs.brio_wu(64)}[case]()
+    assert all(np.array_equal(getattr(axes.rotate(st, 3), k), getattr(st, k)) for k in ("U", "Bx", "By", "Bz"))
+    dt = oracle.cfl_dt(st, 0.4)
+    ref = oracle.step(st, dt, nsteps=3)
+    bmax = max(np.max(np.abs(getattr(ref, k))) for k in ("Bx", "By", "Bz"))
+    for r in (1, 2):
+        s = axes.rotate(st, r)
+        assert abs(oracle.cfl_dt(s, 0.4) - dt) <= 1e-15 * dt
+        back = axes.rotate(oracle.step(s, dt, nsteps=3), 3 - r)
+        for f in range(5):
+            assert np.max(np.abs(back.U[f] - ref.U[f])) <= 1e-13 * np.max(np.abs(ref.U[f])), (r, f)
+        for k in ("Bx", "By", "Bz"):
+            assert np.max(np.abs(getattr(back, k) - getattr(ref, k))) <= 1e-13 * bmax, (r, k)
 
 
 @pytest.mark.parametrize("pol", ["inplane", "z"])
