@@ -172,3 +172,34 @@ def test_persistent_carries_solver_and_reconstruction(precision):
         assert_close(sb, sa, tol, f"patch {p}", normalized=(precision == "mixed"))
     a.close()
     b.close()
+
+
+def degenerate_batch():
+    g = lambda n, bc: inputs.Geom(n[0], n[1], n[2], 0, 0, 0, 0.05, 0.06, 0.07, bc, 5.0 / 3.0)
+    return [inputs.turbulence((13, 11, 6), seed=41),
+            inputs.smooth_random(g((1, 20, 14), (0, 0, 1, 1, 0, 0)), 42),
+            inputs.smooth_random(g((18, 1, 12), (1, 1, 0, 0, 0, 0)), 43),
+            inputs.smooth_random(g((2, 2, 2), (0,) * 6), 44),
+            inputs.smooth_random(g((3, 2, 2), (1,) * 6), 45),
+            inputs.smooth_random(g((33, 9, 2), (0, 0, 1, 1, 0, 0)), 46),
+            inputs.brio_wu(64, axis=2)]
+
+
+@pytest.mark.parametrize("scheme", ["per_phase", "persistent"])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
+def test_degenerate_patches_match_oracle(precision, tol, scheme):
+    """A batch of degenerate patches in both schemes: a y-z and an x-z plane, 2 x 2 x 2 and
+    3 x 2 x 2 boxes (the per-phase chains run the fused donor-cell kernel on them, in
+    segments of 2 planes), a slab two planes thick and a line along z, beside a small 3D box.
+    Each patch equals the oracle run with its own CFL dt."""
+    sts = degenerate_batch()
+    flags = mhd.FLAG_PERSISTENT if scheme == "persistent" else mhd.FLAG_GRAPH
+    g = mhd.Grid(sts, precision=precision, cfl=0.4, flags=flags)
+    dts = g.cfl_dt_patches()
+    g.step(-1.0)
+    for p, st in enumerate(sts):
+        want_dt = oracle.cfl_dt(st, 0.4)
+        assert abs(dts[p] - want_dt) <= (1e-14 if precision == "fp64" else 1e-6) * want_dt, p
+        ref = oracle.step(st, dts[p], eq11_eps=EQ11[precision])
+        assert_close(g.get_state(p), ref, tol, f"patch {p}", normalized=(precision == "mixed"))
+    g.close()
