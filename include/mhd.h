@@ -143,7 +143,12 @@ typedef struct mhd_ctx mhd_ctx; /* opaque, library-owned */
 
 /* Create a context, allocate the device state of every patch and copy the
  * initial state in.  U0[p] / Bface0[p] follow the host state format above.
- * On failure *out is NULL and nothing stays allocated. */
+ * On failure *out is NULL and nothing stays allocated.  MHD_ERR_ARG for a bad
+ * descriptor: a cell count outside [1, 2^20] per axis or above 2^40 per patch, an
+ * active axis (more than one cell) without a boundary condition on each side or
+ * with periodicity on one side only, a non-positive spacing, gamma <= 1, a null
+ * state pointer.  MHD_ERR_NOMEM when the device cannot hold the buffers; the
+ * runtime's error state is left clear, so other contexts are unaffected. */
 int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* grid, const double* const* U0,
                   const double* const* Bface0, int on_device);
 

@@ -243,6 +243,9 @@ struct mhd_ctx {
 
 static int fail(mhd_ctx* c, int code, const std::string& msg) {
   if (c) c->last_error = msg;
+  // a failed allocation leaves its (non-sticky) error as the runtime's last error, where the
+  // next launch check of this or another context would find it: consume it here
+  if (code == MHD_ERR_NOMEM) cudaGetLastError();
   return code;
 }
 
@@ -321,6 +324,9 @@ static int validate_patch(const mhd_patch_desc& d, std::string& why) {
     }
   }
   if (!(d.gamma > 1.0) || !std::isfinite(d.gamma)) { why = "gamma must be > 1"; return -1; }
+  // 2^40 cells (140 TB of state): far above any device, and low enough that no buffer size
+  // computed from the extents overflows
+  if ((double)n[0] * n[1] * n[2] > 1099511627776.0) { why = "patch too large"; return -1; }
   return 0;
 }
 
@@ -644,6 +650,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
       ctx->sms = sms;
   }
   auto bail = [&](int code) {
+    if (code == MHD_ERR_NOMEM) cudaGetLastError();  // as in fail()
     free_ctx(ctx);
     return code;
   };

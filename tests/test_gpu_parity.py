@@ -612,3 +612,26 @@ def test_blast_reflection_symmetry_on_gpu(precision, tol, axis):
     for c, b in enumerate(faces):
         s = (1.0 if c == axis else -1.0) if axis == 0 else (-1.0 if c == axis else 1.0)
         assert np.max(np.abs(b - s * np.flip(b, axis=2 - axis))) <= tol * bmax, c
+
+
+def test_oversized_grids_are_refused_and_leave_the_device_usable():
+    """Maximum sizes.  A 2048^3 patch (1.1 TB of FP64 state alone) is refused with
+    MHD_ERR_NOMEM by its first allocation, before any host array is read; a patch above
+    2^40 cells with MHD_ERR_ARG, before any allocation.  The failed allocation leaves no
+    error behind: a small grid made afterwards steps and matches the oracle."""
+    import ctypes as C
+    L = mhd.lib()
+    dummy = np.zeros(8)
+    for n, want in (((2048, 2048, 2048), -7), ((1 << 14, 1 << 14, 1 << 13), -1)):
+        d = (mhd.PatchDesc * 1)()
+        d[0].nx, d[0].ny, d[0].nz = n
+        d[0].dx = d[0].dy = d[0].dz = 1.0 / n[0]
+        d[0].gamma = 5.0 / 3.0
+        gd = mhd.GridDesc(1, d, 1, 0.4, 0, None)
+        ptr = (C.c_void_p * 1)(dummy.ctypes.data)
+        h = C.c_void_p()
+        assert L.mhd_init_grid(C.byref(h), C.byref(gd), ptr, ptr, 0) == want, n
+        assert not h.value
+    st, src = CASES["outflow_17x9x5"]()
+    got, ref, _ = _run_pair(st, src, "fp64", 1)
+    assert_close(got, ref, FP64_TOL, "after the refused grids")
