@@ -354,6 +354,10 @@ const char* mhd_last_error(const mhd_ctx* ctx);
 
 void mhd_destroy(mhd_ctx* ctx);
 
+/* The unit-level entries below (mhd_riemann_hlld, mhd_riemann_flux, mhd_thermal_cells,
+ * mhd_mlp_forward[_tc], mhd_convert_fp) accept n = 0, launch nothing and then allow NULL
+ * array pointers; n < 0 is MHD_ERR_ARG.  mhd_mlp_grad[_tc] need 1 <= n <= 2^20. */
+
 /* Unit-level entry for parity tests: HLLD fluxes (Miyoshi & Kusano 2005, the solver
  * named in Section 2.1) of n interfaces in the interface frame, computed by the
  * same device function the step uses.  wl, wr: n*8 values [rho, vn, vt1, vt2, p,

@@ -1234,7 +1234,7 @@ template <class R>
 static int issue_riemann(int solver, int n, const double* wl, const double* wr, const double* bn, double gam,
                          double* flux, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_riemann<R><<<(n + 127) / 128, 128, 0, s>>>(solver, n, wl, wr, bn, gam, flux);
+  k_riemann<R><<<(unsigned)(((long long)n + 127) / 128), 128, 0, s>>>(solver, n, wl, wr, bn, gam, flux);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
