@@ -83,8 +83,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 1) k_flux(PatchDe
 // spill at four).
 constexpr int kMarch = 16;
 
+// Block size of the marching kernels: 128 threads for the FP32 kappa-scheme, seven blocks per
+// SM (72 registers, 28 warps; at 256^3 the y and z launches took 0.333 and 0.315 ms against
+// 0.356 and 0.347 with three blocks of 256 threads at 78 registers, 24 warps; eight blocks
+// spill), kBlock otherwise.
+template <class R, int ORDER> constexpr int march_block() { return sizeof(R) == 4 && ORDER == 2 ? 128 : kBlock; }
+
 template <class R, int D, int ORDER, int S>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ORDER == 1 ? 4 : 3) : 1) k_flux_march(PatchDev P,
+__global__ void __launch_bounds__(march_block<R, ORDER>(), sizeof(R) == 4 ? (ORDER == 1 ? 4 : 7) : 1) k_flux_march(PatchDev P,
                                                                              const double* __restrict__ Ub,
                                                                              Range rg, int seg) {
   static_assert(D == 1 || D == 2, "marching along y or z");
@@ -992,8 +998,8 @@ static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cu
   if constexpr (D > 0) {
     // y and z faces: the marching kernel, one thread per (x, other transverse) position and
     // segment of seg faces.  seg = 16, 8, 4 or 2, the longest that still gives two waves of
-    // three resident CTAs of kBlock threads per SM; a box too thin even for seg = 2 (a 2D
-    // plane, a small patch) takes the per-face kernel, which has one thread per face
+    // 3 kBlock (768) resident threads per SM; a box too thin even for seg = 2 (a 2D plane, a
+    // small patch) takes the per-face kernel, which has one thread per face
     constexpr int T = D == 1 ? 2 : 1;
     const long long plane = (long long)fr.ext[0] * fr.ext[T];
     const long long want = 2LL * 3 * kBlock * sm_count();
@@ -1001,10 +1007,11 @@ static void launch_flux(const PatchDev& P, const double* Ub, const Range& fr, cu
     while (P.flux_scheme == FLUX_AUTO && seg > 2 && plane * ((fr.ext[D] + seg - 1) / seg) < want) seg >>= 1;
     if (P.flux_scheme == FLUX_MARCH ||
         (P.flux_scheme == FLUX_AUTO && plane * ((fr.ext[D] + seg - 1) / seg) >= want)) {
-      const dim3 g((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)((fr.ext[D] + seg - 1) / seg), 1);
-      if (P.riemann == RIEMANN_HLLC) k_flux_march<R, D, ORDER, RIEMANN_HLLC><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
-      else if (P.riemann == RIEMANN_HLL) k_flux_march<R, D, ORDER, RIEMANN_HLL><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
-      else k_flux_march<R, D, ORDER, RIEMANN_HLLD><<<g, kBlock, 0, s>>>(P, Ub, fr, seg);
+      constexpr int B = march_block<R, ORDER>();
+      const dim3 g((unsigned)((plane + B - 1) / B), (unsigned)((fr.ext[D] + seg - 1) / seg), 1);
+      if (P.riemann == RIEMANN_HLLC) k_flux_march<R, D, ORDER, RIEMANN_HLLC><<<g, B, 0, s>>>(P, Ub, fr, seg);
+      else if (P.riemann == RIEMANN_HLL) k_flux_march<R, D, ORDER, RIEMANN_HLL><<<g, B, 0, s>>>(P, Ub, fr, seg);
+      else k_flux_march<R, D, ORDER, RIEMANN_HLLD><<<g, B, 0, s>>>(P, Ub, fr, seg);
       return;
     }
   }
