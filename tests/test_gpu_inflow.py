@@ -34,13 +34,19 @@ def _hydro2d():
                       2: (1.1, 0.1, 0.6, 0.0, 1.2, 0.0, 0.0, 0.0)}
 
 
+def _xz_plane():
+    # an x-z plane (trivial y): inflow on x-lo and z-hi, outflow on x-hi and z-lo
+    st = inputs.smooth_random(_geom((18, 1, 12), (2, 1, 0, 0, 1, 2)), 13)
+    return st, None, {0: (1.1, 0.7, 0.1, 0.1, 1.0, 0.2, -0.1, 0.3), 5: (0.9, 0.1, 0.2, -0.5, 1.1, -0.2, 0.1, 0.25)}
+
+
 def _well():
     st, src = inputs.isothermal_well(128)
     return st, src, None
 
 
 CASES = {"bow_shock_200": _bow, "mhd_inflow_17x13x6": _mhd3d, "hydro_inflow_24x20": _hydro2d,
-         "isothermal_well_128": _well}
+         "isothermal_well_128": _well, "xz_inflow_18x1x12": _xz_plane}
 
 
 def _run(case, precision, nsteps, cfl=0.4):

@@ -27,12 +27,16 @@ def _cases():
         "inflow_16x12x8": (inputs.smooth_random(g, 5), {0: (1.1, 0.6, 0.1, 0.0, 0.9, 0.2, 0.1, -0.1)},
                            {0: [0.9, 0.8, 0.1]}),
         "orszag_tang_64x48": (inputs.orszag_tang(64, 48), None, None),
+        # a y-z plane (trivial x) with X entering through the z-lo inflow face
+        "yz_inflow_1x20x14": (inputs.smooth_random(
+            inputs.Geom(1, 20, 14, 0.0, 0.0, 0.0, 0.1, 0.12, 0.09, (0, 0, 1, 1, 2, 1), 5.0 / 3.0), 6),
+            {4: (1.1, 0.1, -0.2, 0.7, 0.9, 0.15, 0.2, 0.3)}, {4: [0.2, 0.9, 0.5]}),
     }
 
 
 @pytest.mark.parametrize("recon", ["kappa_third", "kappa_upwind"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["turbulence_37x29x23", "inflow_16x12x8", "orszag_tang_64x48"])
+@pytest.mark.parametrize("case", ["turbulence_37x29x23", "inflow_16x12x8", "orszag_tang_64x48", "yz_inflow_1x20x14"])
 def test_scalars_match_oracle(case, precision, recon):
     st, inflow, inflow_x = _cases()[case]
     S = _scalars(st, 7)
