@@ -147,7 +147,7 @@ typedef struct mhd_ctx mhd_ctx; /* opaque, library-owned */
  * descriptor: a cell count outside [1, 2^20] per axis or above 2^40 per patch, an
  * active axis (more than one cell) without a boundary condition on each side or
  * with periodicity on one side only, a non-positive spacing, gamma <= 1, a null
- * state pointer.  MHD_ERR_NOMEM when the device cannot hold the buffers; the
+ * state pointer, an unknown precision, a Courant number that is not finite and > 0.  MHD_ERR_NOMEM when the device cannot hold the buffers; the
  * runtime's error state is left clear, so other contexts are unaffected. */
 int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* grid, const double* const* U0,
                   const double* const* Bface0, int on_device);

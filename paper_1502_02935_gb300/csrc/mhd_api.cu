@@ -636,7 +636,7 @@ int mhd_init_grid(mhd_ctx** out, const mhd_grid_desc* g, const double* const* U0
   *out = nullptr;
   if (!g || g->n_patches < 1 || !g->patches || !U0 || !B0) return MHD_ERR_ARG;
   if (g->precision != MHD_PREC_FP64 && g->precision != MHD_PREC_MIXED) return MHD_ERR_ARG;
-  if (!(g->cfl > 0.0)) return MHD_ERR_ARG;
+  if (!(g->cfl > 0.0) || !std::isfinite(g->cfl)) return MHD_ERR_ARG;
   mhd_ctx* ctx = new mhd_ctx();
   ctx->np = g->n_patches;
   ctx->precision = g->precision;
